@@ -1,0 +1,161 @@
+/*
+ * libfbcc: FAST-BCC biconnected components on one GPU (sm_103a), C ABI.
+ *
+ * The operation is the one the paper (Dong, Wang, Gu, Sun, "Provably Fast and
+ * Space-Efficient Parallel Biconnectivity", PPoPP'23) states in Algorithm 1: given
+ * an undirected graph G = (V, E), find its biconnected components (BCCs). The four
+ * steps of Algorithm 1 (First-CC, Rooting, Tagging, Last-CC plus heads; section
+ * 4.1) all run as CUDA kernels on the caller's stream. Where the paper outputs
+ * vertex labels plus a head per label (section 3.4, "space-efficient BCC
+ * representation"), this library expands them into the per-edge form below.
+ *
+ * Graph format (all calls): symmetric CSR. offsets has n+1 entries (int32 or
+ * int64, chosen by `offsets_64`), offsets[0] = 0, offsets[n] = 2m; adj has 2m int32
+ * vertex ids. Every undirected edge {u,v} appears as the two arcs u->v and v->u;
+ * each adjacency list is sorted strictly ascending; no self-loops (a simple graph).
+ * fbcc_validate checks this; the solvers assume it.
+ *
+ * Canonical output (identical, bit for bit, to the Hopcroft-Tarjan oracle):
+ *  - edge id of {u,v}: the rank, in CSR order, of its arc with src < dst among all
+ *    arcs with src < dst;
+ *  - BCC k (k = 0 .. n_bcc-1) is the BCC with the k-th smallest smallest-edge-id;
+ *  - edge_bcc[a]: the BCC index k of arc a (both arcs of an edge agree);
+ *  - bcc_head[k]: the head of BCC k, its shallowest vertex when every connected
+ *    component is rooted at its smallest vertex id (section 4.2);
+ *  - is_ap[v] = 1 iff v is an articulation point; is_bridge[a] = 1 iff arc a's
+ *    edge is a bridge (section 2: removal increases the number of components);
+ *  - isolated vertices belong to no BCC and count as connected components.
+ *
+ * Memory: the caller owns every input and output buffer. Device buffers are
+ * plain device pointers (e.g. from PyTorch). The library owns only the workspace,
+ * allocated once by fbcc_workspace_create. `stream` is a cudaStream_t passed as
+ * void* (NULL = the legacy default stream). Calls are asynchronous on the stream
+ * unless stated; host-checked argument errors return immediately without
+ * launching anything. No C++ exception crosses this interface.
+ */
+#ifndef FBCC_H
+#define FBCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FBCC_OK = 0,
+    FBCC_E_INVALID = 1,     /* bad argument: null pointer, negative size, offsets[n] != 2m, ... */
+    FBCC_E_NOT_SIMPLE = 2,  /* fbcc_validate: self-loop, duplicate, unsorted or asymmetric CSR */
+    FBCC_E_OOM = 3,         /* device memory for the workspace could not be allocated */
+    FBCC_E_CUDA = 4,        /* a CUDA runtime call failed (message: fbcc_last_cuda_error) */
+    FBCC_E_ITER_LIMIT = 5,  /* a bounded device loop hit its cap (reported in stats.device_status) */
+    FBCC_E_WORKSPACE = 6    /* the graph exceeds the workspace's n_max / nnz_max */
+} fbcc_status;
+
+typedef struct fbcc_workspace fbcc_workspace; /* opaque; library-owned device memory */
+
+/* Counts of one solve. device_status is 0 or an fbcc_status a kernel raised. */
+typedef struct {
+    int64_t n_bcc;     /* number of BCCs */
+    int64_t n_ap;      /* number of articulation points */
+    int64_t n_bridge;  /* number of bridges (undirected edges) */
+    int64_t n_cc;      /* connected components, isolated vertices included */
+    int32_t device_status;
+    int32_t reserved;
+} fbcc_stats;
+
+/* Tuning knobs; zero in a field means "library default". */
+typedef struct {
+    int32_t ruler_stride;  /* list ranking: one ruler per this many tree arcs (power of 2) */
+    int32_t cc_sample;     /* First-CC: neighbours per vertex hooked before the full pass (0 = off) */
+    int32_t grid_ctas;     /* CTAs of the persistent grid-stride kernels */
+    int32_t use_graph;     /* 1 = replay a captured CUDA graph for repeated identical calls (default), -1 = never */
+} fbcc_config;
+
+/* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds. */
+size_t fbcc_workspace_bytes(int64_t n, int64_t nnz);
+
+/* Allocate a workspace for graphs with n <= n_max and 2m <= nnz_max.
+ * Returns FBCC_OK and *ws, FBCC_E_INVALID for bad sizes, FBCC_E_OOM or FBCC_E_CUDA. */
+fbcc_status fbcc_workspace_create(int64_t n_max, int64_t nnz_max, fbcc_workspace **ws);
+
+/* Release a workspace (synchronises the device first). NULL is ignored. */
+void fbcc_workspace_destroy(fbcc_workspace *ws);
+
+/* Set tuning knobs of a workspace (copied). NULL restores the defaults. */
+fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg);
+
+/*
+ * Biconnected components of one graph (Algorithm 1), device-resident.
+ *   csr_offsets  device, n+1 entries, int64 if offsets_64 else int32
+ *   csr_adj      device, 2m int32 (format above)
+ *   edge_bcc     device out, 2m int32: BCC index per arc
+ *   bcc_head     device out, capacity >= max(n,1) int32: head of BCC k at [k]
+ *   is_ap        device out, n uint8
+ *   is_bridge    device out, 2m uint8
+ *   stats        host out (may be NULL); written by an async copy on `stream`,
+ *                valid after the stream is synchronised
+ * Returns FBCC_OK once every kernel is enqueued; kernel-side failures appear in
+ * stats->device_status. Calls on one workspace must not overlap on the device.
+ */
+fbcc_status fbcc_solve(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
+                       int64_t n, int64_t m,
+                       int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
+                       fbcc_stats *stats, fbcc_workspace *ws, void *stream);
+
+/*
+ * Same as fbcc_solve with every buffer in HOST memory (pinned memory makes the
+ * copies asynchronous-capable). The inputs are copied into workspace-owned device
+ * staging buffers, solved, and the outputs copied back; the call returns after the
+ * stream has been synchronised, so stats is valid on return.
+ */
+fbcc_status fbcc_solve_host(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
+                            int64_t n, int64_t m,
+                            int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
+                            fbcc_stats *stats, fbcc_workspace *ws, void *stream);
+
+/*
+ * Many independent graphs in one call (the graphs are solved together as one
+ * disjoint union; every kernel launch covers all of them).
+ *   vtx_base   device, n_graphs+1 int64: graph g owns global vertices
+ *              [vtx_base[g], vtx_base[g+1]); vtx_base[0] = 0, vtx_base[G] = n_total
+ *   arc_base   device, n_graphs+1 int64: graph g owns arcs [arc_base[g], arc_base[g+1])
+ *   local_off  device, n_total int32: for vertex i of graph g, the start of its list
+ *              relative to arc_base[g] is local_off[vtx_base[g] + i] (its end is the
+ *              next vertex's start, or arc_base[g+1] - arc_base[g] for the last vertex)
+ *   local_adj  device, nnz_total int32 neighbour ids local to their graph
+ *   outputs    at the same global positions as their inputs: edge_bcc / is_bridge per
+ *              arc (BCC indices numbered within each graph), is_ap per vertex, and
+ *              bcc_head[vtx_base[g] + k] = local head id of graph g's BCC k
+ *   stats      device out, n_graphs fbcc_stats (device_status is set in every entry)
+ *   host_vtx_base / host_arc_base  the same two arrays in host memory (sizes only)
+ */
+fbcc_status fbcc_solve_batch(int32_t n_graphs, const int64_t *vtx_base, const int64_t *arc_base,
+                             const int64_t *host_vtx_base, const int64_t *host_arc_base,
+                             const int32_t *local_off, const int32_t *local_adj,
+                             int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
+                             fbcc_stats *stats, fbcc_workspace *ws, void *stream);
+
+/* Device bytes fbcc_solve_batch needs beyond the inputs and outputs (for admission). */
+size_t fbcc_batch_workspace_bytes(int64_t n_total, int64_t nnz_total, int32_t n_graphs);
+
+/*
+ * Check the graph format on the device: ids in range, lists sorted strictly
+ * ascending, no self-loops, every arc has its reverse, offsets monotone with
+ * offsets[n] = 2m. Synchronous. Returns FBCC_OK, FBCC_E_INVALID or FBCC_E_NOT_SIMPLE.
+ */
+fbcc_status fbcc_validate(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
+                          int64_t n, int64_t m, fbcc_workspace *ws, void *stream);
+
+/* Static description of a status code. */
+const char *fbcc_status_string(fbcc_status s);
+
+/* Text of the last CUDA error this thread saw inside the library ("" if none). */
+const char *fbcc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBCC_H */

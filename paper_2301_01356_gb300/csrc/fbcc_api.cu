@@ -1,0 +1,540 @@
+// libfbcc C ABI: workspace management, the per-solve driver (optionally replayed
+// from a captured CUDA graph) and format validation.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "fbcc_internal.cuh"
+
+using namespace fbcc;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+fbcc_status cuda_fail(cudaError_t e, const char *where)
+{
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FBCC_E_OOM : FBCC_E_CUDA;
+}
+
+#define API_CK(x, where)                                   \
+    do {                                                   \
+        cudaError_t e_ = (x);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+constexpr int kMinStride = 4;
+
+struct GraphKey {
+    const void *off, *adj, *edge_bcc, *bcc_head, *is_ap, *is_bridge;
+    const void *vtx_base, *arc_base, *bstats;
+    int64_t n, m;
+    int offsets_64, G;
+    fbcc_config cfg;
+    bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+// Lays out every workspace array in one allocation (256-byte aligned pieces).
+struct Carver {
+    char *base;
+    size_t used = 0;
+    template <typename T>
+    T *take(int64_t count)
+    {
+        size_t at = (used + 255) & ~size_t(255);
+        used = at + size_t(count > 0 ? count : 1) * sizeof(T);
+        return base ? reinterpret_cast<T *>(base + at) : nullptr;
+    }
+};
+
+int64_t st_levels_for(int64_t tiles)
+{
+    int64_t l = 1;
+    while ((1ll << l) <= tiles) ++l;
+    return l;
+}
+
+size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
+{
+    if (N < 1) N = 1;
+    if (Z < 1) Z = 1;
+    Carver c{base};
+    d.n_max = N;
+    d.nnz_max = Z;
+    d.ruler_max = N + ceil_div(2 * N, kMinStride) + 2;
+    d.rmq_tiles_max = ceil_div(N, kRmqTile);
+    d.st_levels = st_levels_for(d.rmq_tiles_max);
+    const int64_t words = ceil_div(Z, 32) + 1;
+    int64_t scan_items = 2 * N + 1;
+    if (words + 1 > scan_items) scan_items = words + 1;
+    d.err = c.take<int>(4);
+    d.counters = c.take<long long>(16);
+    d.scan_status = c.take<uint64_t>(ceil_div(scan_items, kTile) + 2);
+    d.uf = c.take<int32_t>(N);
+    d.te_u = c.take<int32_t>(N);
+    d.te_v = c.take<int32_t>(N);
+    d.tile_v = c.take<int32_t>(ceil_div(Z, kTile) + 2);
+    d.tree_bits = c.take<uint32_t>(words);
+    d.tdeg = c.take<int32_t>(N + 1);
+    d.toff = c.take<int32_t>(N + 1);
+    d.tadj = c.take<int32_t>(2 * N);
+    d.twin = c.take<int32_t>(2 * N);
+    d.succ = c.take<int32_t>(2 * N);
+    d.is_head = c.take<uint8_t>(2 * N);
+    d.link = c.take<int2>(2 * N);
+    d.relem = c.take<int32_t>(d.ruler_max);
+    d.owner = c.take<int32_t>(2 * N);
+    d.offs = c.take<int32_t>(2 * N);
+    for (int i = 0; i < 2; ++i) {
+        d.rnext[i] = c.take<int32_t>(d.ruler_max);
+        d.rval[i] = c.take<int32_t>(d.ruler_max);
+    }
+    d.rlen = c.take<int32_t>(d.ruler_max);
+    d.csize = c.take<int32_t>(N + 1);
+    d.vbase = c.take<int32_t>(N + 1);
+    d.pos = c.take<int32_t>(2 * N);
+    d.tour = c.take<int32_t>(2 * N);
+    d.first = c.take<int32_t>(N);
+    d.last = c.take<int32_t>(N);
+    d.parent = c.take<int32_t>(N);
+    d.ord = c.take<int32_t>(N);
+    d.lastp = c.take<int32_t>(N);
+    d.porig = c.take<int32_t>(N);
+    d.w1 = c.take<int32_t>(N);
+    d.w2 = c.take<int32_t>(N);
+    d.pmin = c.take<int32_t>(N);
+    d.pmax = c.take<int32_t>(N);
+    d.tmin = c.take<int32_t>(d.st_levels * d.rmq_tiles_max);
+    d.tmax = c.take<int32_t>(d.st_levels * d.rmq_tiles_max);
+    d.vbits = c.take<uint8_t>(N);
+    d.head = c.take<int32_t>(N);
+    d.nh = c.take<int32_t>(N);
+    d.key = c.take<unsigned long long>(N);
+    d.scanv = c.take<uint8_t>(N);
+    d.key_bits = c.take<uint32_t>(words);
+    d.key_pre = c.take<int32_t>(words + 1);
+    d.rank = c.take<int32_t>(N);
+    d.fo = c.take<int2>(N);
+    d.stats = c.take<fbcc_stats>(1);
+    return c.used + 256;
+}
+
+}  // namespace
+
+struct fbcc_workspace {
+    Dev d;
+    void *slab = nullptr;
+    size_t bytes = 0;
+    fbcc_config cfg;
+    cudaStream_t cap = nullptr;        // private stream used for graph capture
+    cudaGraphExec_t exec = nullptr;
+    GraphKey key;
+    bool have_key = false;
+    // staging buffers of fbcc_solve_host (allocated on first use)
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    // global offsets/adjacency and per-graph bases of fbcc_solve_batch (first use)
+    void *bstage = nullptr;
+    size_t bstage_bytes = 0;
+};
+
+static fbcc_config default_config()
+{
+    fbcc_config c;
+    c.ruler_stride = 16;
+    c.cc_sample = 0;
+    c.grid_ctas = 0;
+    c.use_graph = 1;
+    return c;
+}
+
+static int device_grid(const fbcc_config &c)
+{
+    if (c.grid_ctas > 0) return c.grid_ctas;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (sms > 0 ? sms : 1) * 8;
+}
+
+extern "C" {
+
+size_t fbcc_workspace_bytes(int64_t n, int64_t nnz)
+{
+    Dev d;
+    return carve(d, nullptr, n, nnz);
+}
+
+fbcc_status fbcc_workspace_create(int64_t n_max, int64_t nnz_max, fbcc_workspace **ws)
+{
+    if (!ws || n_max < 0 || nnz_max < 0 || n_max >= (1ll << 30) || nnz_max >= (1ll << 40)) return FBCC_E_INVALID;
+    *ws = nullptr;
+    fbcc_workspace *w = new (std::nothrow) fbcc_workspace();
+    if (!w) return FBCC_E_OOM;
+    w->cfg = default_config();
+    w->bytes = carve(w->d, nullptr, n_max, nnz_max);
+    cudaError_t e = cudaMalloc(&w->slab, w->bytes);
+    if (e != cudaSuccess) {
+        delete w;
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    carve(w->d, static_cast<char *>(w->slab), n_max, nnz_max);
+    e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(w->slab);
+        delete w;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    *ws = w;
+    return FBCC_OK;
+}
+
+void fbcc_workspace_destroy(fbcc_workspace *ws)
+{
+    if (!ws) return;
+    cudaDeviceSynchronize();
+    if (ws->exec) cudaGraphExecDestroy(ws->exec);
+    if (ws->cap) cudaStreamDestroy(ws->cap);
+    cudaFree(ws->slab);
+    cudaFree(ws->stage);
+    cudaFree(ws->bstage);
+    delete ws;
+}
+
+fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
+{
+    if (!ws) return FBCC_E_INVALID;
+    fbcc_config c = default_config();
+    if (cfg) {
+        if (cfg->ruler_stride) {
+            if (cfg->ruler_stride < kMinStride || (cfg->ruler_stride & (cfg->ruler_stride - 1))) return FBCC_E_INVALID;
+            c.ruler_stride = cfg->ruler_stride;
+        }
+        if (cfg->cc_sample < 0 || cfg->grid_ctas < 0) return FBCC_E_INVALID;
+        c.cc_sample = cfg->cc_sample;
+        c.grid_ctas = cfg->grid_ctas;
+        if (cfg->use_graph) c.use_graph = cfg->use_graph;
+    }
+    ws->cfg = c;
+    return FBCC_OK;
+}
+
+const char *fbcc_status_string(fbcc_status s)
+{
+    switch (s) {
+    case FBCC_OK: return "ok";
+    case FBCC_E_INVALID: return "invalid argument";
+    case FBCC_E_NOT_SIMPLE: return "graph is not a simple symmetric sorted CSR";
+    case FBCC_E_OOM: return "out of device memory";
+    case FBCC_E_CUDA: return "CUDA runtime error";
+    case FBCC_E_ITER_LIMIT: return "a bounded device loop reached its iteration cap";
+    case FBCC_E_WORKSPACE: return "graph exceeds the workspace size";
+    }
+    return "unknown status";
+}
+
+const char *fbcc_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The solve itself
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_finish(const int *err, fbcc_stats *stats)
+{
+    stats->device_status = !*err ? FBCC_OK : (*err & kErrIndex) ? FBCC_E_INVALID : FBCC_E_ITER_LIMIT;
+}
+
+// Batch input: global int64 offsets and global neighbour ids from the packed
+// per-graph local CSR (one thread per vertex; its list is translated in place).
+__global__ void k_batch_globalize(int32_t G, const int64_t *__restrict__ vtx_base,
+                                  const int64_t *__restrict__ arc_base, const int32_t *__restrict__ loff,
+                                  const int32_t *__restrict__ ladj, int64_t n, int64_t *goff, int32_t *gadj)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = graph_of(vtx_base, G, v);
+        const int64_t vb = vtx_base[g], ab = arc_base[g];
+        const int64_t b = ab + loff[v];
+        const int64_t e = (v + 1 < vtx_base[g + 1]) ? ab + loff[v + 1] : arc_base[g + 1];
+        goff[v] = b;
+        for (int64_t a = b; a < e; ++a) gadj[a] = ladj[a] + (int32_t)vb;
+        if (v == n - 1) goff[n] = arc_base[G];
+    }
+}
+
+template <typename OffT>
+cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *adj, int64_t n, int64_t m,
+                          int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge, cudaStream_t s,
+                          const Batch &B = Batch())
+{
+    const Dev &d = ws->d;
+    const int64_t nnz = 2 * m;
+    Launch L{s, device_grid(ws->cfg)};
+    const bool vec = ((uintptr_t)adj & 15) == 0;
+    cudaError_t e;
+#define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+    CK(cudaMemsetAsync(d.err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(d.stats, 0, sizeof(fbcc_stats), s));
+    if (n > 0) {
+        CK(cudaMemsetAsync(d.tree_bits, 0, (ceil_div(nnz, 32) + 1) * sizeof(uint32_t), s));
+        CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, vec, L));
+        CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, L));
+        CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, L));
+        CK(launch_last_cc<OffT>(d, off, adj, n, nnz, vec, L));
+        CK(launch_outputs<OffT>(d, off, adj, n, nnz, vec, edge_bcc, bcc_head, is_ap, is_bridge, B, L));
+    }
+    k_finish<<<1, 1, 0, s>>>(d.err, d.stats);
+#undef CK
+    return cudaGetLastError();
+}
+
+fbcc_status check_args(const void *off, const int32_t *adj, int64_t n, int64_t m, const void *edge_bcc,
+                       const void *bcc_head, const void *is_ap, const void *is_bridge, fbcc_workspace *ws)
+{
+    if (!ws || n < 0 || m < 0) return FBCC_E_INVALID;
+    if (n >= (1ll << 30)) return FBCC_E_INVALID;
+    if (n > ws->d.n_max || 2 * m > ws->d.nnz_max) return FBCC_E_WORKSPACE;
+    if (m > 0 && n < 2) return FBCC_E_INVALID;
+    if (n > 0 && (!off || !is_ap || !bcc_head)) return FBCC_E_INVALID;
+    if (m > 0 && (!adj || !edge_bcc || !is_bridge)) return FBCC_E_INVALID;
+    return FBCC_OK;
+}
+
+fbcc_status solve_device(const void *off, int offsets_64, const int32_t *adj, int64_t n, int64_t m,
+                         int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge, fbcc_stats *stats,
+                         fbcc_workspace *ws, cudaStream_t s, const Batch &B = Batch(),
+                         const int32_t *loff = nullptr, const int32_t *ladj = nullptr)
+{
+    // A batch first translates its packed local CSR into global ids (in the graph too).
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+        if (B.G > 0 && n > 0) {
+            k_batch_globalize<<<device_grid(ws->cfg), kThreads, 0, q>>>(B.G, B.vtx_base, B.arc_base, loff, ladj, n,
+                                                                         (int64_t *)off, (int32_t *)adj);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return offsets_64
+            ? enqueue_solve<int64_t>(ws, (const int64_t *)off, adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, q, B)
+            : enqueue_solve<int32_t>(ws, (const int32_t *)off, adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, q, B);
+    };
+    if (ws->cfg.use_graph > 0) {
+        GraphKey k;
+        memset(&k, 0, sizeof(k));
+        k.off = off; k.adj = adj; k.edge_bcc = edge_bcc; k.bcc_head = bcc_head; k.is_ap = is_ap;
+        k.is_bridge = is_bridge; k.n = n; k.m = m; k.offsets_64 = offsets_64; k.cfg = ws->cfg;
+        k.vtx_base = B.vtx_base; k.arc_base = loff; k.bstats = B.stats; k.G = B.G;
+        if (B.G > 0) k.adj = ladj;
+        if (!ws->have_key || !(ws->key == k)) {
+            if (ws->exec) {
+                cudaGraphExecDestroy(ws->exec);
+                ws->exec = nullptr;
+            }
+            ws->have_key = false;
+            API_CK(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+            cudaError_t e = enqueue(ws->cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(ws->cap, &g);
+            if (e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(e, "enqueue (capture)");
+            }
+            API_CK(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ws->exec, g, 0);
+            cudaGraphDestroy(g);
+            API_CK(e, "cudaGraphInstantiate");
+            ws->key = k;
+            ws->have_key = true;
+        }
+        API_CK(cudaGraphLaunch(ws->exec, s), "cudaGraphLaunch");
+    } else {
+        API_CK(enqueue(s), "enqueue");
+    }
+    if (stats) API_CK(cudaMemcpyAsync(stats, ws->d.stats, sizeof(fbcc_stats), cudaMemcpyDeviceToHost, s), "stats copy");
+    return FBCC_OK;
+}
+
+size_t batch_stage_bytes(int64_t N, int64_t Z, int32_t G)
+{
+    Carver c{nullptr};
+    c.take<int64_t>(N + 1);
+    c.take<int32_t>(Z);
+    c.take<int64_t>((int64_t)G + 1);
+    return c.used + 256;
+}
+
+}  // namespace
+
+extern "C" {
+
+fbcc_status fbcc_solve(const void *csr_offsets, int offsets_64, const int32_t *csr_adj, int64_t n, int64_t m,
+                       int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge, fbcc_stats *stats,
+                       fbcc_workspace *ws, void *stream)
+{
+    fbcc_status st = check_args(csr_offsets, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, ws);
+    if (st != FBCC_OK) return st;
+    return solve_device(csr_offsets, offsets_64, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, stats, ws,
+                        (cudaStream_t)stream);
+}
+
+fbcc_status fbcc_solve_host(const void *csr_offsets, int offsets_64, const int32_t *csr_adj, int64_t n, int64_t m,
+                            int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
+                            fbcc_stats *stats, fbcc_workspace *ws, void *stream)
+{
+    fbcc_status st = check_args(csr_offsets, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, ws);
+    if (st != FBCC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = ws->d.n_max, Z = ws->d.nnz_max;
+    if (!ws->stage) {
+        Dev tmp;
+        (void)tmp;
+        ws->stage_bytes = size_t(N + 1) * 8 + size_t(Z) * 4 + size_t(Z) * 4 + size_t(N) * 4 + size_t(N) + size_t(Z) + 5 * 256;
+        API_CK(cudaMalloc(&ws->stage, ws->stage_bytes), "cudaMalloc(staging)");
+    }
+    Carver c{static_cast<char *>(ws->stage)};
+    void *d_off = c.take<int64_t>(N + 1);
+    int32_t *d_adj = c.take<int32_t>(Z);
+    int32_t *d_eb = c.take<int32_t>(Z);
+    int32_t *d_bh = c.take<int32_t>(N);
+    uint8_t *d_ap = c.take<uint8_t>(N);
+    uint8_t *d_br = c.take<uint8_t>(Z);
+    const int64_t nnz = 2 * m;
+    const size_t ob = size_t(n + 1) * (offsets_64 ? 8 : 4);
+    if (n > 0) API_CK(cudaMemcpyAsync(d_off, csr_offsets, ob, cudaMemcpyHostToDevice, s), "H2D offsets");
+    if (nnz > 0) API_CK(cudaMemcpyAsync(d_adj, csr_adj, nnz * 4, cudaMemcpyHostToDevice, s), "H2D adj");
+    fbcc_stats hs;
+    st = solve_device(d_off, offsets_64, d_adj, n, m, d_eb, d_bh, d_ap, d_br, &hs, ws, s);
+    if (st != FBCC_OK) return st;
+    if (nnz > 0) {
+        API_CK(cudaMemcpyAsync(edge_bcc, d_eb, nnz * 4, cudaMemcpyDeviceToHost, s), "D2H edge_bcc");
+        API_CK(cudaMemcpyAsync(is_bridge, d_br, nnz, cudaMemcpyDeviceToHost, s), "D2H is_bridge");
+    }
+    if (n > 0) API_CK(cudaMemcpyAsync(is_ap, d_ap, n, cudaMemcpyDeviceToHost, s), "D2H is_ap");
+    API_CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (hs.n_bcc > 0)
+        API_CK(cudaMemcpy(bcc_head, d_bh, hs.n_bcc * 4, cudaMemcpyDeviceToHost), "D2H bcc_head");
+    if (stats) *stats = hs;
+    return FBCC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Validation (warp per vertex)
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename OffT>
+__global__ void k_validate(const OffT *__restrict__ off, const int32_t *__restrict__ adj, int64_t n, int64_t nnz,
+                           int *bad)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
+        const int64_t b = off[v], e = off[v + 1];
+        if (lane == 0 && (e < b || b < 0 || e > nnz)) atomicOr(bad, 1);
+        if (e < b || b < 0 || e > nnz) continue;
+        for (int64_t a = b + lane; a < e; a += 32) {
+            const int32_t w = adj[a];
+            if (w < 0 || w >= n) { atomicOr(bad, 1); continue; }
+            if (w == v || (a > b && adj[a - 1] >= w)) { atomicOr(bad, 2); continue; }
+            int64_t lo = off[w], hi = off[w + 1];
+            if (lo < 0 || hi > nnz || hi < lo) { atomicOr(bad, 1); continue; }
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (adj[mid] < v) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= off[w + 1] || adj[lo] != v) atomicOr(bad, 2);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" fbcc_status fbcc_validate(const void *csr_offsets, int offsets_64, const int32_t *csr_adj, int64_t n,
+                                     int64_t m, fbcc_workspace *ws, void *stream)
+{
+    if (!ws || n < 0 || m < 0 || (n > 0 && !csr_offsets) || (m > 0 && !csr_adj)) return FBCC_E_INVALID;
+    if (n > ws->d.n_max || 2 * m > ws->d.nnz_max) return FBCC_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t ends[2] = {0, 0};
+    if (n == 0) return m == 0 ? FBCC_OK : FBCC_E_INVALID;
+    if (offsets_64) {
+        API_CK(cudaMemcpyAsync(&ends[0], csr_offsets, 8, cudaMemcpyDeviceToHost, s), "D2H");
+        API_CK(cudaMemcpyAsync(&ends[1], (const int64_t *)csr_offsets + n, 8, cudaMemcpyDeviceToHost, s), "D2H");
+    } else {
+        int32_t e32[2] = {0, 0};
+        API_CK(cudaMemcpyAsync(&e32[0], csr_offsets, 4, cudaMemcpyDeviceToHost, s), "D2H");
+        API_CK(cudaMemcpyAsync(&e32[1], (const int32_t *)csr_offsets + n, 4, cudaMemcpyDeviceToHost, s), "D2H");
+        API_CK(cudaStreamSynchronize(s), "sync");
+        ends[0] = e32[0];
+        ends[1] = e32[1];
+    }
+    API_CK(cudaStreamSynchronize(s), "sync");
+    if (ends[0] != 0 || ends[1] != 2 * m) return FBCC_E_INVALID;
+    API_CK(cudaMemsetAsync(ws->d.err, 0, sizeof(int), s), "memset");
+    const int grid = device_grid(ws->cfg);
+    if (offsets_64)
+        k_validate<int64_t><<<grid, kThreads, 0, s>>>((const int64_t *)csr_offsets, csr_adj, n, 2 * m, ws->d.err);
+    else
+        k_validate<int32_t><<<grid, kThreads, 0, s>>>((const int32_t *)csr_offsets, csr_adj, n, 2 * m, ws->d.err);
+    API_CK(cudaGetLastError(), "k_validate");
+    int bad = 0;
+    API_CK(cudaMemcpyAsync(&bad, ws->d.err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
+    API_CK(cudaStreamSynchronize(s), "sync");
+    if (bad & 1) return FBCC_E_INVALID;
+    if (bad & 2) return FBCC_E_NOT_SIMPLE;
+    return FBCC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solve
+// ---------------------------------------------------------------------------
+extern "C" size_t fbcc_batch_workspace_bytes(int64_t n_total, int64_t nnz_total, int32_t n_graphs)
+{
+    return fbcc_workspace_bytes(n_total, nnz_total) + batch_stage_bytes(n_total, nnz_total, n_graphs);
+}
+
+extern "C" fbcc_status fbcc_solve_batch(int32_t n_graphs, const int64_t *vtx_base, const int64_t *arc_base,
+                                        const int64_t *host_vtx_base, const int64_t *host_arc_base,
+                                        const int32_t *local_off, const int32_t *local_adj, int32_t *edge_bcc,
+                                        int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge, fbcc_stats *stats,
+                                        fbcc_workspace *ws, void *stream)
+{
+    if (!ws || n_graphs < 1 || !vtx_base || !arc_base || !host_vtx_base || !host_arc_base || !stats)
+        return FBCC_E_INVALID;
+    const int64_t n = host_vtx_base[n_graphs], nnz = host_arc_base[n_graphs];
+    if (host_vtx_base[0] != 0 || host_arc_base[0] != 0 || nnz % 2) return FBCC_E_INVALID;
+    for (int32_t g = 0; g < n_graphs; ++g)
+        if (host_vtx_base[g + 1] < host_vtx_base[g] || host_arc_base[g + 1] < host_arc_base[g] ||
+            (host_arc_base[g + 1] - host_arc_base[g]) % 2)
+            return FBCC_E_INVALID;
+    fbcc_status st = check_args(host_vtx_base, local_adj, n, nnz / 2, edge_bcc, bcc_head, is_ap, is_bridge, ws);
+    if (st != FBCC_OK) return st;
+    if (n > 0 && !local_off) return FBCC_E_INVALID;
+    const size_t need = batch_stage_bytes(ws->d.n_max, ws->d.nnz_max, n_graphs);
+    if (ws->bstage_bytes < need) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaFree(ws->bstage);
+        ws->bstage = nullptr;
+        ws->bstage_bytes = 0;
+        ws->have_key = false;
+        API_CK(cudaMalloc(&ws->bstage, need), "cudaMalloc(batch staging)");
+        ws->bstage_bytes = need;
+    }
+    Carver c{static_cast<char *>(ws->bstage)};
+    int64_t *goff = c.take<int64_t>(ws->d.n_max + 1);
+    int32_t *gadj = c.take<int32_t>(ws->d.nnz_max);
+    Batch B;
+    B.G = n_graphs;
+    B.vtx_base = vtx_base;
+    B.arc_base = arc_base;
+    B.bcc_base = c.take<int64_t>((int64_t)n_graphs + 1);
+    B.stats = stats;
+    return solve_device(goff, 1, gadj, n, nnz / 2, edge_bcc, bcc_head, is_ap, is_bridge, nullptr, ws,
+                        (cudaStream_t)stream, B, local_off, local_adj);
+}

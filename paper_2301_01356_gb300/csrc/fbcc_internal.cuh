@@ -1,0 +1,392 @@
+// Internal declarations of libfbcc: workspace layout, device building blocks
+// (union-find, arc tiles, block scan with decoupled look-back) and the host
+// launchers each phase's translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fbcc.h"
+
+namespace fbcc {
+
+// ---------------------------------------------------------------------------
+// Launch geometry
+// ---------------------------------------------------------------------------
+constexpr int kThreads = 256;                       // threads per CTA everywhere
+constexpr int kItems = 8;                           // consecutive items per thread
+constexpr int kTile = kThreads * kItems;            // 2048 items (arcs, positions) per CTA tile
+constexpr int kOffWin = kTile + 256;                // offsets cached in shared memory per arc tile
+constexpr int kRmqTile = 1024;                      // positions per low/high tile
+constexpr int kChunk = 32;                          // positions per in-tile RMQ chunk
+
+// Device error bits (workspace error word); reported as FBCC_E_ITER_LIMIT.
+constexpr int kErrUnite = 1;      // union-find retry cap
+constexpr int kErrChase = 2;      // list-ranking chase longer than the list
+constexpr int kErrLookback = 4;   // scan look-back wait cap
+constexpr int kErrIndex = 8;      // a computed index fell outside its array (inconsistent input)
+constexpr int kUniteCap = 1 << 26;
+constexpr int kLookbackCap = 1 << 22;
+
+// ---------------------------------------------------------------------------
+// Workspace: every O(n) / O(nnz) array of one solve (device pointers).
+// ---------------------------------------------------------------------------
+struct Dev {
+    // sizes the workspace was created for
+    int64_t n_max, nnz_max;
+    int64_t ruler_max;        // capacity of the ruler arrays
+    int64_t rmq_tiles_max, st_levels;
+
+    int *err;                 // device error word
+    long long *counters;      // [0] scan tile ticket, [1] ruler count, [2..] stats accumulators
+    uint64_t *scan_status;    // per-tile look-back status (largest scan: 2n positions)
+
+    // First-CC
+    int32_t *uf;              // union-find parent (First-CC, then Last-CC)
+    int32_t *te_u, *te_v;     // tree edge recorded at the vertex it hooked (-1: none)
+    int32_t *tile_v;          // source vertex of the first arc of every arc tile (+1 sentinel)
+    uint32_t *tree_bits;      // one bit per arc: tree arc
+    // Rooting
+    int32_t *tdeg;            // tree degree, then fill cursor
+    int32_t *toff;            // tree CSR offsets (n+1)
+    int32_t *tadj, *twin;     // tree CSR targets and reverse-arc index (2n)
+    int32_t *succ;            // Euler-circuit successor (2n), -1 at a tour's end
+    uint8_t *is_head;         // first arc of a tour (2n)
+    int2 *link;               // {succ, ruler id or -1} per tree arc
+    int32_t *relem;           // arc of ruler r
+    int32_t *owner, *offs;    // ruler owning each arc and the arc's distance from it
+    int32_t *rnext[2], *rval[2];  // ruler list: next ruler and suffix weight (double buffered)
+    int32_t *rlen;            // ruler segment length
+    int32_t *csize;           // component size at its root, 0 elsewhere
+    int32_t *vbase;           // first preorder number of the component at its root
+    int32_t *pos;             // tour position of every tree arc
+    int32_t *tour;            // tree arc at every tour position (-1/-2: padding)
+    // Tagging (first/last/parent indexed by vertex; the rest by preorder number)
+    int32_t *first, *last, *parent;
+    int32_t *ord;             // vertex at preorder number p
+    int32_t *lastp;           // last[] at preorder number p
+    int32_t *porig;           // parent vertex of the vertex at preorder number p (-1 root)
+    int32_t *w1, *w2;         // w1/w2 at preorder number p
+    int32_t *pmin, *pmax;     // in-tile prefix min/max of w1/w2
+    int32_t *tmin, *tmax;     // sparse tables over RMQ tiles: st_levels x rmq_tiles_max
+    uint8_t *vbits;           // per vertex: bit0 = tree edge to parent is a bridge
+    // Last-CC and outputs
+    int32_t *head;            // head of label L at [L]
+    int32_t *nh;              // number of labels a vertex heads
+    unsigned long long *key;  // smallest arc id (src < dst) of label L at [L]
+    uint8_t *scanv;           // vertex whose list must be scanned for keys
+    uint32_t *key_bits;       // one bit per arc: arc is the key of its BCC
+    int32_t *key_pre;         // exclusive popcount prefix per 32-bit word of key_bits
+    int32_t *rank;            // canonical BCC index of label L at [L]
+    int2 *fo;                 // {first, output word} per vertex
+    fbcc_stats *stats;        // device-side counts
+};
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t ld_cg(const int32_t *p) { return __ldcg(p); }
+
+// True when 0 <= i < n; otherwise raises kErrIndex (the access is then skipped).
+__device__ __forceinline__ bool in_range(int64_t i, int64_t n, int *err)
+{
+    if ((uint64_t)i < (uint64_t)n) return true;
+    atomicOr(err, kErrIndex);
+    return false;
+}
+
+__device__ __forceinline__ bool test_bit(const uint32_t *bits, int64_t i)
+{
+    return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
+}
+
+__device__ __forceinline__ void set_bit(uint32_t *bits, int64_t i)
+{
+    atomicOr(bits + (i >> 5), 1u << (i & 31));
+}
+
+// Union-find root with path halving. Parents only ever point to smaller ids
+// (larger roots are hooked under smaller ones), so the walk strictly decreases
+// and the root of a set is its smallest member. Reads bypass L1 (other SMs write).
+__device__ __forceinline__ int32_t uf_find(int32_t *uf, int32_t v)
+{
+    while (true) {
+        int32_t p = ld_cg(uf + v);
+        if (p == v) return v;
+        int32_t gp = ld_cg(uf + p);
+        if (gp == p) return p;
+        uf[v] = gp;  // halving: gp is an ancestor of v, so the store is always safe
+        v = gp;
+    }
+}
+
+// Union of the sets of u and v by CAS-hooking the larger root under the smaller.
+// Returns the root that got hooked, or -1 when u and v were already joined.
+__device__ __forceinline__ int32_t uf_unite(int32_t *uf, int32_t u, int32_t v, int *err)
+{
+    int32_t ru = uf_find(uf, u), rv = uf_find(uf, v);
+    for (int it = 0; it < kUniteCap; ++it) {
+        if (ru == rv) return -1;
+        int32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
+        int32_t old = atomicCAS(uf + hi, hi, lo);
+        if (old == hi) return hi;
+        ru = uf_find(uf, old);  // hi was hooked meanwhile; continue from its new parent
+        rv = uf_find(uf, lo);
+    }
+    atomicOr(err, kErrUnite);
+    return -1;
+}
+
+__device__ __forceinline__ int32_t warp_sum_i32(int32_t x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Block-wide sum of one value per thread, result valid in every thread.
+__device__ __forceinline__ long long block_sum(long long x)
+{
+    __shared__ long long part[kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = x;
+    __syncthreads();
+    long long t = 0;
+#pragma unroll
+    for (int i = 0; i < kThreads / 32; ++i) t += part[i];
+    return t;
+}
+
+// Add a per-thread count into a device counter with one atomic per CTA.
+__device__ __forceinline__ void block_count(long long *dst, long long x)
+{
+    long long t = block_sum(x);
+    if (threadIdx.x == 0 && t) atomicAdd((unsigned long long *)dst, (unsigned long long)t);
+}
+
+// ---------------------------------------------------------------------------
+// Single-pass exclusive scan with decoupled look-back (Merrill & Garland, 2016).
+// A CTA takes the next tile ticket, scans its kTile items in registers, publishes
+// its aggregate, waits (bounded) for its predecessors' prefix and publishes its
+// inclusive prefix. Status word: bits 62..63 flag (1 aggregate, 2 prefix),
+// bits 0..61 value.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62, kValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ int64_t scan_ticket(long long *ticket)
+{
+    __shared__ int64_t t;
+    __syncthreads();
+    if (threadIdx.x == 0) t = (int64_t)atomicAdd((unsigned long long *)ticket, 1ull);
+    __syncthreads();
+    return t;
+}
+
+// In: v[] the thread's kItems values (items tile*kTile + threadIdx.x*kItems + j).
+// Out: v[] their global exclusive prefixes; returns the tile's inclusive total end.
+__device__ __forceinline__ long long scan_tile_exclusive(long long (&v)[kItems], int64_t tile,
+                                                         uint64_t *status, int *err)
+{
+    __shared__ long long warp_tot[kThreads / 32];
+    __shared__ long long tile_excl;
+    long long run = 0;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        long long x = v[j];
+        v[j] = run;
+        run += x;
+    }
+    // exclusive scan of the per-thread totals across the CTA
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    long long wexcl = 0, agg = 0;
+#pragma unroll
+    for (int i = 0; i < kThreads / 32; ++i) {
+        if (i < wid) wexcl += warp_tot[i];
+        agg += warp_tot[i];
+    }
+    long long texcl = wexcl + inc - run;
+    if (threadIdx.x == 0) {
+        long long excl = 0;
+        if (tile == 0) {
+            atomicExch((unsigned long long *)(status + tile), (unsigned long long)(kFlagPre | (uint64_t)agg));
+        } else {
+            atomicExch((unsigned long long *)(status + tile), (unsigned long long)(kFlagAgg | (uint64_t)agg));
+            int64_t j = tile - 1;
+            int spins = 0;
+            while (j >= 0) {
+                uint64_t s = *(volatile uint64_t *)(status + j);
+                uint64_t f = s & ~kValMask;
+                if (f == 0) {
+                    if (++spins > kLookbackCap) { atomicOr(err, kErrLookback); break; }
+                    continue;
+                }
+                excl += (long long)(s & kValMask);
+                if (f == kFlagPre) break;
+                --j;
+            }
+            atomicExch((unsigned long long *)(status + tile),
+                       (unsigned long long)(kFlagPre | (uint64_t)(excl + agg)));
+        }
+        tile_excl = excl;
+    }
+    __syncthreads();
+    long long base = tile_excl + texcl;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) v[j] += base;
+    return tile_excl + agg;
+}
+
+// ---------------------------------------------------------------------------
+// Arc tiles: CTA tile t covers arcs [t*kTile, (t+1)*kTile); thread i covers the
+// kItems consecutive arcs starting at t*kTile + i*kItems. The source vertex of
+// every arc comes from the tile's window of offsets, staged in shared memory.
+// tile_v[t] is the source of the tile's first arc, tile_v[ntiles] that of the
+// graph's last arc.
+// ---------------------------------------------------------------------------
+template <typename OffT>
+struct ArcTile {
+    int64_t a0;        // first arc of this thread
+    int cnt;           // arcs of this thread (0..kItems)
+    int32_t src[kItems];
+};
+
+template <typename OffT>
+__device__ __forceinline__ void arc_tile_sources(const OffT *__restrict__ off, int64_t nnz,
+                                                 const int32_t *__restrict__ tile_v, int64_t t,
+                                                 OffT *win, ArcTile<OffT> &at)
+{
+    const int32_t vlo = tile_v[t], vhi = tile_v[t + 1];
+    const int64_t wn = (int64_t)vhi - vlo + 2;  // off[vlo .. vhi+1]
+    const bool sm = wn <= kOffWin;
+    __syncthreads();
+    if (sm)
+        for (int64_t i = threadIdx.x; i < wn; i += kThreads) win[i] = off[vlo + i];
+    __syncthreads();
+    at.a0 = t * (int64_t)kTile + (int64_t)threadIdx.x * kItems;
+    at.cnt = 0;
+    if (at.a0 >= nnz) return;
+    at.cnt = (int)((nnz - at.a0) < kItems ? (nnz - at.a0) : kItems);
+    // largest i in [0, wn-2] with off[vlo+i] <= a0
+    int64_t lo = 0, hi = wn - 2;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        int64_t x = sm ? (int64_t)win[mid] : (int64_t)off[vlo + mid];
+        if (x <= at.a0) lo = mid; else hi = mid - 1;
+    }
+    int64_t end = sm ? (int64_t)win[lo + 1] : (int64_t)off[vlo + lo + 1];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        int64_t a = at.a0 + j;
+        if (j < at.cnt) {
+            while (end <= a) {
+                ++lo;
+                end = sm ? (int64_t)win[lo + 1] : (int64_t)off[vlo + lo + 1];
+            }
+        }
+        at.src[j] = vlo + (int32_t)lo;
+    }
+}
+
+// The kItems neighbour ids of the thread's arcs (vector loads when aligned).
+__device__ __forceinline__ void arc_tile_targets(const int32_t *__restrict__ adj, int64_t a0, int cnt,
+                                                 bool vec, int32_t (&d)[kItems])
+{
+    if (vec && cnt == kItems) {
+        int4 x = __ldcs(reinterpret_cast<const int4 *>(adj + a0));
+        int4 y = __ldcs(reinterpret_cast<const int4 *>(adj + a0) + 1);
+        d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+        d[4] = y.x; d[5] = y.y; d[6] = y.z; d[7] = y.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) d[j] = j < cnt ? __ldcs(adj + a0 + j) : 0;
+    }
+}
+
+// The tree bits of the thread's kItems arcs (a0 is a multiple of kItems = 8, so
+// they sit in one 32-bit word).
+__device__ __forceinline__ uint32_t arc_tile_treebits(const uint32_t *__restrict__ bits, int64_t a0)
+{
+    return (__ldg(bits + (a0 >> 5)) >> (a0 & 31)) & 0xffu;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solves: many graphs packed as one disjoint union with global ids.
+// ---------------------------------------------------------------------------
+struct Batch {
+    int32_t G = 0;                       // number of graphs; 0 for a plain solve
+    const int64_t *vtx_base = nullptr;   // device, G+1
+    const int64_t *arc_base = nullptr;   // device, G+1
+    int64_t *bcc_base = nullptr;         // device, G+1: BCCs of the graphs before g
+    fbcc_stats *stats = nullptr;         // device, G
+};
+
+// Graph owning global vertex v: the largest g with vtx_base[g] <= v.
+__device__ __forceinline__ int32_t graph_of(const int64_t *__restrict__ vtx_base, int32_t G, int64_t v)
+{
+    int32_t lo = 0, hi = G - 1;
+    while (lo < hi) {
+        int32_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(vtx_base + mid) <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct Launch {
+    cudaStream_t s;
+    int grid;        // persistent grid size (CTAs)
+};
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline int grid_for(const Launch &L, int64_t items_per_cta_units)
+{
+    int64_t g = items_per_cta_units < 1 ? 1 : items_per_cta_units;
+    return (int)(g < L.grid ? g : L.grid);
+}
+
+// Phase launchers (each returns the first launch error or cudaSuccess).
+template <typename OffT>
+cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                            int cc_sample, bool vec, const Launch &L);
+template <typename OffT>
+cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                           int ruler_stride, const Launch &L);
+template <typename OffT>
+cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                           bool vec, const Launch &L);
+template <typename OffT>
+cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                           bool vec, const Launch &L);
+template <typename OffT>
+cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                           bool vec, int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap,
+                           uint8_t *is_bridge, const Batch &B, const Launch &L);
+template <typename OffT>
+cudaError_t launch_validate(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                            const Launch &L);
+
+// Generic exclusive scan over int32 counts: out[i] = sum of in[0..i), out[len] = total
+// (out has len+1 entries; in may alias out when in_place).
+cudaError_t launch_scan_i32(const Dev &d, const int32_t *in, int32_t *out, int64_t len, const Launch &L);
+// out[i] = set bits in words[0..i), i in [0, len].
+cudaError_t launch_scan_popc(const Dev &d, const uint32_t *words, int32_t *out, int64_t len, const Launch &L);
+
+// Number of ruler-list pointer-jumping rounds for up to r rulers.
+inline int jump_rounds(int64_t r)
+{
+    int k = 0;
+    while ((1ll << k) < r + 1) ++k;
+    return k + 1;
+}
+
+}  // namespace fbcc

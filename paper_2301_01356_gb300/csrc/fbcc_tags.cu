@@ -1,0 +1,289 @@
+// Tagging (Algorithm 1, step 3; section 3.2 for w1/w2/low/high, section 5
+// "Computing Tags"):
+//   w1[u] = min({first[u]} U {first[u'] : u-u' a non-tree edge}), w2 the max;
+//   low[v] = min of w1 over T_v, high[v] = max of w2 over T_v.
+// With preorder numbers, T_v is the position range [first[v], last[v]], so w1/w2
+// are stored by preorder number and low/high are range-min/max queries over that
+// range (the paper uses a sparse table; here: 1024-position tiles, in-tile
+// prefix/suffix and 32-position chunks in shared memory, and a sparse table only
+// over the tile extrema, which keeps the extra space O(n)).
+//
+// The query kernel then tests the tree edge p(v)-v (Algorithm 1, Fence):
+//   fence iff first[p(v)] <= low[v] and last[p(v)] >= high[v];
+// a plain (non-fence) tree edge is an edge of the skeleton G' and is united in the
+// Last-CC union-find right there. The edge is a bridge iff nothing leaves T_v:
+// low[v] == first[v] and high[v] <= last[v].
+#include "fbcc_internal.cuh"
+
+namespace fbcc {
+
+#define GRID_STRIDE(i, n) \
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
+
+// w1/w2 over the non-tree arcs; one atomic per run of equal sources per thread.
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
+                                                  int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
+                                                  const uint32_t *__restrict__ tree_bits,
+                                                  const int32_t *__restrict__ first, int32_t *w1, int32_t *w2,
+                                                  int64_t n, int *err, bool vec)
+{
+    __shared__ OffT win[kOffWin];
+    ArcTile<OffT> at;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        arc_tile_sources(off, nnz, tile_v, t, win, at);
+        if (!at.cnt) continue;
+        uint32_t tb = arc_tile_treebits(tree_bits, at.a0);
+        int32_t d[kItems];
+        arc_tile_targets(adj, at.a0, at.cnt, vec, d);
+        int32_t cur = -1, mn = INT32_MAX, mx = INT32_MIN;
+#pragma unroll
+        for (int j = 0; j <= kItems; ++j) {
+            bool live = j < at.cnt;
+            if (!live || at.src[j] != cur) {
+                if (cur >= 0 && mn != INT32_MAX) {
+                    int32_t fc = __ldg(first + cur);
+                    if (in_range(fc, n, err)) {
+                        if (mn < fc) atomicMin(w1 + fc, mn);
+                        if (mx > fc) atomicMax(w2 + fc, mx);
+                    }
+                }
+                if (!live) break;
+                cur = at.src[j];
+                mn = INT32_MAX;
+                mx = INT32_MIN;
+            }
+            if ((tb >> j) & 1u) continue;
+            int32_t f = __ldg(first + d[j]);
+            mn = f < mn ? f : mn;
+            mx = f > mx ? f : mx;
+        }
+    }
+}
+
+// Per RMQ tile: inclusive prefix min of w1 and max of w2 from the tile start, and
+// the tile's min/max (level 0 of the tile sparse table).
+__global__ void __launch_bounds__(kThreads) k_rmq_prefix(int64_t n, const int32_t *__restrict__ w1,
+                                                         const int32_t *__restrict__ w2, int32_t *pmin, int32_t *pmax,
+                                                         int32_t *tmin, int32_t *tmax)
+{
+    constexpr int kPer = kRmqTile / kThreads;  // 4 positions per thread
+    __shared__ int32_t smin[kThreads / 32], smax[kThreads / 32];
+    const int64_t ntiles = (n + kRmqTile - 1) / kRmqTile;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * kRmqTile + (int64_t)threadIdx.x * kPer;
+        int32_t a[kPer], b[kPer];
+        int32_t rmn = INT32_MAX, rmx = INT32_MIN;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            int64_t p = p0 + j;
+            int32_t x = p < n ? w1[p] : INT32_MAX, y = p < n ? w2[p] : INT32_MIN;
+            rmn = x < rmn ? x : rmn;
+            rmx = y > rmx ? y : rmx;
+            a[j] = rmn;
+            b[j] = rmx;
+        }
+        // exclusive scan of the thread extrema across the CTA
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int32_t imn = rmn, imx = rmx;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y1 = __shfl_up_sync(0xffffffffu, imn, o), y2 = __shfl_up_sync(0xffffffffu, imx, o);
+            if (lane >= o) {
+                imn = y1 < imn ? y1 : imn;
+                imx = y2 > imx ? y2 : imx;
+            }
+        }
+        __syncthreads();
+        if (lane == 31) { smin[wid] = imn; smax[wid] = imx; }
+        __syncthreads();
+        int32_t emn = INT32_MAX, emx = INT32_MIN, tmn = INT32_MAX, tmx = INT32_MIN;
+#pragma unroll
+        for (int i = 0; i < kThreads / 32; ++i) {
+            if (i < wid) { emn = smin[i] < emn ? smin[i] : emn; emx = smax[i] > emx ? smax[i] : emx; }
+            tmn = smin[i] < tmn ? smin[i] : tmn;
+            tmx = smax[i] > tmx ? smax[i] : tmx;
+        }
+        int32_t xmn = __shfl_up_sync(0xffffffffu, imn, 1), xmx = __shfl_up_sync(0xffffffffu, imx, 1);
+        if (lane > 0) {
+            emn = xmn < emn ? xmn : emn;
+            emx = xmx > emx ? xmx : emx;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            int64_t p = p0 + j;
+            if (p < n) {
+                pmin[p] = a[j] < emn ? a[j] : emn;
+                pmax[p] = b[j] > emx ? b[j] : emx;
+            }
+        }
+        if (threadIdx.x == 0) {
+            tmin[t] = tmn;
+            tmax[t] = tmx;
+        }
+    }
+}
+
+// Sparse-table level j over the tile extrema: level j covers 2^j tiles.
+__global__ void __launch_bounds__(kThreads) k_rmq_level(int64_t ntiles, int j, int64_t stride,
+                                                        int32_t *tmin, int32_t *tmax)
+{
+    const int32_t *pm = tmin + (int64_t)(j - 1) * stride, *pM = tmax + (int64_t)(j - 1) * stride;
+    int32_t *qm = tmin + (int64_t)j * stride, *qM = tmax + (int64_t)j * stride;
+    const int64_t h = 1ll << (j - 1);
+    GRID_STRIDE(t, ntiles)
+    {
+        int32_t a = pm[t], b = pM[t];
+        if (t + h < ntiles) {
+            a = pm[t + h] < a ? pm[t + h] : a;
+            b = pM[t + h] > b ? pM[t + h] : b;
+        }
+        qm[t] = a;
+        qM[t] = b;
+    }
+}
+
+// low/high for every position, the fence and bridge tests, and the Last-CC union
+// of every plain tree edge.
+__global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t *__restrict__ w1,
+                                                        const int32_t *__restrict__ w2, const int32_t *__restrict__ pmin,
+                                                        const int32_t *__restrict__ pmax, const int32_t *__restrict__ tmin,
+                                                        const int32_t *__restrict__ tmax, int64_t st_stride,
+                                                        const int32_t *__restrict__ ord, const int32_t *__restrict__ lastp,
+                                                        const int32_t *__restrict__ porig,
+                                                        const int32_t *__restrict__ first,
+                                                        const int32_t *__restrict__ last, uint8_t *vbits, int32_t *uf,
+                                                        int *err)
+{
+    constexpr int kPer = kRmqTile / kThreads;
+    constexpr int kNChunk = kRmqTile / kChunk;
+    __shared__ int32_t s1[kRmqTile], s2[kRmqTile];          // w1, w2
+    __shared__ int32_t pre1[kRmqTile], pre2[kRmqTile];      // prefix within the chunk
+    __shared__ int32_t suf1[kRmqTile], suf2[kRmqTile];      // suffix within the chunk
+    __shared__ int32_t c1[kNChunk], c2[kNChunk];            // chunk extrema
+    __shared__ int32_t cs1[kNChunk], cs2[kNChunk];          // suffix over chunks (tile suffix helper)
+    const int64_t ntiles = (n + kRmqTile - 1) / kRmqTile;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t base = t * kRmqTile;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kRmqTile; i += kThreads) {
+            int64_t p = base + i;
+            s1[i] = p < n ? w1[p] : INT32_MAX;
+            s2[i] = p < n ? w2[p] : INT32_MIN;
+        }
+        __syncthreads();
+        // chunk prefix/suffix: warp w handles chunks w, w+8, ... one position per lane
+        for (int c = wid; c < kNChunk; c += kThreads / 32) {
+            int i = c * kChunk + lane;
+            int32_t x = s1[i], y = s2[i], px = x, py = y, sx = x, sy = y;
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t a = __shfl_up_sync(0xffffffffu, px, o), b = __shfl_up_sync(0xffffffffu, py, o);
+                int32_t a2 = __shfl_down_sync(0xffffffffu, sx, o), b2 = __shfl_down_sync(0xffffffffu, sy, o);
+                if (lane >= o) { px = a < px ? a : px; py = b > py ? b : py; }
+                if (lane + o < 32) { sx = a2 < sx ? a2 : sx; sy = b2 > sy ? b2 : sy; }
+            }
+            pre1[i] = px; pre2[i] = py; suf1[i] = sx; suf2[i] = sy;
+            if (lane == 31) { c1[c] = px; c2[c] = py; }
+        }
+        __syncthreads();
+        if (wid == 0) {
+            int32_t x = c1[lane], y = c2[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t a = __shfl_down_sync(0xffffffffu, x, o), b = __shfl_down_sync(0xffffffffu, y, o);
+                if (lane + o < 32) { x = a < x ? a : x; y = b > y ? b : y; }
+            }
+            cs1[lane] = x;
+            cs2[lane] = y;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * kThreads;
+            const int64_t p = base + i;
+            if (p >= n) continue;
+            int32_t e = lastp[p];
+            if (e < p || e >= n) { atomicOr(err, kErrIndex); e = (int32_t)p; }
+            int32_t lo, hi;
+            const int ci = i / kChunk;
+            if (e < base + kRmqTile) {
+                const int je = (int)(e - base), ce = je / kChunk;
+                if (ci == ce) {
+                    lo = INT32_MAX; hi = INT32_MIN;
+                    for (int q = i; q <= je; ++q) {
+                        lo = s1[q] < lo ? s1[q] : lo;
+                        hi = s2[q] > hi ? s2[q] : hi;
+                    }
+                } else {
+                    lo = suf1[i] < pre1[je] ? suf1[i] : pre1[je];
+                    hi = suf2[i] > pre2[je] ? suf2[i] : pre2[je];
+                    for (int c = ci + 1; c < ce; ++c) {
+                        lo = c1[c] < lo ? c1[c] : lo;
+                        hi = c2[c] > hi ? c2[c] : hi;
+                    }
+                }
+            } else {
+                lo = suf1[i];
+                hi = suf2[i];
+                if (ci + 1 < kNChunk) {
+                    lo = cs1[ci + 1] < lo ? cs1[ci + 1] : lo;
+                    hi = cs2[ci + 1] > hi ? cs2[ci + 1] : hi;
+                }
+                const int64_t te = e / kRmqTile;
+                if (te > t + 1) {  // whole tiles t+1 .. te-1: two overlapping sparse-table ranges
+                    const int64_t a = t + 1, len = te - 1 - a + 1;
+                    const int lv = 63 - __clzll(len);
+                    const int64_t b = te - 1 - (1ll << lv) + 1;
+                    const int32_t *lm = tmin + (int64_t)lv * st_stride, *lM = tmax + (int64_t)lv * st_stride;
+                    int32_t x = lm[a] < lm[b] ? lm[a] : lm[b], y = lM[a] > lM[b] ? lM[a] : lM[b];
+                    lo = x < lo ? x : lo;
+                    hi = y > hi ? y : hi;
+                }
+                lo = pmin[e] < lo ? pmin[e] : lo;
+                hi = pmax[e] > hi ? pmax[e] : hi;
+            }
+            const int32_t v = ord[p], x = porig[p];
+            if (!in_range(v, n, err) || x >= n) continue;
+            uint8_t bits = 0;
+            if (x >= 0) {
+                if (lo == (int32_t)p && hi <= e) bits |= 1;  // bridge: nothing leaves T_v
+                const bool fence = __ldg(first + x) <= lo && __ldg(last + x) >= hi;
+                if (!fence) uf_unite(uf, v, x, err);           // plain tree edge: in G'
+            }
+            vbits[v] = bits;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_iota(int32_t *a, int64_t n)
+{
+    GRID_STRIDE(i, n) a[i] = (int32_t)i;
+}
+
+template <typename OffT>
+cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                           bool vec, const Launch &L)
+{
+    const int64_t ntiles = ceil_div(nnz, kTile);
+    if (nnz > 0)
+        k_w12<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits, d.first,
+                                                              d.w1, d.w2, n, d.err, vec);
+    const int64_t rt = ceil_div(n, kRmqTile);
+    k_rmq_prefix<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax);
+    for (int j = 1; (1ll << j) <= rt; ++j)
+        k_rmq_level<<<grid_for(L, ceil_div(rt, kThreads)), kThreads, 0, L.s>>>(rt, j, d.rmq_tiles_max, d.tmin,
+                                                                                 d.tmax);
+    // Last-CC starts here: a fresh union-find that the query kernel fills with the
+    // plain tree edges.
+    k_iota<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(d.uf, n);
+    k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax,
+                                                       d.rmq_tiles_max, d.ord, d.lastp, d.porig, d.first, d.last,
+                                                       d.vbits, d.uf, d.err);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tagging<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, bool,
+                                             const Launch &);
+template cudaError_t launch_tagging<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, bool,
+                                             const Launch &);
+
+}  // namespace fbcc

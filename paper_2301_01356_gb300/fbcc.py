@@ -1,0 +1,228 @@
+"""Thin ctypes binding of libfbcc (the C ABI in ``include/fbcc.h``).
+
+Same names as the C entry points; only argument marshalling happens here. Device
+buffers are PyTorch CUDA tensors (their ``data_ptr()`` is passed through) and the
+stream is a ``torch.cuda.Stream`` (or the current stream). Every step of the
+computation runs in the library's CUDA kernels; there is no CPU fallback: if the
+library is not built, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfbcc.so")
+
+FBCC_OK, FBCC_E_INVALID, FBCC_E_NOT_SIMPLE, FBCC_E_OOM, FBCC_E_CUDA, FBCC_E_ITER_LIMIT, FBCC_E_WORKSPACE = range(7)
+
+# Every entry point include/fbcc.h declares (checked by the tests).
+EXPORTS = (
+    "fbcc_workspace_bytes", "fbcc_workspace_create", "fbcc_workspace_destroy", "fbcc_workspace_configure",
+    "fbcc_solve", "fbcc_solve_host", "fbcc_solve_batch", "fbcc_batch_workspace_bytes", "fbcc_validate",
+    "fbcc_status_string", "fbcc_last_cuda_error",
+)
+
+
+class fbcc_stats(ctypes.Structure):
+    _fields_ = [("n_bcc", ctypes.c_int64), ("n_ap", ctypes.c_int64), ("n_bridge", ctypes.c_int64),
+                ("n_cc", ctypes.c_int64), ("device_status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class fbcc_config(ctypes.Structure):
+    _fields_ = [("ruler_stride", ctypes.c_int32), ("cc_sample", ctypes.c_int32),
+                ("grid_ctas", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class FbccError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        lib = _lib
+        msg = lib.fbcc_status_string(status).decode() if lib else str(status)
+        if status == FBCC_E_CUDA and lib:
+            msg += ": " + lib.fbcc_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg}" if where else msg)
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfbcc (no build step here: run ``build()`` of ``__graft_entry__``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libfbcc is not built ({path} missing); build it with "
+                               "`python -m paper_2301_01356_gb300.build`")
+        lib = ctypes.CDLL(path)
+        P, I64, I32, INT = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        S = ctypes.POINTER(fbcc_stats)
+        lib.fbcc_workspace_bytes.argtypes = [I64, I64]
+        lib.fbcc_workspace_bytes.restype = ctypes.c_size_t
+        lib.fbcc_workspace_create.argtypes = [I64, I64, ctypes.POINTER(P)]
+        lib.fbcc_workspace_create.restype = INT
+        lib.fbcc_workspace_destroy.argtypes = [P]
+        lib.fbcc_workspace_destroy.restype = None
+        lib.fbcc_workspace_configure.argtypes = [P, ctypes.POINTER(fbcc_config)]
+        lib.fbcc_workspace_configure.restype = INT
+        for name in ("fbcc_solve", "fbcc_solve_host"):
+            f = getattr(lib, name)
+            f.argtypes = [P, INT, P, I64, I64, P, P, P, P, S, P, P]
+            f.restype = INT
+        lib.fbcc_solve_batch.argtypes = [I32, P, P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.fbcc_solve_batch.restype = INT
+        lib.fbcc_batch_workspace_bytes.argtypes = [I64, I64, I32]
+        lib.fbcc_batch_workspace_bytes.restype = ctypes.c_size_t
+        lib.fbcc_validate.argtypes = [P, INT, P, I64, I64, P, P]
+        lib.fbcc_validate.restype = INT
+        lib.fbcc_status_string.argtypes = [INT]
+        lib.fbcc_status_string.restype = ctypes.c_char_p
+        lib.fbcc_last_cuda_error.argtypes = []
+        lib.fbcc_last_cuda_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != FBCC_OK:
+        raise FbccError(status, where)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+# ---- the C entry points ----------------------------------------------------------
+
+def fbcc_workspace_bytes(n: int, nnz: int) -> int:
+    return int(load().fbcc_workspace_bytes(n, nnz))
+
+
+def fbcc_workspace_create(n_max: int, nnz_max: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().fbcc_workspace_create(n_max, nnz_max, ctypes.byref(h)), "fbcc_workspace_create")
+    return h.value
+
+
+def fbcc_workspace_destroy(ws: int) -> None:
+    load().fbcc_workspace_destroy(ws)
+
+
+def fbcc_workspace_configure(ws: int, ruler_stride=0, cc_sample=0, grid_ctas=0, use_graph=0) -> None:
+    cfg = fbcc_config(ruler_stride, cc_sample, grid_ctas, use_graph)
+    _check(load().fbcc_workspace_configure(ws, ctypes.byref(cfg)), "fbcc_workspace_configure")
+
+
+def fbcc_solve(offsets, adj, n: int, m: int, edge_bcc, bcc_head, is_ap, is_bridge, ws: int,
+               stream=None, stats: fbcc_stats | None = None) -> fbcc_stats:
+    """Enqueue one solve on device tensors; ``stats`` is valid after a stream sync."""
+    import torch
+    stats = stats if stats is not None else fbcc_stats()
+    off64 = int(offsets.dtype == torch.int64)
+    _check(load().fbcc_solve(_ptr(offsets), off64, _ptr(adj), n, m, _ptr(edge_bcc), _ptr(bcc_head), _ptr(is_ap),
+                             _ptr(is_bridge), ctypes.byref(stats), ws, _stream_handle(stream)), "fbcc_solve")
+    return stats
+
+
+def fbcc_solve_host(offsets: np.ndarray, adj: np.ndarray, edge_bcc: np.ndarray, bcc_head: np.ndarray,
+                    is_ap: np.ndarray, is_bridge: np.ndarray, ws: int, stream=None) -> fbcc_stats:
+    """Solve on host (numpy, ideally pinned) buffers; synchronous."""
+    stats = fbcc_stats()
+    n = offsets.size - 1
+    m = int(offsets[-1]) // 2
+    _check(load().fbcc_solve_host(offsets.ctypes.data, int(offsets.dtype == np.int64), adj.ctypes.data, n, m,
+                                  edge_bcc.ctypes.data, bcc_head.ctypes.data, is_ap.ctypes.data,
+                                  is_bridge.ctypes.data, ctypes.byref(stats), ws, _stream_handle(stream)),
+           "fbcc_solve_host")
+    return stats
+
+
+def fbcc_validate(offsets, adj, n: int, m: int, ws: int, stream=None) -> int:
+    """Status of the device-side format check (FBCC_OK, FBCC_E_INVALID or FBCC_E_NOT_SIMPLE)."""
+    import torch
+    return int(load().fbcc_validate(_ptr(offsets), int(offsets.dtype == torch.int64), _ptr(adj), n, m, ws,
+                                    _stream_handle(stream)))
+
+
+def fbcc_solve_batch(vtx_base, arc_base, host_vtx_base: np.ndarray, host_arc_base: np.ndarray, local_off,
+                     local_adj, edge_bcc, bcc_head, is_ap, is_bridge, stats_dev, ws: int, stream=None) -> None:
+    g = host_vtx_base.size - 1
+    _check(load().fbcc_solve_batch(g, _ptr(vtx_base), _ptr(arc_base), host_vtx_base.ctypes.data,
+                                   host_arc_base.ctypes.data, _ptr(local_off), _ptr(local_adj), _ptr(edge_bcc),
+                                   _ptr(bcc_head), _ptr(is_ap), _ptr(is_bridge), _ptr(stats_dev), ws,
+                                   _stream_handle(stream)), "fbcc_solve_batch")
+
+
+def fbcc_batch_workspace_bytes(n_total: int, nnz_total: int, n_graphs: int) -> int:
+    return int(load().fbcc_batch_workspace_bytes(n_total, nnz_total, n_graphs))
+
+
+# ---- convenience wrapper ---------------------------------------------------------
+
+class Solver:
+    """A workspace plus output tensors for graphs up to (n_max, nnz_max)."""
+
+    def __init__(self, n_max: int, nnz_max: int, device="cuda", **config):
+        import torch
+        self.device = torch.device(device)
+        self.n_max, self.nnz_max = n_max, nnz_max
+        self.ws = fbcc_workspace_create(n_max, nnz_max)
+        if config:
+            fbcc_workspace_configure(self.ws, **config)
+        self.edge_bcc = torch.empty(max(nnz_max, 1), dtype=torch.int32, device=self.device)
+        self.bcc_head = torch.empty(max(n_max, 1), dtype=torch.int32, device=self.device)
+        self.is_ap = torch.empty(max(n_max, 1), dtype=torch.uint8, device=self.device)
+        self.is_bridge = torch.empty(max(nnz_max, 1), dtype=torch.uint8, device=self.device)
+        self.stats = fbcc_stats()
+
+    def configure(self, **config):
+        fbcc_workspace_configure(self.ws, **config)
+
+    def enqueue(self, offsets, adj, stream=None) -> fbcc_stats:
+        n = offsets.numel() - 1
+        m = (adj.numel()) // 2
+        return fbcc_solve(offsets, adj, n, m, self.edge_bcc, self.bcc_head, self.is_ap, self.is_bridge, self.ws,
+                          stream, self.stats)
+
+    def solve(self, offsets, adj, stream=None) -> dict:
+        """Solve and return host copies of the outputs (synchronises the stream)."""
+        import torch
+        n = offsets.numel() - 1
+        nnz = adj.numel()
+        st = self.enqueue(offsets, adj, stream)
+        (stream or torch.cuda.current_stream()).synchronize()
+        s = st.as_dict()
+        return {
+            "edge_bcc": self.edge_bcc[:nnz].cpu().numpy(),
+            "bcc_head": self.bcc_head[:s["n_bcc"]].cpu().numpy(),
+            "is_ap": self.is_ap[:n].cpu().numpy(),
+            "is_bridge": self.is_bridge[:nnz].cpu().numpy(),
+            **s,
+        }
+
+    def close(self):
+        if self.ws:
+            fbcc_workspace_destroy(self.ws)
+            self.ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,215 @@
+"""GPU parity: libfbcc (through its C ABI) against the Hopcroft-Tarjan oracle.
+
+Every output must be bit-identical after the shared canonical numbering:
+edge_bcc, bcc_head[0:n_bcc], is_ap, is_bridge and the four counts.
+"""
+import numpy as np
+import pytest
+
+from paper_2301_01356_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("edge_bcc", "bcc_head", "is_ap", "is_bridge", "n_bcc", "n_ap", "n_bridge", "n_cc")
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def solver(torch_cuda):
+    from paper_2301_01356_gb300 import fbcc
+    s = fbcc.Solver(1 << 17, 1 << 21)
+    yield s
+    s.close()
+
+
+def to_dev(torch, g, off64=True):
+    off = torch.from_numpy(g.offsets.astype(np.int64 if off64 else np.int32)).cuda()
+    adj = torch.from_numpy(g.adj).cuda()
+    return off, adj
+
+
+def assert_same(got, exp, what=""):
+    for k in KEYS:
+        assert np.array_equal(np.asarray(got[k]), np.asarray(exp[k])), f"{what}: {k} differs"
+    assert got["device_status"] == 0, f"{what}: device status {got['device_status']}"
+
+
+def check(torch, solver, oracle, g, off64=True, what=None):
+    off, adj = to_dev(torch, g, off64)
+    got = solver.solve(off, adj)
+    exp = oracle.solve(g.offsets, g.adj)
+    assert_same(got, exp, what or g.name)
+    return got
+
+
+def small_graphs():
+    out = [gg.cycle(3), gg.cycle(50), gg.path(2), gg.path(300), gg.star(40), gg.complete(12),
+           gg.grid(7, 9), gg.grid(6, 6, torus=True), gg.cycles_chain_exact([3, 4, 5, 6], 3),
+           gg.from_edges(6, [], []), gg.from_edges(3, [1], [2]), gg.random_tree(500, 3)]
+    for seed in range(12):
+        rng = np.random.default_rng(seed)
+        n = int(rng.integers(5, 400))
+        m = int(rng.integers(0, min(n * (n - 1) // 2, 3 * n)))
+        out.append(gg.uniform(n, m, seed))
+    return out
+
+
+def test_small_graphs(torch_cuda, solver, oracle):
+    for g in small_graphs():
+        for off64 in (True, False):
+            check(torch_cuda, solver, oracle, g, off64)
+
+
+def test_random_tiny_graphs(torch_cuda, solver, oracle):
+    rng = np.random.default_rng(7)
+    for it in range(150):
+        n = int(rng.integers(1, 12))
+        p = float(rng.uniform(0.1, 0.9))
+        e = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+        g = gg.from_edges(n, [a for a, _ in e], [b for _, b in e])
+        check(torch_cuda, solver, oracle, g, bool(it & 1), f"tiny#{it}")
+
+
+@pytest.mark.parametrize("family", ["uniform", "grid", "rmat", "chain", "knn", "union"])
+def test_families_several_tiles(torch_cuda, solver, oracle, family):
+    """Graphs spanning many arc tiles, RMQ tiles and rulers, with a ragged tail."""
+    g = {
+        "uniform": lambda: gg.uniform(30011, 70001, 5),
+        "grid": lambda: gg.grid(211, 173, p=0.62, extra_frac=0.001, seed=9),
+        "rmat": lambda: gg.rmat(15, 8, seed=4),
+        "chain": lambda: gg.cycle_chain(60013, 40, 3, 3000, 11),
+        "knn": lambda: gg.knn3(25000, 5, 2),
+        "union": lambda: gg.disjoint_union(gg.from_edges(5, [], []), gg.grid(50, 61, p=0.7, seed=1),
+                                           gg.path(4000), gg.uniform(3000, 9000, 3), gg.from_edges(7, [], [])),
+    }[family]()
+    assert g.n <= solver.n_max and g.nnz <= solver.nnz_max
+    check(torch_cuda, solver, oracle, g, True)
+    check(torch_cuda, solver, oracle, g, False)
+
+
+def test_uniform_64k_workload(torch_cuda, solver, oracle):
+    g = gg.workload_uniform_64k()
+    got = check(torch_cuda, solver, oracle, g, False)
+    assert got["n_bcc"] > 1 and got["n_bridge"] > 0 and got["n_ap"] > 0
+
+
+def test_repeated_solves_and_configs(torch_cuda, oracle):
+    """Graph replay, re-capture on new inputs, and every tuning knob give the same result."""
+    from paper_2301_01356_gb300 import fbcc
+    g1, g2 = gg.grid(100, 120, p=0.6, seed=3), gg.uniform(9000, 20000, 4)
+    e1, e2 = oracle.solve(g1.offsets, g1.adj), oracle.solve(g2.offsets, g2.adj)
+    for cfg in ({}, {"ruler_stride": 4}, {"ruler_stride": 256}, {"cc_sample": 2}, {"use_graph": -1},
+                {"grid_ctas": 3}):
+        s = fbcc.Solver(20000, 50000, **cfg)
+        for _ in range(2):
+            for g, e in ((g1, e1), (g2, e2), (g1, e1)):
+                off, adj = to_dev(torch_cuda, g)
+                assert_same(s.solve(off, adj), e, f"{cfg} {g.name}")
+        s.close()
+
+
+def test_host_entry_point(torch_cuda, oracle):
+    from paper_2301_01356_gb300 import fbcc
+    g = gg.uniform(5000, 12000, 8)
+    s = fbcc.Solver(g.n, g.nnz)
+    eb = np.empty(g.nnz, np.int32)
+    bh = np.empty(g.n, np.int32)
+    ap = np.empty(g.n, np.uint8)
+    br = np.empty(g.nnz, np.uint8)
+    for off in (g.offsets, g.offsets.astype(np.int32)):
+        st = fbcc.fbcc_solve_host(off, g.adj, eb, bh, ap, br, s.ws).as_dict()
+        got = {"edge_bcc": eb, "bcc_head": bh[:st["n_bcc"]], "is_ap": ap, "is_bridge": br, **st}
+        assert_same(got, oracle.solve(g.offsets, g.adj), "host")
+    s.close()
+
+
+def test_validate(torch_cuda):
+    from paper_2301_01356_gb300 import fbcc
+    s = fbcc.Solver(100, 1000)
+    g = gg.cycle(6)
+    off, adj = to_dev(torch_cuda, g)
+    assert fbcc.fbcc_validate(off, adj, g.n, g.m, s.ws) == fbcc.FBCC_OK
+    bad = g.adj.copy()
+    bad[0] = 0                                       # self-loop
+    assert fbcc.fbcc_validate(off, torch_cuda.from_numpy(bad).cuda(), g.n, g.m, s.ws) == fbcc.FBCC_E_NOT_SIMPLE
+    bad = g.adj.copy()
+    bad[0], bad[1] = bad[1], bad[0]                  # unsorted
+    assert fbcc.fbcc_validate(off, torch_cuda.from_numpy(bad).cuda(), g.n, g.m, s.ws) == fbcc.FBCC_E_NOT_SIMPLE
+    bad = g.adj.copy()
+    bad[0] = 2                                       # asymmetric
+    assert fbcc.fbcc_validate(off, torch_cuda.from_numpy(bad).cuda(), g.n, g.m, s.ws) == fbcc.FBCC_E_NOT_SIMPLE
+    bad = g.adj.copy()
+    bad[0] = 99                                      # out of range
+    assert fbcc.fbcc_validate(off, torch_cuda.from_numpy(bad).cuda(), g.n, g.m, s.ws) == fbcc.FBCC_E_INVALID
+    off_bad = off.clone()
+    off_bad[-1] += 2                                 # offsets[n] != 2m
+    assert fbcc.fbcc_validate(off_bad, adj, g.n, g.m, s.ws) == fbcc.FBCC_E_INVALID
+    # host-side argument checks
+    with pytest.raises(fbcc.FbccError):
+        fbcc.fbcc_solve(off, adj, g.n, 10**6, s.edge_bcc, s.bcc_head, s.is_ap, s.is_bridge, s.ws)
+    s.close()
+
+
+def _pack(graphs):
+    vb = np.zeros(len(graphs) + 1, np.int64)
+    ab = np.zeros(len(graphs) + 1, np.int64)
+    for i, g in enumerate(graphs):
+        vb[i + 1] = vb[i] + g.n
+        ab[i + 1] = ab[i] + g.nnz
+    loff = np.concatenate([g.offsets[:-1] for g in graphs]).astype(np.int32) if vb[-1] else np.zeros(0, np.int32)
+    ladj = np.concatenate([g.adj for g in graphs]).astype(np.int32)
+    return vb, ab, loff, ladj
+
+
+def test_batch_matches_per_graph(torch_cuda, oracle):
+    """Each graph's result in a batch equals its result alone (and the oracle's)."""
+    from paper_2301_01356_gb300 import fbcc
+    torch = torch_cuda
+    rng = np.random.default_rng(3)
+    graphs = []
+    for i in range(37):
+        kind = i % 4
+        n = int(rng.integers(3, 3000))
+        graphs.append([
+            lambda: gg.uniform(n, min(n * (n - 1) // 2, int(n * rng.uniform(2, 6))), i),
+            lambda: gg.grid(max(2, int(np.sqrt(n))), max(2, int(np.sqrt(n))), p=float(rng.uniform(0.55, 0.75)), seed=i),
+            lambda: gg.cycle_chain(max(n, 10), int(rng.integers(2, 8)), 3, 500, i),
+            lambda: gg.from_edges(n, [], []),
+        ][kind]())
+    vb, ab, loff, ladj = _pack(graphs)
+    n_tot, z_tot = int(vb[-1]), int(ab[-1])
+    s = fbcc.Solver(n_tot, z_tot)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    stats = torch.zeros(len(graphs) * 5, dtype=torch.int64, device="cuda")  # 40-byte fbcc_stats
+    for _ in range(2):
+        fbcc.fbcc_solve_batch(dev(vb), dev(ab), vb, ab, dev(loff), dev(ladj), s.edge_bcc, s.bcc_head, s.is_ap,
+                              s.is_bridge, stats, s.ws)
+        torch.cuda.synchronize()
+        eb, bh = s.edge_bcc[:z_tot].cpu().numpy(), s.bcc_head[:n_tot].cpu().numpy()
+        ap, br = s.is_ap[:n_tot].cpu().numpy(), s.is_bridge[:z_tot].cpu().numpy()
+        st = stats.cpu().numpy().reshape(len(graphs), 5)
+        for i, g in enumerate(graphs):
+            e = oracle.solve(g.offsets, g.adj)
+            got = {"edge_bcc": eb[ab[i]:ab[i + 1]], "bcc_head": bh[vb[i]:vb[i] + st[i, 0]],
+                   "is_ap": ap[vb[i]:vb[i + 1]], "is_bridge": br[ab[i]:ab[i + 1]], "n_bcc": st[i, 0],
+                   "n_ap": st[i, 1], "n_bridge": st[i, 2], "n_cc": st[i, 3], "device_status": int(st[i, 4] & 0xffffffff)}
+            assert_same(got, e, f"batch graph {i}")
+    s.close()
+
+
+def test_grid_4096_full_size(torch_cuda, oracle):
+    """The benchmark's large-diameter workload at full size, every output."""
+    from paper_2301_01356_gb300 import fbcc
+    g = gg.workload_grid_4096()
+    s = fbcc.Solver(g.n, g.nnz)
+    off, adj = to_dev(torch_cuda, g, off64=False)
+    got = s.solve(off, adj)
+    assert_same(got, oracle.solve(g.offsets, g.adj), "grid 4096")
+    s.close()
