@@ -71,6 +71,7 @@ typedef struct {
     int32_t cc_sample;     /* First-CC: neighbours per vertex hooked before the full pass (0 = off) */
     int32_t grid_ctas;     /* CTAs of the persistent grid-stride kernels */
     int32_t use_graph;     /* 1 = replay a captured CUDA graph for repeated identical calls (default), -1 = never */
+    int32_t profile;       /* 1 = record a CUDA event after every kernel (no graph); see fbcc_profile_get */
 } fbcc_config;
 
 /* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds. */
@@ -147,6 +148,32 @@ size_t fbcc_batch_workspace_bytes(int64_t n_total, int64_t nnz_total, int32_t n_
  */
 fbcc_status fbcc_validate(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
                           int64_t n, int64_t m, fbcc_workspace *ws, void *stream);
+
+/* Number of kernels timed in the last solve made with fbcc_config.profile = 1. */
+int32_t fbcc_profile_count(const fbcc_workspace *ws);
+
+/* Name and device time (ms, from CUDA events on the solve's stream) of timed
+ * kernel i of the last profiled solve; waits for that solve to finish. */
+fbcc_status fbcc_profile_get(const fbcc_workspace *ws, int32_t i, const char **name, float *ms);
+
+/*
+ * Copy the named internal per-vertex array of the workspace's last solve into
+ * host memory (synchronous; for tests of the intermediate phases). Names and
+ * element types (int32 unless stated), all of length n:
+ *   "first", "last", "parent"  preorder number, last preorder number in the
+ *                              subtree, tree parent (-1 for a root), by vertex
+ *   "label"                    Last-CC label by vertex (a root is its own label)
+ *   "w1", "w2"                 w1/w2 by preorder number
+ *   "low", "high"              low/high by preorder number (only when the solve
+ *                              ran with fbcc_config.profile = 1)
+ *   "tree_u", "tree_v"         forest edge recorded at the vertex it hooked (-1: none)
+ *   "ord", "lastp", "porig"    vertex, last[] and parent vertex (-1: root) by preorder number
+ *   "vbits" (uint8)            bit 0: the tree edge to the parent is a bridge;
+ *                              bit 1: it is a fence edge
+ *   "err" (count 1)            the device error bits of the last solve
+ * Returns FBCC_E_INVALID for an unknown name or count > workspace n_max.
+ */
+fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *name, void *host_dst, int64_t count);
 
 /* Static description of a status code. */
 const char *fbcc_status_string(fbcc_status s);

@@ -110,6 +110,8 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.tmin = c.take<int32_t>(d.st_levels * d.rmq_tiles_max);
     d.tmax = c.take<int32_t>(d.st_levels * d.rmq_tiles_max);
     d.vbits = c.take<uint8_t>(N);
+    d.low = c.take<int32_t>(N);
+    d.high = c.take<int32_t>(N);
     d.head = c.take<int32_t>(N);
     d.nh = c.take<int32_t>(N);
     d.key = c.take<unsigned long long>(N);
@@ -139,6 +141,7 @@ struct fbcc_workspace {
     // global offsets/adjacency and per-graph bases of fbcc_solve_batch (first use)
     void *bstage = nullptr;
     size_t bstage_bytes = 0;
+    Prof prof;             // per-kernel events of profiled solves
 };
 
 static fbcc_config default_config()
@@ -148,6 +151,7 @@ static fbcc_config default_config()
     c.cc_sample = 0;
     c.grid_ctas = 0;
     c.use_graph = 1;
+    c.profile = 0;
     return c;
 }
 
@@ -198,6 +202,8 @@ void fbcc_workspace_destroy(fbcc_workspace *ws)
     cudaDeviceSynchronize();
     if (ws->exec) cudaGraphExecDestroy(ws->exec);
     if (ws->cap) cudaStreamDestroy(ws->cap);
+    if (ws->prof.ready)
+        for (int i = 0; i <= kProfMax; ++i) cudaEventDestroy(ws->prof.ev[i]);
     cudaFree(ws->slab);
     cudaFree(ws->stage);
     cudaFree(ws->bstage);
@@ -217,6 +223,7 @@ fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
         c.cc_sample = cfg->cc_sample;
         c.grid_ctas = cfg->grid_ctas;
         if (cfg->use_graph) c.use_graph = cfg->use_graph;
+        c.profile = cfg->profile > 0;
     }
     ws->cfg = c;
     return FBCC_OK;
@@ -275,6 +282,11 @@ cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *ad
     const Dev &d = ws->d;
     const int64_t nnz = 2 * m;
     Launch L{s, device_grid(ws->cfg)};
+    if (ws->cfg.profile) {
+        L.prof = &ws->prof;
+        ws->prof.count = 0;
+        cudaEventRecord(ws->prof.ev[0], s);
+    }
     const bool vec = ((uintptr_t)adj & 15) == 0;
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
@@ -284,11 +296,12 @@ cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *ad
         CK(cudaMemsetAsync(d.tree_bits, 0, (ceil_div(nnz, 32) + 1) * sizeof(uint32_t), s));
         CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, vec, L));
         CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, L));
-        CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, L));
+        CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, ws->cfg.profile != 0, L));
         CK(launch_last_cc<OffT>(d, off, adj, n, nnz, vec, L));
         CK(launch_outputs<OffT>(d, off, adj, n, nnz, vec, edge_bcc, bcc_head, is_ap, is_bridge, B, L));
     }
     k_finish<<<1, 1, 0, s>>>(d.err, d.stats);
+    L.mark("k_finish");
 #undef CK
     return cudaGetLastError();
 }
@@ -315,6 +328,7 @@ fbcc_status solve_device(const void *off, int offsets_64, const int32_t *adj, in
         if (B.G > 0 && n > 0) {
             k_batch_globalize<<<device_grid(ws->cfg), kThreads, 0, q>>>(B.G, B.vtx_base, B.arc_base, loff, ladj, n,
                                                                          (int64_t *)off, (int32_t *)adj);
+            // (in a profiled solve this kernel's time is folded into the first phase's first mark)
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
@@ -322,7 +336,11 @@ fbcc_status solve_device(const void *off, int offsets_64, const int32_t *adj, in
             ? enqueue_solve<int64_t>(ws, (const int64_t *)off, adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, q, B)
             : enqueue_solve<int32_t>(ws, (const int32_t *)off, adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, q, B);
     };
-    if (ws->cfg.use_graph > 0) {
+    if (ws->cfg.profile && !ws->prof.ready) {
+        for (int i = 0; i <= kProfMax; ++i) API_CK(cudaEventCreate(&ws->prof.ev[i]), "cudaEventCreate");
+        ws->prof.ready = true;
+    }
+    if (ws->cfg.use_graph > 0 && !ws->cfg.profile) {
         GraphKey k;
         memset(&k, 0, sizeof(k));
         k.off = off; k.adj = adj; k.edge_bcc = edge_bcc; k.bcc_head = bcc_head; k.is_ap = is_ap;
@@ -537,4 +555,42 @@ extern "C" fbcc_status fbcc_solve_batch(int32_t n_graphs, const int64_t *vtx_bas
     B.stats = stats;
     return solve_device(goff, 1, gadj, n, nnz / 2, edge_bcc, bcc_head, is_ap, is_bridge, nullptr, ws,
                         (cudaStream_t)stream, B, local_off, local_adj);
+}
+
+extern "C" int32_t fbcc_profile_count(const fbcc_workspace *ws) { return ws ? ws->prof.count : 0; }
+
+extern "C" fbcc_status fbcc_profile_get(const fbcc_workspace *ws, int32_t i, const char **name, float *ms)
+{
+    if (!ws || !ws->prof.ready || i < 0 || i >= ws->prof.count || !name || !ms) return FBCC_E_INVALID;
+    API_CK(cudaEventSynchronize(ws->prof.ev[i + 1]), "cudaEventSynchronize");
+    API_CK(cudaEventElapsedTime(ms, ws->prof.ev[i], ws->prof.ev[i + 1]), "cudaEventElapsedTime");
+    *name = ws->prof.names[i];
+    return FBCC_OK;
+}
+
+extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *name, void *host_dst, int64_t count)
+{
+    if (!ws || !name || !host_dst || count < 0 || count > ws->d.n_max) return FBCC_E_INVALID;
+    const Dev &d = ws->d;
+    const void *src = nullptr;
+    size_t elem = 4;
+    if (!strcmp(name, "first")) src = d.first;
+    else if (!strcmp(name, "last")) src = d.last;
+    else if (!strcmp(name, "parent")) src = d.parent;
+    else if (!strcmp(name, "label")) src = d.uf;
+    else if (!strcmp(name, "w1")) src = d.w1;
+    else if (!strcmp(name, "w2")) src = d.w2;
+    else if (!strcmp(name, "low")) src = d.low;
+    else if (!strcmp(name, "high")) src = d.high;
+    else if (!strcmp(name, "tree_u")) src = d.te_u;
+    else if (!strcmp(name, "tree_v")) src = d.te_v;
+    else if (!strcmp(name, "ord")) src = d.ord;
+    else if (!strcmp(name, "lastp")) src = d.lastp;
+    else if (!strcmp(name, "porig")) src = d.porig;
+    else if (!strcmp(name, "err")) { src = d.err; if (count > 1) return FBCC_E_INVALID; }
+    else if (!strcmp(name, "vbits")) { src = d.vbits; elem = 1; }
+    else return FBCC_E_INVALID;
+    API_CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    API_CK(cudaMemcpy(host_dst, src, size_t(count) * elem, cudaMemcpyDeviceToHost), "debug copy");
+    return FBCC_OK;
 }

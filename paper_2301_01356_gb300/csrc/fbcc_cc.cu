@@ -122,10 +122,12 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_skip(const OffT *__restric
     }
 }
 
+// Flatten every set to its root. Only roots are ever stored, so concurrent
+// threads cannot leave a vertex pointing at a non-root (see uf_root).
 __global__ void __launch_bounds__(kThreads) k_uf_compress(int32_t *uf, int64_t n)
 {
     for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads)
-        uf[v] = uf_find(uf, (int32_t)v);
+        uf[v] = uf_root(uf, (int32_t)v);
 }
 
 // The root of the component holding most sampled vertices: a vote over a fixed
@@ -158,20 +160,27 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
     const int gv = grid_for(L, ceil_div(n, kThreads));
     const int ga = grid_for(L, ntiles);
     k_cc_init<OffT><<<gv, kThreads, 0, L.s>>>(off, n, nnz, d.tile_v, ntiles, d.uf, d.te_u);
+    L.mark("k_cc_init");
     if (nnz > 0) {
         if (cc_sample > 0) {
             int32_t *big = reinterpret_cast<int32_t *>(d.counters + 8);
             k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, d.err);
+            L.mark("k_cc_sample");
             k_uf_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
+            L.mark("k_uf_compress");
             k_cc_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, n, big);
+            L.mark("k_cc_pick_big");
             k_cc_hook_skip<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
                                                           big, d.err, vec);
+            L.mark("k_cc_hook_skip");
         } else {
             k_cc_hook<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v, d.err,
                                                      vec);
+            L.mark("k_cc_hook");
         }
     }
     k_uf_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
+    L.mark("k_uf_compress");
     return cudaGetLastError();
 }
 
@@ -220,7 +229,9 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
     if (nnz > 0)
         k_last_cc_cross<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
                                                                         d.first, d.last, d.uf, d.err, vec);
+        L.mark("k_last_cc_cross");
     k_uf_compress<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(d.uf, n);
+    L.mark("k_uf_compress");
     return cudaGetLastError();
 }
 

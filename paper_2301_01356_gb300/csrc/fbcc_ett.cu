@@ -309,35 +309,45 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
     CK(cudaMemsetAsync(d.tdeg, 0, (n + 1) * sizeof(int32_t), L.s));
     k_tree_count<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, d.te_u, d.te_v, d.tdeg, d.tree_bits);
+    L.mark("k_tree_count");
     CK(cudaGetLastError());
     CK(launch_scan_i32(d, d.tdeg, d.toff, n, L));
     CK(cudaMemsetAsync(d.tdeg, 0, (n + 1) * sizeof(int32_t), L.s));
     k_tree_fill<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.toff, d.tdeg, d.tadj, d.twin, d.err);
+    L.mark("k_tree_fill");
     k_succ<<<ga, kThreads, 0, L.s>>>(2 * n, d.toff, n, d.tadj, d.twin, d.succ, d.is_head);
+    L.mark("k_succ");
     k_tour_cut<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.toff, d.twin, d.succ, d.is_head);
+    L.mark("k_tour_cut");
     long long *nr = d.counters + 1;
     CK(cudaMemsetAsync(nr, 0, sizeof(long long), L.s));
     k_rulers<<<ga, kThreads, 0, L.s>>>(d.toff, n, ruler_stride, d.succ, d.is_head, d.link, d.relem, nr);
+    L.mark("k_rulers");
     // upper bound on the number of rulers: every tour head plus one per stride
     const int64_t rbound = n + ceil_div(2 * n, ruler_stride) + 1;
     const int gr = grid_for(L, ceil_div(rbound, kThreads));
     k_chase<<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.owner, d.offs, d.rnext[0], d.rval[0],
                                       d.rlen, d.err);
+    L.mark("k_chase");
     int cur = 0;
     const int rounds = jump_rounds(rbound);
     for (int i = 0; i < rounds; ++i) {
         k_jump<<<gr, kThreads, 0, L.s>>>(nr, d.rnext[cur], d.rval[cur], d.rnext[cur ^ 1], d.rval[cur ^ 1]);
+        L.mark("k_jump");
         cur ^= 1;
     }
     const int32_t *sd = d.rval[cur];
     k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.toff, d.link, sd, nr, d.csize, d.err);
+    L.mark("k_comp_size");
     CK(cudaGetLastError());
     CK(launch_scan_i32(d, d.csize, d.vbase, n, L));
     CK(cudaMemsetAsync(d.tour, 0xff, 2 * n * sizeof(int32_t), L.s));
     k_place<<<ga, kThreads, 0, L.s>>>(d.toff, n, d.tadj, d.uf, d.csize, d.vbase, d.owner, d.offs, sd, d.pos, d.tour,
                                       d.err);
+    L.mark("k_place");
     k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.tour, d.first, d.last, d.parent, d.ord,
                                           d.lastp, d.porig, d.w1, d.w2);
+    L.mark("k_root_tags");
     CK(cudaGetLastError());
     const int64_t ntiles = ceil_div(2 * n, kTile);
     CK(cudaMemsetAsync(d.counters, 0, sizeof(long long), L.s));
@@ -345,6 +355,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     k_preorder<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(2 * n, d.tour, d.pos, d.tadj, d.twin, d.first, d.last,
                                                            d.parent, d.ord, d.lastp, d.porig, d.w1, d.w2, d.counters,
                                                            d.scan_status, d.err);
+    L.mark("k_preorder");
 #undef CK
     return cudaGetLastError();
 }

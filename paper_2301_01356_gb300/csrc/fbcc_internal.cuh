@@ -70,6 +70,7 @@ struct Dev {
     int32_t *pmin, *pmax;     // in-tile prefix min/max of w1/w2
     int32_t *tmin, *tmax;     // sparse tables over RMQ tiles: st_levels x rmq_tiles_max
     uint8_t *vbits;           // per vertex: bit0 = tree edge to parent is a bridge
+    int32_t *low, *high;      // low/high by preorder number (written by profiled solves only)
     // Last-CC and outputs
     int32_t *head;            // head of label L at [L]
     int32_t *nh;              // number of labels a vertex heads
@@ -118,6 +119,19 @@ __device__ __forceinline__ int32_t uf_find(int32_t *uf, int32_t v)
         uf[v] = gp;  // halving: gp is an ancestor of v, so the store is always safe
         v = gp;
     }
+}
+
+// Root of v without writing anything. The final flattening pass uses this: a
+// halving store made there by one thread could land after another thread had
+// already stored the root into the same slot and leave a non-root behind.
+__device__ __forceinline__ int32_t uf_root(const int32_t *uf, int32_t v)
+{
+    int32_t p = ld_cg(uf + v);
+    while (p != v) {
+        v = p;
+        p = ld_cg(uf + v);
+    }
+    return v;
 }
 
 // Union of the sets of u and v by CAS-hooking the larger root under the smaller.
@@ -341,9 +355,27 @@ __device__ __forceinline__ int32_t graph_of(const int64_t *__restrict__ vtx_base
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// Per-kernel timing of a solve (fbcc_config.profile): an event after every launch.
+constexpr int kProfMax = 160;
+struct Prof {
+    int count = 0;
+    const char *names[kProfMax];
+    cudaEvent_t ev[kProfMax + 1];
+    bool ready = false;
+};
+
 struct Launch {
     cudaStream_t s;
-    int grid;        // persistent grid size (CTAs)
+    int grid;              // persistent grid size (CTAs)
+    Prof *prof = nullptr;  // set when the solve is profiled
+    void mark(const char *name) const
+    {
+        if (prof && prof->count < kProfMax) {
+            prof->names[prof->count] = name;
+            cudaEventRecord(prof->ev[prof->count + 1], s);
+            ++prof->count;
+        }
+    }
 };
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -363,7 +395,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
                            int ruler_stride, const Launch &L);
 template <typename OffT>
 cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           bool vec, const Launch &L);
+                           bool vec, bool keep_low_high, const Launch &L);
 template <typename OffT>
 cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, const Launch &L);

@@ -308,29 +308,40 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     CK(cudaMemsetAsync(d.nh, 0, n * sizeof(int32_t), L.s));
     CK(cudaMemsetAsync(d.scanv, 0, n, L.s));
     k_heads<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.head);
+    L.mark("k_heads");
     k_label_count<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.head, d.nh, d.stats, d.err);
+    L.mark("k_label_count");
     k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.parent, d.uf, d.head, d.nh, is_ap, d.key, d.scanv, d.stats, d.err);
+    L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
         k_key_scan<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.first,
                                                                    d.uf, d.head, d.key, vec);
+        L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
         k_key_bits<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.key, d.key_bits, nnz, d.err);
+        L.mark("k_key_bits");
         CK(cudaGetLastError());
         CK(launch_scan_popc(d, d.key_bits, d.key_pre, nwords, L));
-        if (B.G > 0)
+        if (B.G > 0) {
             k_bcc_base<<<grid_for(L, ceil_div(B.G + 1, kThreads)), kThreads, 0, L.s>>>(B, d.key_bits, d.key_pre);
+            L.mark("k_bcc_base");
+        }
         k_rank<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.key, d.key_bits, d.key_pre, d.head, d.rank, bcc_head, B, nnz, d.err);
+        L.mark("k_rank");
         k_fo<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.rank, d.first, d.vbits, d.fo, d.stats);
+        L.mark("k_fo");
         const bool vec_out = ((uintptr_t)edge_bcc & 15) == 0 && ((uintptr_t)is_bridge & 7) == 0;
         k_edge_out<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
                                                                    d.fo, edge_bcc, is_bridge, vec, vec_out);
+        L.mark("k_edge_out");
     } else if (B.G > 0) {
         CK(cudaMemsetAsync(B.bcc_base, 0, (B.G + 1) * sizeof(int64_t), L.s));
     }
     if (B.G > 0) {
         CK(cudaMemsetAsync(B.stats, 0, B.G * sizeof(fbcc_stats), L.s));
         k_batch_stats<<<gv, kThreads, 0, L.s>>>(n, B, d.parent, is_ap, d.vbits, d.err);
+        L.mark("k_batch_stats");
     }
 #undef CK
     return cudaGetLastError();

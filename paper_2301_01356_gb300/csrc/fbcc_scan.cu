@@ -57,6 +57,7 @@ cudaError_t launch_scan_i32(const Dev &d, const int32_t *in, int32_t *out, int64
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (len + 1 + kTile - 1) / kTile;
     k_scan_i32<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(in, out, len, d.counters, d.scan_status, d.err);
+    L.mark("k_scan_i32");
     return cudaGetLastError();
 }
 
@@ -66,6 +67,7 @@ cudaError_t launch_scan_popc(const Dev &d, const uint32_t *words, int32_t *out, 
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (len + 1 + kTile - 1) / kTile;
     k_scan_popc<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(words, out, len, d.counters, d.scan_status, d.err);
+    L.mark("k_scan_popc");
     return cudaGetLastError();
 }
 

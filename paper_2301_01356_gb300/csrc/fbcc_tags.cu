@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                                                         const int32_t *__restrict__ porig,
                                                         const int32_t *__restrict__ first,
                                                         const int32_t *__restrict__ last, uint8_t *vbits, int32_t *uf,
-                                                        int *err)
+                                                        int32_t *low_out, int32_t *high_out, int *err)
 {
     constexpr int kPer = kRmqTile / kThreads;
     constexpr int kNChunk = kRmqTile / kChunk;
@@ -241,13 +241,18 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                 lo = pmin[e] < lo ? pmin[e] : lo;
                 hi = pmax[e] > hi ? pmax[e] : hi;
             }
+            if (low_out) {
+                low_out[p] = lo;
+                high_out[p] = hi;
+            }
             const int32_t v = ord[p], x = porig[p];
             if (!in_range(v, n, err) || x >= n) continue;
             uint8_t bits = 0;
             if (x >= 0) {
                 if (lo == (int32_t)p && hi <= e) bits |= 1;  // bridge: nothing leaves T_v
                 const bool fence = __ldg(first + x) <= lo && __ldg(last + x) >= hi;
-                if (!fence) uf_unite(uf, v, x, err);           // plain tree edge: in G'
+                if (fence) bits |= 2;
+                else uf_unite(uf, v, x, err);                  // plain tree edge: in G'
             }
             vbits[v] = bits;
         }
@@ -261,29 +266,36 @@ __global__ void __launch_bounds__(kThreads) k_iota(int32_t *a, int64_t n)
 
 template <typename OffT>
 cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           bool vec, const Launch &L)
+                           bool vec, bool keep_low_high, const Launch &L)
 {
     const int64_t ntiles = ceil_div(nnz, kTile);
     if (nnz > 0)
         k_w12<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits, d.first,
                                                               d.w1, d.w2, n, d.err, vec);
+        L.mark("k_w12");
     const int64_t rt = ceil_div(n, kRmqTile);
     k_rmq_prefix<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax);
-    for (int j = 1; (1ll << j) <= rt; ++j)
+    L.mark("k_rmq_prefix");
+    for (int j = 1; (1ll << j) <= rt; ++j) {
         k_rmq_level<<<grid_for(L, ceil_div(rt, kThreads)), kThreads, 0, L.s>>>(rt, j, d.rmq_tiles_max, d.tmin,
                                                                                  d.tmax);
+        L.mark("k_rmq_level");
+    }
     // Last-CC starts here: a fresh union-find that the query kernel fills with the
     // plain tree edges.
     k_iota<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(d.uf, n);
+    L.mark("k_iota");
     k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax,
                                                        d.rmq_tiles_max, d.ord, d.lastp, d.porig, d.first, d.last,
-                                                       d.vbits, d.uf, d.err);
+                                                       d.vbits, d.uf, keep_low_high ? d.low : nullptr,
+                                                       keep_low_high ? d.high : nullptr, d.err);
+    L.mark("k_rmq_query");
     return cudaGetLastError();
 }
 
 template cudaError_t launch_tagging<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, bool,
-                                             const Launch &);
+                                             bool, const Launch &);
 template cudaError_t launch_tagging<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, bool,
-                                             const Launch &);
+                                             bool, const Launch &);
 
 }  // namespace fbcc

@@ -23,7 +23,7 @@ FBCC_OK, FBCC_E_INVALID, FBCC_E_NOT_SIMPLE, FBCC_E_OOM, FBCC_E_CUDA, FBCC_E_ITER
 EXPORTS = (
     "fbcc_workspace_bytes", "fbcc_workspace_create", "fbcc_workspace_destroy", "fbcc_workspace_configure",
     "fbcc_solve", "fbcc_solve_host", "fbcc_solve_batch", "fbcc_batch_workspace_bytes", "fbcc_validate",
-    "fbcc_status_string", "fbcc_last_cuda_error",
+    "fbcc_profile_count", "fbcc_profile_get", "fbcc_debug_read", "fbcc_status_string", "fbcc_last_cuda_error",
 )
 
 
@@ -37,7 +37,7 @@ class fbcc_stats(ctypes.Structure):
 
 class fbcc_config(ctypes.Structure):
     _fields_ = [("ruler_stride", ctypes.c_int32), ("cc_sample", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("grid_ctas", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32)]
 
 
 class FbccError(RuntimeError):
@@ -84,6 +84,12 @@ def load(path: str = LIB_PATH):
         lib.fbcc_batch_workspace_bytes.restype = ctypes.c_size_t
         lib.fbcc_validate.argtypes = [P, INT, P, I64, I64, P, P]
         lib.fbcc_validate.restype = INT
+        lib.fbcc_profile_count.argtypes = [P]
+        lib.fbcc_profile_count.restype = I32
+        lib.fbcc_profile_get.argtypes = [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float)]
+        lib.fbcc_profile_get.restype = INT
+        lib.fbcc_debug_read.argtypes = [P, ctypes.c_char_p, P, I64]
+        lib.fbcc_debug_read.restype = INT
         lib.fbcc_status_string.argtypes = [INT]
         lib.fbcc_status_string.restype = ctypes.c_char_p
         lib.fbcc_last_cuda_error.argtypes = []
@@ -124,8 +130,8 @@ def fbcc_workspace_destroy(ws: int) -> None:
     load().fbcc_workspace_destroy(ws)
 
 
-def fbcc_workspace_configure(ws: int, ruler_stride=0, cc_sample=0, grid_ctas=0, use_graph=0) -> None:
-    cfg = fbcc_config(ruler_stride, cc_sample, grid_ctas, use_graph)
+def fbcc_workspace_configure(ws: int, ruler_stride=0, cc_sample=0, grid_ctas=0, use_graph=0, profile=0) -> None:
+    cfg = fbcc_config(ruler_stride, cc_sample, grid_ctas, use_graph, profile)
     _check(load().fbcc_workspace_configure(ws, ctypes.byref(cfg)), "fbcc_workspace_configure")
 
 
@@ -151,6 +157,24 @@ def fbcc_solve_host(offsets: np.ndarray, adj: np.ndarray, edge_bcc: np.ndarray, 
                                   is_bridge.ctypes.data, ctypes.byref(stats), ws, _stream_handle(stream)),
            "fbcc_solve_host")
     return stats
+
+
+def fbcc_profile(ws: int) -> list:
+    """[(kernel name, ms)] of the last profiled solve (waits for it)."""
+    lib = load()
+    out = []
+    for i in range(lib.fbcc_profile_count(ws)):
+        name, ms = ctypes.c_char_p(), ctypes.c_float()
+        _check(lib.fbcc_profile_get(ws, i, ctypes.byref(name), ctypes.byref(ms)), "fbcc_profile_get")
+        out.append((name.value.decode(), float(ms.value)))
+    return out
+
+
+def fbcc_debug_read(ws: int, name: str, n: int) -> np.ndarray:
+    """Host copy of an internal per-vertex array of the last solve (see include/fbcc.h)."""
+    out = np.empty(max(n, 1), np.uint8 if name == "vbits" else np.int32)
+    _check(load().fbcc_debug_read(ws, name.encode(), out.ctypes.data, n), "fbcc_debug_read")
+    return out[:n]
 
 
 def fbcc_validate(offsets, adj, n: int, m: int, ws: int, stream=None) -> int:
