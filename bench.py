@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark: FAST-BCC biconnected components on one GB300 (or N replicas).
+
+One step = one full solve (First-CC, rooting, tagging, Last-CC, heads and the
+per-edge outputs) of the workload graph, already resident in HBM. The metric is
+undirected edges per second. Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl fbcc|reference]
+
+Workloads: grid4096 (default; the large-diameter road-like graph: 4096x4096
+open grid, edges kept with p = 0.62, plus 0.1 % short-range extra edges),
+uniform64k, rmat24. `--impl reference` times the CPU Hopcroft-Tarjan oracle (the
+only reference that exists for this method) on the same metric and workload.
+The GPU path is replicated per rank (the problem does not shard): N ranks each
+solve their own copy and the value is the whole job's edges per second.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2301_01356_gb300 import graphgen as gg  # noqa: E402
+
+METRIC = "undirected edges/sec, full BCC on 1 GB300 (plain vs batched); p50/p99 ms"
+UNIT = "undirected edges/s"
+
+WORKLOADS = {
+    "grid4096": (gg.workload_grid_4096, False,
+                 "large-diameter road-like graph: 4096x4096 open grid, each edge kept with p=0.62, plus 0.1% "
+                 "extra edges of Manhattan length 1..8, seed 2; int32 CSR"),
+    "grid2896": (gg.workload_grid_2896, False,
+                 "the grid4096 recipe on a 2896x2896 grid (profiler captures); int32 CSR"),
+    "uniform64k": (gg.workload_uniform_64k, False,
+                   "uniform random graph: n=65,536, m=196,608 distinct edges, seed 1; int32 CSR"),
+    "rmat24": (gg.workload_rmat_24, True,
+               "power-law R-MAT scale 24, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, seed 3; "
+               "int64 offsets, int32 adjacency"),
+}
+
+L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
+
+
+# ---------------------------------------------------------------------------
+# multi-process plumbing (replicas): plain torch.distributed, gloo on CPU tests
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def whole_job_rate(units_per_rank: float, steps: int, world: int, max_seconds: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return units_per_rank * steps * world / max_seconds
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# roofline: algorithmic bytes per launch of each kernel
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, stride: int) -> int | None:
+    """Bytes the method must move in one launch of `kernel`: every array the kernel
+    needs counted once, gathers at element size (derivations in the design doc)."""
+    A = 2 * (n - n_cc)                 # tree arcs
+    nr = n_cc + A // stride            # rulers (upper estimate)
+    B = off_bytes
+    table = {
+        "k_cc_init": B * (n + 1) + 8 * n,
+        "k_cc_hook": B * (n + 1) + 4 * nnz + 2 * nnz + 8 * (n - n_cc),
+        "k_uf_compress": 8 * n,
+        "k_tree_count": 8 * n + 16 * (n - n_cc),
+        "k_scan_i32": 8 * n,
+        "k_tree_fill": 8 * n + 8 * A + 16 * A,
+        "k_succ": 21 * A,
+        "k_tour_cut": 12 * n,
+        "k_rulers": 13 * A + 4 * nr,
+        "k_chase": 16 * A + 16 * nr,
+        "k_jump": 24 * nr,
+        "k_comp_size": 16 * n,
+        "k_place": 36 * A,
+        "k_root_tags": 12 * n_cc,
+        "k_preorder": 8 * n + 8 * A + 32 * n,
+        "k_w12": B * (n + 1) + 4 * nnz + nnz // 8 + 4 * nnz + 8 * n,
+        "k_rmq_prefix": 16 * n,
+        "k_iota": 4 * n,
+        "k_rmq_query": 45 * n,
+        "k_last_cc_cross": B * (n + 1) + 8 * nnz + nnz // 8 + 8 * n,
+        "k_heads": 12 * n,
+        "k_label_count": 12 * n,
+        "k_ap_keys": 13 * n,
+        "k_key_bits": 16 * n,
+        "k_scan_popc": nnz // 4,
+        "k_rank": 16 * n,
+        "k_fo": 25 * n,
+        "k_edge_out": B * (n + 1) + 4 * nnz + nnz // 8 + 8 * nnz + 4 * nnz + nnz,
+    }
+    return table.get(kernel)
+
+
+def load_traffic(kernel: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, or None when absent
+    or when the kernel's source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernel") == kernel and kv.get("workload") == workload:
+            src = os.path.join(ROOT, "paper_2301_01356_gb300", "csrc", kv.get("file", ""))
+            if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] != kv.get("sha"):
+                return None
+            return int(float(kv["bytes_per_launch"]))
+    return None
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import ht
+    fn, _, desc = WORKLOADS[args.workload]
+    g = fn()
+    ht.load()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ht.solve(g.offsets, g.adj)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    mean = sum(times) / len(times)
+    value = g.m / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "n": g.n, "m": g.m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the full {args.workload} graph per step (single-threaded Hopcroft-Tarjan)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(g, runs: int = 3):
+    from oracle import ht
+    ht.load()
+    res, ts = None, []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        res = ht.solve(g.offsets, g.adj)
+        ts.append(time.perf_counter() - t0)
+    return res, statistics.median(ts)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_2301_01356_gb300 import fbcc
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
+    torch.cuda.set_device(local)
+    fn, off64, desc = WORKLOADS[args.workload]
+    g = fn()
+    n, nnz, m = g.n, g.nnz, g.m
+    off_np = g.offsets.astype(np.int64 if off64 else np.int32)
+    off = torch.from_numpy(off_np).cuda()
+    adj = torch.from_numpy(g.adj).cuda()
+    solver = fbcc.Solver(n, nnz, ruler_stride=args.ruler_stride)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also builds the captured graph)
+    for _ in range(args.warmup):
+        solver.enqueue(off, adj)
+    torch.cuda.synchronize()
+    st = solver.stats.as_dict()
+    if st["device_status"] != 0:
+        raise SystemExit(f"device status {st['device_status']} in warm-up")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()                      # evict the previous step's data from L2
+        ev[i][0].record(stream)
+        solver.enqueue(off, adj)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    # keep the GPU busy a little longer so the clock sampler brackets the region
+    t_end = time.time() + 0.3
+    while time.time() < t_end:
+        solver.enqueue(off, adj)
+        torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_s = sum(step_ms) / 1e3
+    max_s = max_over_ranks(total_s, world)
+    value = whole_job_rate(m, args.steps, world, max_s)
+    ms_sorted = sorted(step_ms)
+    p50 = ms_sorted[len(ms_sorted) // 2]
+    p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
+
+    # per-kernel times (profiled solves: an event after every kernel)
+    solver.configure(ruler_stride=args.ruler_stride, profile=1)
+    prof = {}
+    launches_per_step = 0
+    for _ in range(args.profile_steps):
+        flush.zero_()
+        solver.enqueue(off, adj)
+        rows = fbcc.fbcc_profile(solver.ws)
+        launches_per_step = len(rows)
+        for name, ms in rows:
+            tot, cnt = prof.get(name, (0.0, 0))
+            prof[name] = (tot + ms, cnt + 1)
+    torch.cuda.synchronize()
+    solver.configure(ruler_stride=args.ruler_stride)
+    kernels = {k: {"ms_per_step": t / args.profile_steps, "launches_per_step": c // args.profile_steps,
+                   "ms_per_launch": t / c} for k, (t, c) in prof.items()}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    peak, peak_kind = measured_peak_gbs()
+    ab = algorithmic_bytes(dom, n, nnz, st["n_cc"], off_np.itemsize, args.ruler_stride)
+    achieved = ab / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9 if ab else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": load_traffic(dom, args.workload),
+                "algorithmic_bytes_per_launch": ab, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "ms_per_launch": kernels[dom]["ms_per_launch"]}
+
+    # end to end through the public host API: pinned host in, pinned host out
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    h_off, h_adj = pin(off_np), pin(g.adj)
+    h_eb = torch.empty(nnz, dtype=torch.int32).pin_memory().numpy()
+    h_bh = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    h_ap = torch.empty(n, dtype=torch.uint8).pin_memory().numpy()
+    h_br = torch.empty(nnz, dtype=torch.uint8).pin_memory().numpy()
+    for _ in range(2):
+        fbcc.fbcc_solve_host(h_off, h_adj, h_eb, h_bh, h_ap, h_br, solver.ws)
+    e2e_ts = []
+    barrier(world)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        hs = fbcc.fbcc_solve_host(h_off, h_adj, h_eb, h_bh, h_ap, h_br, solver.ws)
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_max = max_over_ranks(sum(e2e_ts), world)
+    h2d = h_off.nbytes + h_adj.nbytes
+    d2h = h_eb.nbytes + h_br.nbytes + h_ap.nbytes + 4 * hs.n_bcc + ctypes.sizeof(fbcc.fbcc_stats)
+
+    # parity of the benchmarked configuration and the CPU baseline (rank 0 only)
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        exp, cpu_s = cpu_baseline(g)
+        got = {"edge_bcc": h_eb, "bcc_head": h_bh[:hs.n_bcc], "is_ap": h_ap, "is_bridge": h_br,
+               "n_bcc": hs.n_bcc, "n_ap": hs.n_ap, "n_bridge": hs.n_bridge, "n_cc": hs.n_cc}
+        parity = all(np.array_equal(np.asarray(got[k]), np.asarray(exp[k])) for k in got)
+        cpu = {"value": m / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the full {args.workload} graph, median of 3 single-threaded Hopcroft-Tarjan runs "
+                         f"({cpu_s:.2f} s each)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "n": n, "m": m, "parallelism": f"replicas{world}",
+                   "l2": "flushed between timed steps (256 MiB write)", "ruler_stride": args.ruler_stride,
+                   "p50_ms": p50, "p99_ms": p99},
+        "e2e": {"value": whole_job_rate(m, args.steps, world, e2e_max), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max * 1e3 / args.steps,
+                "api": "fbcc_solve_host (pinned host buffers)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "parity_vs_oracle": parity,
+        "stats": {k: st[k] for k in ("n_bcc", "n_ap", "n_bridge", "n_cc")},
+        "kernels": {k: round(v["ms_per_step"], 4) for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms_per_step"])},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="grid4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="fbcc", choices=("fbcc", "reference"))
+    ap.add_argument("--ruler-stride", type=int, default=16)
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -158,6 +158,12 @@ def workload_grid_4096() -> Graph:
     return grid(4096, 4096, p=0.62, extra_frac=0.001, max_l1=8, seed=2)
 
 
+def workload_grid_2896() -> Graph:
+    """The same recipe as workload_grid_4096 on a 2896 x 2896 grid (half the vertices);
+    used for detailed profiler captures."""
+    return grid(2896, 2896, p=0.62, extra_frac=0.001, max_l1=8, seed=2)
+
+
 def workload_rmat_24() -> Graph:
     """R-MAT scale 24, edge factor 16, (a,b,c) = (0.57, 0.19, 0.19), seed 3."""
     return rmat(24, 16, 0.57, 0.19, 0.19, 3)
