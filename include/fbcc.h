@@ -138,6 +138,29 @@ fbcc_status fbcc_solve_batch(int32_t n_graphs, const int64_t *vtx_base, const in
                              int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
                              fbcc_stats *stats, fbcc_workspace *ws, void *stream);
 
+/*
+ * fbcc_solve for small graphs without allocating anything (the paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, such as code
+ * under an allocator or memory pool that forbids it, plugin hosts that own all
+ * device memory, or paths that cannot afford an allocation's synchronisation).
+ * The scratch is a fixed 8 MiB static device array inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   Limits: n <= 32768 vertices and 2m <= 262144 arcs; larger graphs return
+ *   FBCC_E_WORKSPACE without launching anything.
+ *   Arguments: as fbcc_solve, except `stats_dev`, a DEVICE pointer to one
+ *   fbcc_stats (or NULL) filled by a device-to-device copy on `stream`.
+ *   Set-up: the first call on each device looks up that device's copy of the
+ *   array (cudaGetSymbolAddress) with the device current; make that first call
+ *   before any stream capture.
+ *   Sharing: all calls use the same array and every call re-initialises what it
+ *   needs; calls that overlap on the GPU (other streams, other threads) race on
+ *   it and must be serialised by the caller.
+ */
+fbcc_status fbcc_solve_noalloc(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
+                               int64_t n, int64_t m,
+                               int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
+                               fbcc_stats *stats_dev, void *stream);
+
 /* Device bytes fbcc_solve_batch needs beyond the inputs and outputs (for admission). */
 size_t fbcc_batch_workspace_bytes(int64_t n_total, int64_t nnz_total, int32_t n_graphs);
 

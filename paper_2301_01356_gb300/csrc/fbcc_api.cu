@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "fbcc_internal.cuh"
@@ -592,5 +593,70 @@ extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *nam
     else return FBCC_E_INVALID;
     API_CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     API_CK(cudaMemcpy(host_dst, src, size_t(count) * elem, cudaMemcpyDeviceToHost), "debug copy");
+    return FBCC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solve with no allocation at all: the workspace lives in a fixed device array.
+//
+// For callers that must not allocate device memory themselves or through us:
+// code running under an allocator or memory pool that forbids cudaMalloc,
+// plugin hosts that own every byte of device memory, latency-critical paths
+// where an allocation's implicit synchronisation is not acceptable. They pass
+// their inputs and outputs; the scratch is kNoAllocBytes of static device memory
+// that every GPU loading this library keeps until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 1 << 15;     // vertices
+constexpr int64_t kNoAllocMaxNnz = 1 << 18;   // arcs (2m)
+constexpr size_t kNoAllocBytes = size_t(8) << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+char *g_noalloc_base[kNoAllocMaxDevices];  // device address of g_noalloc_scratch, per device
+
+}  // namespace
+
+extern "C" fbcc_status fbcc_solve_noalloc(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
+                                          int64_t n, int64_t m, int32_t *edge_bcc, int32_t *bcc_head,
+                                          uint8_t *is_ap, uint8_t *is_bridge, fbcc_stats *stats_dev, void *stream)
+{
+    if (n < 0 || m < 0) return FBCC_E_INVALID;
+    if (n > kNoAllocMaxN || 2 * m > kNoAllocMaxNnz) return FBCC_E_WORKSPACE;
+    int dev = 0;
+    API_CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return FBCC_E_INVALID;
+    char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_base[dev]) {
+            // host code may not use g_noalloc_scratch as an address: ask the runtime
+            // for the device address of this device's copy (once per device)
+            void *p = nullptr;
+            API_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+            g_noalloc_base[dev] = static_cast<char *>(p);
+        }
+        base = g_noalloc_base[dev];
+    }
+    fbcc_workspace ws;  // host-side view only: no allocation, no stream, no graph
+    ws.cfg = default_config();
+    ws.cfg.use_graph = -1;
+    if (carve(ws.d, nullptr, kNoAllocMaxN, kNoAllocMaxNnz) > kNoAllocBytes) return FBCC_E_WORKSPACE;
+    carve(ws.d, base, kNoAllocMaxN, kNoAllocMaxNnz);
+    fbcc_status st = check_args(csr_offsets, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, &ws);
+    if (st != FBCC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = offsets_64
+        ? enqueue_solve<int64_t>(&ws, (const int64_t *)csr_offsets, csr_adj, n, m, edge_bcc, bcc_head, is_ap,
+                                 is_bridge, s)
+        : enqueue_solve<int32_t>(&ws, (const int32_t *)csr_offsets, csr_adj, n, m, edge_bcc, bcc_head, is_ap,
+                                 is_bridge, s);
+    API_CK(e, "enqueue (no-alloc)");
+    if (stats_dev)
+        API_CK(cudaMemcpyAsync(stats_dev, ws.d.stats, sizeof(fbcc_stats), cudaMemcpyDeviceToDevice, s),
+               "stats copy");
     return FBCC_OK;
 }

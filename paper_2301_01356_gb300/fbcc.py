@@ -22,7 +22,7 @@ FBCC_OK, FBCC_E_INVALID, FBCC_E_NOT_SIMPLE, FBCC_E_OOM, FBCC_E_CUDA, FBCC_E_ITER
 # Every entry point include/fbcc.h declares (checked by the tests).
 EXPORTS = (
     "fbcc_workspace_bytes", "fbcc_workspace_create", "fbcc_workspace_destroy", "fbcc_workspace_configure",
-    "fbcc_solve", "fbcc_solve_host", "fbcc_solve_batch", "fbcc_batch_workspace_bytes", "fbcc_validate",
+    "fbcc_solve", "fbcc_solve_host", "fbcc_solve_noalloc", "fbcc_solve_batch", "fbcc_batch_workspace_bytes", "fbcc_validate",
     "fbcc_profile_count", "fbcc_profile_get", "fbcc_debug_read", "fbcc_status_string", "fbcc_last_cuda_error",
 )
 
@@ -78,6 +78,8 @@ def load(path: str = LIB_PATH):
             f = getattr(lib, name)
             f.argtypes = [P, INT, P, I64, I64, P, P, P, P, S, P, P]
             f.restype = INT
+        lib.fbcc_solve_noalloc.argtypes = [P, INT, P, I64, I64, P, P, P, P, P, P]
+        lib.fbcc_solve_noalloc.restype = INT
         lib.fbcc_solve_batch.argtypes = [I32, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.fbcc_solve_batch.restype = INT
         lib.fbcc_batch_workspace_bytes.argtypes = [I64, I64, I32]
@@ -144,6 +146,16 @@ def fbcc_solve(offsets, adj, n: int, m: int, edge_bcc, bcc_head, is_ap, is_bridg
     _check(load().fbcc_solve(_ptr(offsets), off64, _ptr(adj), n, m, _ptr(edge_bcc), _ptr(bcc_head), _ptr(is_ap),
                              _ptr(is_bridge), ctypes.byref(stats), ws, _stream_handle(stream)), "fbcc_solve")
     return stats
+
+
+def fbcc_solve_noalloc(offsets, adj, n: int, m: int, edge_bcc, bcc_head, is_ap, is_bridge, stats_dev=None,
+                       stream=None) -> int:
+    """Small-graph solve that allocates nothing (scratch in a static device array);
+    ``stats_dev`` is a device tensor of at least 40 bytes or None. Returns the status."""
+    import torch
+    return int(load().fbcc_solve_noalloc(_ptr(offsets), int(offsets.dtype == torch.int64), _ptr(adj), n, m,
+                                         _ptr(edge_bcc), _ptr(bcc_head), _ptr(is_ap), _ptr(is_bridge),
+                                         _ptr(stats_dev), _stream_handle(stream)))
 
 
 def fbcc_solve_host(offsets: np.ndarray, adj: np.ndarray, edge_bcc: np.ndarray, bcc_head: np.ndarray,
