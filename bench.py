@@ -262,7 +262,8 @@ def run_gpu(args, world, rank, local):
     off_np = g.offsets.astype(np.int64 if off64 else np.int32)
     off = torch.from_numpy(off_np).cuda()
     adj = torch.from_numpy(g.adj).cuda()
-    solver = fbcc.Solver(n, nnz, ruler_stride=args.ruler_stride)
+    cfg = dict(ruler_stride=args.ruler_stride, cc_sample=args.cc_sample)
+    solver = fbcc.Solver(n, nnz, **cfg)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -302,7 +303,7 @@ def run_gpu(args, world, rank, local):
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
 
     # per-kernel times (profiled solves: an event after every kernel)
-    solver.configure(ruler_stride=args.ruler_stride, profile=1)
+    solver.configure(profile=1, **cfg)
     prof = {}
     launches_per_step = 0
     for _ in range(args.profile_steps):
@@ -314,7 +315,7 @@ def run_gpu(args, world, rank, local):
             tot, cnt = prof.get(name, (0.0, 0))
             prof[name] = (tot + ms, cnt + 1)
     torch.cuda.synchronize()
-    solver.configure(ruler_stride=args.ruler_stride)
+    solver.configure(**cfg)
     kernels = {k: {"ms_per_step": t / args.profile_steps, "launches_per_step": c // args.profile_steps,
                    "ms_per_launch": t / c} for k, (t, c) in prof.items()}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
@@ -362,6 +363,7 @@ def run_gpu(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {desc}", "n": n, "m": m, "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MiB write)", "ruler_stride": args.ruler_stride,
+                   "cc_sample": args.cc_sample,
                    "p50_ms": p50, "p99_ms": p99},
         "e2e": {"value": whole_job_rate(m, args.steps, world, e2e_max), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max * 1e3 / args.steps,
@@ -387,6 +389,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="grid4096", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="fbcc", choices=("fbcc", "reference"))
     ap.add_argument("--ruler-stride", type=int, default=16)
+    ap.add_argument("--cc-sample", type=int, default=0, help="First-CC: neighbours hooked per vertex before the full pass")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

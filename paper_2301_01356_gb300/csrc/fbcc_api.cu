@@ -113,6 +113,13 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.vbits = c.take<uint8_t>(N);
     d.low = c.take<int32_t>(N);
     d.high = c.take<int32_t>(N);
+    d.lp = c.take<int32_t>(N);
+    d.ext = c.take<uint8_t>(N);
+    d.qlist = c.take<int32_t>(N);
+    d.vplab = c.take<int32_t>(N);
+    d.fin = c.take<int32_t>(N);
+    d.minorig = c.take<int32_t>(N);
+    d.smin = c.take<int32_t>(N);
     d.head = c.take<int32_t>(N);
     d.nh = c.take<int32_t>(N);
     d.key = c.take<unsigned long long>(N);

@@ -185,18 +185,80 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
 }
 
 // ---------------------------------------------------------------------------
-// Last-CC: cross edges. The tree edges are skipped by their tree bit; a non-tree
-// arc u->w with first[w] > first[u] is a back edge iff first[w] <= last[u] (u is
-// an ancestor of w; Algorithm 1, Back) and a cross edge otherwise. Arcs with
-// first[w] < first[u] are left to the reverse arc, where the comparison is made
-// from the endpoint that comes first in preorder.
+// Last-CC (Algorithm 1, step 4) on the skeleton G' = plain tree edges + cross
+// edges, by preorder number.
+//  1. plain components: the low/high kernel left lp[p] = parent position for a
+//     plain edge, flattened inside each 1024-position tile; positions referenced
+//     from another tile (ext) are compacted and resolved by pointer doubling;
+//  2. cross edges: union-find over the plain components' roots (hook the larger
+//     position under the smaller); tree arcs are skipped by their tree bit, and a
+//     non-tree arc u->w with first[w] > first[u] is a back edge iff first[w] <=
+//     last[u] (u an ancestor of w; Algorithm 1, Back), a cross edge otherwise;
+//     arcs with first[w] < first[u] are left to the reverse arc;
+//  3. every position's final root, the smallest vertex id of each component and
+//     the label of every vertex: the id of its component's top vertex.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_ext_compact(int64_t n, const uint8_t *__restrict__ ext, int32_t *qlist,
+                                                          long long *nq)
+{
+    __shared__ int32_t warp_cnt[kThreads / 32];
+    __shared__ long long block_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n_pad = (n + kThreads - 1) / kThreads * kThreads;
+    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * kThreads) {
+        const bool on = p < n && ext[p];
+        const unsigned mask = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) warp_cnt[wid] = __popc(mask);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t t = 0;
+            for (int w = 0; w < kThreads / 32; ++w) t += warp_cnt[w];
+            block_base = t ? (long long)atomicAdd((unsigned long long *)nq, (unsigned long long)t) : 0;
+        }
+        __syncthreads();
+        int32_t before = 0;
+        for (int w = 0; w < wid; ++w) before += warp_cnt[w];
+        if (on) qlist[block_base + before + __popc(mask & ((1u << lane) - 1u))] = (int32_t)p;
+        __syncthreads();
+    }
+}
+
+// One pointer-doubling round over the cross-tile positions (in place).
+__global__ void __launch_bounds__(kThreads) k_ext_jump(const long long *__restrict__ nq_p,
+                                                       const int32_t *__restrict__ qlist, int32_t *lp)
+{
+    const int64_t nq = *nq_p;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nq; i += (int64_t)gridDim.x * kThreads) {
+        const int32_t q = qlist[i];
+        const int32_t t = ld_cg(lp + q);
+        const int32_t u = ld_cg(lp + t);
+        if (u != t) lp[q] = u;
+    }
+}
+
+__device__ __forceinline__ int32_t plain_root(const int32_t *lp, int64_t p)
+{
+    const int32_t t = lp[p];
+    return t < (p & ~(int64_t)(kRmqTile - 1)) ? lp[t] : t;
+}
+
+// Plain-component root of every vertex (by vertex), and a fresh union-find.
+__global__ void __launch_bounds__(kThreads) k_plain_label(int64_t n, const int32_t *__restrict__ lp,
+                                                          const int32_t *__restrict__ ord, int32_t *vplab, int32_t *uf)
+{
+    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads) {
+        vplab[ord[p]] = plain_root(lp, p);
+        uf[p] = (int32_t)p;
+    }
+}
+
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                             int64_t nnz, const int32_t *__restrict__ tile_v,
                                                             int64_t ntiles, const uint32_t *__restrict__ tree_bits,
                                                             const int32_t *__restrict__ first,
-                                                            const int32_t *__restrict__ last, int32_t *uf, int *err,
+                                                            const int32_t *__restrict__ last,
+                                                            const int32_t *__restrict__ vplab, int32_t *uf, int *err,
                                                             bool vec)
 {
     __shared__ OffT win[kOffWin];
@@ -207,17 +269,59 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
         uint32_t tb = arc_tile_treebits(tree_bits, at.a0);
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
-        int32_t cur = -1, ls = 0;
+        int32_t cur = -1, ls = 0, ps = 0;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             if (j >= at.cnt || ((tb >> j) & 1u)) continue;
             if (at.src[j] != cur) {
                 cur = at.src[j];
                 ls = __ldg(last + cur);
+                ps = __ldg(vplab + cur);
             }
-            int32_t fd = __ldg(first + d[j]);
-            if (fd > ls) uf_unite(uf, cur, d[j], err);
+            const int32_t fd = __ldg(first + d[j]);
+            const int32_t pd = __ldg(vplab + d[j]);
+            if (fd > ls && pd != ps) uf_unite(uf, ps, pd, err);
         }
+    }
+}
+
+// Final root of every position and the smallest vertex id of every component.
+// Lanes with the same root reduce first; a read of the current minimum (stale
+// values only cost an extra atomic) filters most of the remaining atomics.
+__global__ void __launch_bounds__(kThreads) k_final_label(int64_t n, const int32_t *__restrict__ lp,
+                                                          const int32_t *uf, const int32_t *__restrict__ ord,
+                                                          const int32_t *__restrict__ porig, int32_t *fin,
+                                                          int32_t *minorig)
+{
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * kThreads) {
+        int32_t r = -1, v = INT32_MAX;
+        if (p < n) {
+            r = uf_root(uf, plain_root(lp, p));
+            fin[p] = r;
+            if (porig[p] >= 0) v = ord[p];
+            else r = -1;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, r);
+        const int32_t m = (int32_t)__reduce_min_sync(peers, (unsigned)v);
+        if (r >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1 && m < minorig[r]) atomicMin(minorig + r, m);
+    }
+}
+
+// Label of every vertex: the id of its component's top vertex (roots: their own).
+__global__ void __launch_bounds__(kThreads) k_lab_out(int64_t n, const int32_t *__restrict__ fin,
+                                                      const int32_t *__restrict__ ord, const int32_t *__restrict__ porig,
+                                                      const int32_t *__restrict__ minorig, int32_t *lab, int32_t *smin)
+{
+    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads) {
+        const int32_t v = ord[p];
+        if (porig[p] < 0) {
+            lab[v] = v;
+            continue;
+        }
+        const int32_t r = fin[p];
+        lab[v] = ord[r];
+        if (r == p) smin[v] = minorig[r];
     }
 }
 
@@ -225,13 +329,32 @@ template <typename OffT>
 cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, const Launch &L)
 {
+    cudaError_t e;
+#define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
     const int64_t ntiles = ceil_div(nnz, kTile);
-    if (nnz > 0)
+    const int gv = grid_for(L, ceil_div(n, kThreads));
+    long long *nq = d.counters + 2;
+    CK(cudaMemsetAsync(nq, 0, sizeof(long long), L.s));
+    k_ext_compact<<<gv, kThreads, 0, L.s>>>(n, d.ext, d.qlist, nq);
+    L.mark("k_ext_compact");
+    const int rounds = jump_rounds(ceil_div(n, kRmqTile));
+    for (int i = 0; i < rounds; ++i) {
+        k_ext_jump<<<gv, kThreads, 0, L.s>>>(nq, d.qlist, d.lp);
+        L.mark("k_ext_jump");
+    }
+    k_plain_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.ord, d.vplab, d.uf);
+    L.mark("k_plain_label");
+    if (nnz > 0) {
         k_last_cc_cross<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
-                                                                        d.first, d.last, d.uf, d.err, vec);
+                                                                        d.first, d.last, d.vplab, d.uf, d.err, vec);
         L.mark("k_last_cc_cross");
-    k_uf_compress<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(d.uf, n);
-    L.mark("k_uf_compress");
+    }
+    CK(cudaMemsetAsync(d.minorig, 0x7f, n * sizeof(int32_t), L.s));
+    k_final_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.uf, d.ord, d.porig, d.fin, d.minorig);
+    L.mark("k_final_label");
+    k_lab_out<<<gv, kThreads, 0, L.s>>>(n, d.fin, d.ord, d.porig, d.minorig, d.uf, d.smin);
+    L.mark("k_lab_out");
+#undef CK
     return cudaGetLastError();
 }
 

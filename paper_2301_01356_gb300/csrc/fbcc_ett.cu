@@ -108,22 +108,34 @@ __global__ void __launch_bounds__(kThreads) k_tour_cut(int64_t n, const int32_t 
 }
 
 // Rulers: tour heads and every arc whose index is a multiple of the stride.
-// link[s] = {succ[s], ruler id or -1}; relem[id] = s.
+// link[s] = {succ[s], ruler id or -1}; relem[id] = s. Ids come from one atomic
+// per CTA and iteration (a per-warp atomic on a single counter serialises).
 __global__ void __launch_bounds__(kThreads) k_rulers(const int32_t *__restrict__ toff, int64_t n, int stride,
                                                      const int32_t *__restrict__ succ,
                                                      const uint8_t *__restrict__ is_head, int2 *link, int32_t *relem,
                                                      long long *nr)
 {
+    __shared__ int32_t warp_cnt[kThreads / 32];
+    __shared__ long long block_base;
     const int64_t A = toff[n];
-    const int64_t A_pad = (A + 31) & ~31ll;  // whole warps take part in the ballot
+    const int64_t A_pad = (A + kThreads - 1) / kThreads * kThreads;  // whole CTAs take part
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t s = blockIdx.x * (int64_t)kThreads + threadIdx.x; s < A_pad; s += (int64_t)gridDim.x * kThreads) {
-        bool in = s < A;
-        bool ruler = in && (is_head[s] || (s & (stride - 1)) == 0);
-        unsigned mask = __ballot_sync(0xffffffffu, ruler);
-        int lane = threadIdx.x & 31;
-        long long base = 0;
-        if (lane == 0 && mask) base = atomicAdd((unsigned long long *)nr, (unsigned long long)__popc(mask));
-        base = __shfl_sync(0xffffffffu, base, 0);
+        const bool in = s < A;
+        const bool ruler = in && (is_head[s] || (s & (stride - 1)) == 0);
+        const unsigned mask = __ballot_sync(0xffffffffu, ruler);
+        if (lane == 0) warp_cnt[wid] = __popc(mask);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t t = 0;
+            for (int w = 0; w < kThreads / 32; ++w) t += warp_cnt[w];
+            block_base = t ? (long long)atomicAdd((unsigned long long *)nr, (unsigned long long)t) : 0;
+        }
+        __syncthreads();
+        int32_t before = 0;
+        for (int w = 0; w < wid; ++w) before += warp_cnt[w];
+        const long long base = block_base + before;
+        __syncthreads();  // warp_cnt / block_base are rewritten next iteration
         if (!in) continue;
         int32_t id = -1;
         if (ruler) {

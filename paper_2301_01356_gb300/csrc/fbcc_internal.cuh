@@ -71,6 +71,14 @@ struct Dev {
     int32_t *tmin, *tmax;     // sparse tables over RMQ tiles: st_levels x rmq_tiles_max
     uint8_t *vbits;           // per vertex: bit0 = tree edge to parent is a bridge
     int32_t *low, *high;      // low/high by preorder number (written by profiled solves only)
+    // Last-CC by preorder number
+    int32_t *lp;              // plain-component pointer (root: itself), flattened in place
+    uint8_t *ext;             // position referenced across an RMQ tile
+    int32_t *qlist;           // compacted positions with ext set
+    int32_t *vplab;           // plain-component root of every vertex (by vertex)
+    int32_t *fin;             // final skeleton-component root of every position
+    int32_t *minorig;         // smallest vertex id of the component rooted at position r
+    int32_t *smin;            // by label vertex: smallest vertex id of its label class
     // Last-CC and outputs
     int32_t *head;            // head of label L at [L]
     int32_t *nh;              // number of labels a vertex heads
@@ -226,29 +234,46 @@ __device__ __forceinline__ long long scan_tile_exclusive(long long (&v)[kItems],
         agg += warp_tot[i];
     }
     long long texcl = wexcl + inc - run;
-    if (threadIdx.x == 0) {
+    // Look-back by warp 0: each step inspects 32 predecessors at once and adds
+    // the aggregates up to the nearest published prefix.
+    if (wid == 0) {
         long long excl = 0;
         if (tile == 0) {
-            atomicExch((unsigned long long *)(status + tile), (unsigned long long)(kFlagPre | (uint64_t)agg));
+            if (lane == 0)
+                atomicExch((unsigned long long *)(status + tile), (unsigned long long)(kFlagPre | (uint64_t)agg));
         } else {
-            atomicExch((unsigned long long *)(status + tile), (unsigned long long)(kFlagAgg | (uint64_t)agg));
+            if (lane == 0)
+                atomicExch((unsigned long long *)(status + tile), (unsigned long long)(kFlagAgg | (uint64_t)agg));
             int64_t j = tile - 1;
             int spins = 0;
-            while (j >= 0) {
-                uint64_t s = *(volatile uint64_t *)(status + j);
-                uint64_t f = s & ~kValMask;
-                if (f == 0) {
-                    if (++spins > kLookbackCap) { atomicOr(err, kErrLookback); break; }
+            while (true) {
+                const int64_t idx = j - lane;
+                uint64_t st = 2ull << 62;  // before tile 0: an empty published prefix
+                if (idx >= 0) st = *(volatile uint64_t *)(status + idx);
+                const uint64_t f = st & ~kValMask;
+                const unsigned pre = __ballot_sync(0xffffffffu, f == kFlagPre);
+                const unsigned zero = __ballot_sync(0xffffffffu, f == 0);
+                // lanes 0..stop are the window: up to and including the nearest prefix
+                const int stop = pre ? __ffs(pre) - 1 : 31;
+                const unsigned window = stop == 31 ? 0xffffffffu : ((1u << (stop + 1)) - 1u);
+                if (zero & window) {
+                    if (++spins > kLookbackCap) {
+                        if (lane == 0) atomicOr(err, kErrLookback);
+                        break;
+                    }
                     continue;
                 }
-                excl += (long long)(s & kValMask);
-                if (f == kFlagPre) break;
-                --j;
+                long long v = ((window >> lane) & 1u) ? (long long)(st & kValMask) : 0;
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                excl += v;
+                if (pre) break;
+                j -= 32;
             }
-            atomicExch((unsigned long long *)(status + tile),
-                       (unsigned long long)(kFlagPre | (uint64_t)(excl + agg)));
+            if (lane == 0)
+                atomicExch((unsigned long long *)(status + tile),
+                           (unsigned long long)(kFlagPre | (uint64_t)(excl + agg)));
         }
-        tile_excl = excl;
+        if (lane == 0) tile_excl = excl;
     }
     __syncthreads();
     long long base = tile_excl + texcl;

@@ -1,8 +1,8 @@
 // Heads and outputs (Algorithm 1, the component-head loop after Last-CC; section
 // 4.2 for why it is right).
 //
-// After Last-CC every non-root vertex v has a label l[v] (the smallest vertex of
-// its skeleton component). For each v with l[v] != l[p(v)], p(v) is the head of
+// After Last-CC every non-root vertex v has a label l[v] (the top vertex of its
+// skeleton component). For each v with l[v] != l[p(v)], p(v) is the head of
 // label l[v]; every such writer of one label stores the same vertex (head lemma,
 // section 4.2). Label l's BCC is {v : l[v] = l} plus its head.
 //
@@ -15,10 +15,11 @@
 //  - a tree edge p(v)-v is a bridge iff no edge leaves T_v (flag from tagging);
 //  - canonical BCC numbers: the key of a BCC is its smallest arc id with
 //    src < dst, which orders BCCs exactly like their smallest edge ids. Its source
-//    is u0 = min(l, head(l)) (the BCC's smallest vertex). If u0 lies in this BCC
+//    is u0 = min(smin(l), head(l)) (the BCC's smallest vertex). If u0 lies in this BCC
 //    only, the key is u0's first arc; otherwise u0's list is scanned for the arcs
 //    of this BCC. Keys are set in a bitmap over arcs whose popcount prefix gives
-//    each BCC its rank.
+//    each BCC its rank. (A label is the id of its class's top vertex; smin[l]
+//    holds the class's smallest vertex id.)
 #include "fbcc_internal.cuh"
 
 namespace fbcc {
@@ -59,6 +60,7 @@ template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__restrict__ off,
                                                       const int32_t *__restrict__ parent, const int32_t *__restrict__ lab,
                                                       const int32_t *__restrict__ head, const int32_t *__restrict__ nh,
+                                                      const int32_t *__restrict__ smin,
                                                       uint8_t *is_ap, unsigned long long *key, uint8_t *scanv,
                                                       fbcc_stats *stats, int *err)
 {
@@ -74,7 +76,8 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
         if (root || lab[v] != v) continue;
         const int32_t hd = head[v];
         if (!in_range(hd, n, err)) continue;
-        const int32_t u0 = hd < v ? hd : (int32_t)v;
+        const int32_t sm = smin[v];
+        const int32_t u0 = hd < sm ? hd : sm;
         const int32_t in_bccs = (parent[u0] >= 0) + nh[u0];
         if (in_bccs == 1) {
             key[v] = (unsigned long long)off[u0];
@@ -95,7 +98,8 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
                                                        const uint8_t *__restrict__ scanv,
                                                        const int32_t *__restrict__ first,
                                                        const int32_t *__restrict__ lab,
-                                                       const int32_t *__restrict__ head, unsigned long long *key,
+                                                       const int32_t *__restrict__ head,
+                                                       const int32_t *__restrict__ smin, unsigned long long *key,
                                                        bool vec)
 {
     __shared__ OffT win[kOffWin];
@@ -130,8 +134,8 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
             const int32_t l = __ldg(lab + x);
             if (l == last_l) continue;  // a later arc of the same BCC cannot be smaller
             last_l = l;
-            const int32_t hd = __ldg(head + l);
-            if ((hd < l ? hd : l) == u) atomicMin(key + l, (unsigned long long)(at.a0 + j));
+            const int32_t hd = __ldg(head + l), sm = __ldg(smin + l);
+            if ((hd < sm ? hd : sm) == u) atomicMin(key + l, (unsigned long long)(at.a0 + j));
         }
     }
 }
@@ -311,12 +315,12 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_heads");
     k_label_count<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.head, d.nh, d.stats, d.err);
     L.mark("k_label_count");
-    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.parent, d.uf, d.head, d.nh, is_ap, d.key, d.scanv, d.stats, d.err);
+    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.parent, d.uf, d.head, d.nh, d.smin, is_ap, d.key, d.scanv, d.stats, d.err);
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
         k_key_scan<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.first,
-                                                                   d.uf, d.head, d.key, vec);
+                                                                   d.uf, d.head, d.smin, d.key, vec);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
         k_key_bits<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.key, d.key_bits, nnz, d.err);

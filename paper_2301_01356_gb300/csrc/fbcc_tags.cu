@@ -142,8 +142,12 @@ __global__ void __launch_bounds__(kThreads) k_rmq_level(int64_t ntiles, int j, i
     }
 }
 
-// low/high for every position, the fence and bridge tests, and the Last-CC union
-// of every plain tree edge.
+// low/high for every position, the fence and bridge tests, and the start of
+// Last-CC: every plain tree edge v-p(v) becomes the pointer lp[pos(v)] = pos(p(v))
+// (fence edges and roots point to themselves), so each plain component is a tree
+// of pointers to smaller preorder numbers whose root is its top vertex. Chains
+// inside the tile are flattened in shared memory (pointer doubling); a pointer that
+// leaves the tile marks its target in `ext` for the cross-tile resolution.
 __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t *__restrict__ w1,
                                                         const int32_t *__restrict__ w2, const int32_t *__restrict__ pmin,
                                                         const int32_t *__restrict__ pmax, const int32_t *__restrict__ tmin,
@@ -151,8 +155,8 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                                                         const int32_t *__restrict__ ord, const int32_t *__restrict__ lastp,
                                                         const int32_t *__restrict__ porig,
                                                         const int32_t *__restrict__ first,
-                                                        const int32_t *__restrict__ last, uint8_t *vbits, int32_t *uf,
-                                                        int32_t *low_out, int32_t *high_out, int *err)
+                                                        const int32_t *__restrict__ last, uint8_t *vbits, int32_t *lp,
+                                                        uint8_t *ext, int32_t *low_out, int32_t *high_out, int *err)
 {
     constexpr int kPer = kRmqTile / kThreads;
     constexpr int kNChunk = kRmqTile / kChunk;
@@ -161,6 +165,7 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
     __shared__ int32_t suf1[kRmqTile], suf2[kRmqTile];      // suffix within the chunk
     __shared__ int32_t c1[kNChunk], c2[kNChunk];            // chunk extrema
     __shared__ int32_t cs1[kNChunk], cs2[kNChunk];          // suffix over chunks (tile suffix helper)
+    __shared__ int32_t sp[kRmqTile];                        // plain pointers of the tile
     const int64_t ntiles = (n + kRmqTile - 1) / kRmqTile;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -246,22 +251,44 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                 high_out[p] = hi;
             }
             const int32_t v = ord[p], x = porig[p];
-            if (!in_range(v, n, err) || x >= n) continue;
-            uint8_t bits = 0;
-            if (x >= 0) {
-                if (lo == (int32_t)p && hi <= e) bits |= 1;  // bridge: nothing leaves T_v
-                const bool fence = __ldg(first + x) <= lo && __ldg(last + x) >= hi;
-                if (fence) bits |= 2;
-                else uf_unite(uf, v, x, err);                  // plain tree edge: in G'
+            int32_t ptr = (int32_t)p;
+            if (in_range(v, n, err) && x < n) {
+                uint8_t bits = 0;
+                if (x >= 0) {
+                    if (lo == (int32_t)p && hi <= e) bits |= 1;  // bridge: nothing leaves T_v
+                    const int32_t fx = __ldg(first + x);
+                    const bool fence = fx <= lo && __ldg(last + x) >= hi;
+                    if (fence) bits |= 2;
+                    else ptr = fx;                                // plain tree edge: in G'
+                }
+                vbits[v] = bits;
             }
-            vbits[v] = bits;
+            sp[i] = ptr;
+        }
+        for (int i = threadIdx.x; i < kRmqTile; i += kThreads)
+            if (base + i >= n) sp[i] = (int32_t)(base + i);
+        __syncthreads();
+        // pointer doubling inside the tile (10 rounds cover 1024 positions); pointers
+        // only move towards their root, so updating in place is safe
+        for (int r = 0; r < 10; ++r) {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int i = threadIdx.x + k * kThreads;
+                const int32_t t = sp[i];
+                if (t >= base) sp[i] = sp[t - base];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * kThreads;
+            const int64_t p = base + i;
+            if (p >= n) continue;
+            const int32_t t = sp[i];
+            lp[p] = t;
+            if (t < base) ext[t] = 1;
         }
     }
-}
-
-__global__ void __launch_bounds__(kThreads) k_iota(int32_t *a, int64_t n)
-{
-    GRID_STRIDE(i, n) a[i] = (int32_t)i;
 }
 
 template <typename OffT>
@@ -269,10 +296,11 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
                            bool vec, bool keep_low_high, const Launch &L)
 {
     const int64_t ntiles = ceil_div(nnz, kTile);
-    if (nnz > 0)
+    if (nnz > 0) {
         k_w12<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits, d.first,
                                                               d.w1, d.w2, n, d.err, vec);
         L.mark("k_w12");
+    }
     const int64_t rt = ceil_div(n, kRmqTile);
     k_rmq_prefix<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax);
     L.mark("k_rmq_prefix");
@@ -281,13 +309,12 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
                                                                                  d.tmax);
         L.mark("k_rmq_level");
     }
-    // Last-CC starts here: a fresh union-find that the query kernel fills with the
-    // plain tree edges.
-    k_iota<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(d.uf, n);
-    L.mark("k_iota");
+    // Last-CC starts here: plain-edge pointers by preorder number
+    cudaError_t e = cudaMemsetAsync(d.ext, 0, n, L.s);
+    if (e != cudaSuccess) return e;
     k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax,
                                                        d.rmq_tiles_max, d.ord, d.lastp, d.porig, d.first, d.last,
-                                                       d.vbits, d.uf, keep_low_high ? d.low : nullptr,
+                                                       d.vbits, d.lp, d.ext, keep_low_high ? d.low : nullptr,
                                                        keep_low_high ? d.high : nullptr, d.err);
     L.mark("k_rmq_query");
     return cudaGetLastError();
