@@ -262,7 +262,8 @@ def run_gpu(args, world, rank, local):
     off_np = g.offsets.astype(np.int64 if off64 else np.int32)
     off = torch.from_numpy(off_np).cuda()
     adj = torch.from_numpy(g.adj).cuda()
-    cfg = dict(ruler_stride=args.ruler_stride, cc_sample=args.cc_sample)
+    cfg = dict(ruler_stride=args.ruler_stride, cc_sample=args.cc_sample, chase_chains=args.chase_chains,
+               cc_local=args.cc_local)
     solver = fbcc.Solver(n, nnz, **cfg)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -363,7 +364,7 @@ def run_gpu(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {desc}", "n": n, "m": m, "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MiB write)", "ruler_stride": args.ruler_stride,
-                   "cc_sample": args.cc_sample,
+                   "cc_sample": args.cc_sample, "chase_chains": args.chase_chains, "cc_local": args.cc_local,
                    "p50_ms": p50, "p99_ms": p99},
         "e2e": {"value": whole_job_rate(m, args.steps, world, e2e_max), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max * 1e3 / args.steps,
@@ -390,6 +391,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="fbcc", choices=("fbcc", "reference"))
     ap.add_argument("--ruler-stride", type=int, default=16)
     ap.add_argument("--cc-sample", type=int, default=0, help="First-CC: neighbours hooked per vertex before the full pass")
+    ap.add_argument("--chase-chains", type=int, default=1, help="list ranking: walks per thread (1, 2, 4)")
+    ap.add_argument("--cc-local", type=int, default=0, help="First-CC: shared-memory range in vertices (0 = off)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

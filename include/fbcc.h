@@ -72,6 +72,9 @@ typedef struct {
     int32_t grid_ctas;     /* CTAs of the persistent grid-stride kernels */
     int32_t use_graph;     /* 1 = replay a captured CUDA graph for repeated identical calls (default), -1 = never */
     int32_t profile;       /* 1 = record a CUDA event after every kernel (no graph); see fbcc_profile_get */
+    int32_t chase_chains;  /* list ranking: walks a thread advances together (1, 2 or 4) */
+    int32_t cc_local;      /* First-CC: unite inside ranges of this many consecutive vertex ids in
+                              shared memory first (power of 2, 1024..16384; 0 = off) */
 } fbcc_config;
 
 /* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds. */
@@ -143,7 +146,7 @@ fbcc_status fbcc_solve_batch(int32_t n_graphs, const int64_t *vtx_base, const in
  * counterpart: this serves callers that cannot call cudaMalloc, such as code
  * under an allocator or memory pool that forbids it, plugin hosts that own all
  * device memory, or paths that cannot afford an allocation's synchronisation).
- * The scratch is a fixed 8 MiB static device array inside the library, which
+ * The scratch is a fixed 12 MiB static device array inside the library, which
  * every GPU that loads the library holds until the process exits.
  *   Limits: n <= 32768 vertices and 2m <= 262144 arcs; larger graphs return
  *   FBCC_E_WORKSPACE without launching anything.
@@ -190,7 +193,7 @@ fbcc_status fbcc_profile_get(const fbcc_workspace *ws, int32_t i, const char **n
  *   "low", "high"              low/high by preorder number (only when the solve
  *                              ran with fbcc_config.profile = 1)
  *   "tree_u", "tree_v"         forest edge recorded at the vertex it hooked (-1: none)
- *   "ord", "lastp", "porig"    vertex, last[] and parent vertex (-1: root) by preorder number
+ *   "ord", "porig"             vertex and parent vertex (-1: root) by preorder number
  *   "vbits" (uint8)            bit 0: the tree edge to the parent is a bridge;
  *                              bit 1: it is a fence edge
  *   "err" (count 1)            the device error bits of the last solve

@@ -77,7 +77,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.uf = c.take<int32_t>(N);
     d.te_u = c.take<int32_t>(N);
     d.te_v = c.take<int32_t>(N);
-    d.tile_v = c.take<int32_t>(ceil_div(Z, kTile) + 2);
+    d.tile_v = c.take<int32_t>(ceil_div(Z, kWTile) + 2);
     d.tree_bits = c.take<uint32_t>(words);
     d.tdeg = c.take<int32_t>(N + 1);
     d.toff = c.take<int32_t>(N + 1);
@@ -87,22 +87,27 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.is_head = c.take<uint8_t>(2 * N);
     d.link = c.take<int2>(2 * N);
     d.relem = c.take<int32_t>(d.ruler_max);
-    d.owner = c.take<int32_t>(2 * N);
-    d.offs = c.take<int32_t>(2 * N);
+    d.oo = c.take<int2>(2 * N);
+    d.tsrc = c.take<int32_t>(2 * N);
     for (int i = 0; i < 2; ++i) {
         d.rnext[i] = c.take<int32_t>(d.ruler_max);
         d.rval[i] = c.take<int32_t>(d.ruler_max);
     }
     d.rlen = c.take<int32_t>(d.ruler_max);
+    d.rnx1 = c.take<int32_t>(d.ruler_max);
+    d.l2 = c.take<int2>(d.ruler_max);
+    d.relem2 = c.take<int32_t>(d.ruler_max);
+    d.owner2 = c.take<int32_t>(d.ruler_max);
+    d.offs2 = c.take<int32_t>(d.ruler_max);
+    d.sd1 = c.take<int32_t>(d.ruler_max);
     d.csize = c.take<int32_t>(N + 1);
     d.vbase = c.take<int32_t>(N + 1);
     d.pos = c.take<int32_t>(2 * N);
-    d.tour = c.take<int32_t>(2 * N);
+    d.rec = c.take<int2>(2 * N);
     d.first = c.take<int32_t>(N);
     d.last = c.take<int32_t>(N);
     d.parent = c.take<int32_t>(N);
     d.ord = c.take<int32_t>(N);
-    d.lastp = c.take<int32_t>(N);
     d.porig = c.take<int32_t>(N);
     d.w1 = c.take<int32_t>(N);
     d.w2 = c.take<int32_t>(N);
@@ -160,6 +165,8 @@ static fbcc_config default_config()
     c.grid_ctas = 0;
     c.use_graph = 1;
     c.profile = 0;
+    c.chase_chains = 1;
+    c.cc_local = 0;
     return c;
 }
 
@@ -232,6 +239,17 @@ fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
         c.grid_ctas = cfg->grid_ctas;
         if (cfg->use_graph) c.use_graph = cfg->use_graph;
         c.profile = cfg->profile > 0;
+        if (cfg->cc_local) {
+            if (cfg->cc_local < 1024 || cfg->cc_local > 16384 || (cfg->cc_local & (cfg->cc_local - 1)))
+                return FBCC_E_INVALID;
+            cudaError_t e = prepare_cc_local(cfg->cc_local);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            c.cc_local = cfg->cc_local;
+        }
+        if (cfg->chase_chains) {
+            if (cfg->chase_chains != 1 && cfg->chase_chains != 2 && cfg->chase_chains != 4) return FBCC_E_INVALID;
+            c.chase_chains = cfg->chase_chains;
+        }
     }
     ws->cfg = c;
     return FBCC_OK;
@@ -302,8 +320,8 @@ cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *ad
     CK(cudaMemsetAsync(d.stats, 0, sizeof(fbcc_stats), s));
     if (n > 0) {
         CK(cudaMemsetAsync(d.tree_bits, 0, (ceil_div(nnz, 32) + 1) * sizeof(uint32_t), s));
-        CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, vec, L));
-        CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, L));
+        CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, ws->cfg.cc_local, vec, L));
+        CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, ws->cfg.chase_chains, L));
         CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, ws->cfg.profile != 0, L));
         CK(launch_last_cc<OffT>(d, off, adj, n, nnz, vec, L));
         CK(launch_outputs<OffT>(d, off, adj, n, nnz, vec, edge_bcc, bcc_head, is_ap, is_bridge, B, L));
@@ -593,7 +611,6 @@ extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *nam
     else if (!strcmp(name, "tree_u")) src = d.te_u;
     else if (!strcmp(name, "tree_v")) src = d.te_v;
     else if (!strcmp(name, "ord")) src = d.ord;
-    else if (!strcmp(name, "lastp")) src = d.lastp;
     else if (!strcmp(name, "porig")) src = d.porig;
     else if (!strcmp(name, "err")) { src = d.err; if (count > 1) return FBCC_E_INVALID; }
     else if (!strcmp(name, "vbits")) { src = d.vbits; elem = 1; }
@@ -617,7 +634,7 @@ namespace {
 
 constexpr int64_t kNoAllocMaxN = 1 << 15;     // vertices
 constexpr int64_t kNoAllocMaxNnz = 1 << 18;   // arcs (2m)
-constexpr size_t kNoAllocBytes = size_t(8) << 20;
+constexpr size_t kNoAllocBytes = size_t(12) << 20;
 constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];

@@ -13,7 +13,7 @@
 
 namespace fbcc {
 
-// tile_v[t] = source of arc t*kTile; tile_v[ntiles] = source of the last arc.
+// tile_v[t] = source of arc t*kWTile; tile_v[ntiles] = source of the last arc.
 // Also resets the union-find and the tree-edge record.
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_init(const OffT *__restrict__ off, int64_t n, int64_t nnz,
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) k_cc_init(const OffT *__restrict__ o
         te_u[v] = -1;
         int64_t b = off[v], e = off[v + 1];
         if (e > b) {
-            for (int64_t t = (b + kTile - 1) / kTile; t * kTile < e; ++t) tile_v[t] = (int32_t)v;
+            for (int64_t t = (b + kWTile - 1) / kWTile; t * kWTile < e; ++t) tile_v[t] = (int32_t)v;
             if (b <= nnz - 1 && nnz - 1 < e) tile_v[ntiles] = (int32_t)v;
         }
     }
@@ -38,10 +38,11 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook(const OffT *__restrict__ o
                                                       int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
                                                       int32_t *uf, int32_t *te_u, int32_t *te_v, int *err, bool vec)
 {
-    __shared__ OffT win[kOffWin];
+    __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        arc_tile_sources(off, nnz, tile_v, t, win, at);
+    const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
+        arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
         if (!at.cnt) continue;
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
@@ -85,11 +86,12 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_skip(const OffT *__restric
                                                            int64_t ntiles, int32_t *uf, int32_t *te_u, int32_t *te_v,
                                                            const int32_t *big, int *err, bool vec)
 {
-    __shared__ OffT win[kOffWin];
+    __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
     const int32_t root = *big;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        arc_tile_sources(off, nnz, tile_v, t, win, at);
+    const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
+        arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
         if (!at.cnt) continue;
         bool any = false;
         int32_t rs[kItems];
@@ -152,17 +154,140 @@ __global__ void __launch_bounds__(kThreads) k_cc_pick_big(int32_t *uf, int64_t n
     }
 }
 
+// Local-first variant: each CTA owns a range of V consecutive vertex ids and
+// unites the edges inside the range in shared memory (graphs whose ids follow
+// their geometry, such as grids or meshes, keep most edges inside a range); the
+// range's sets then enter the global union-find flattened, and only edges
+// between ranges are hooked globally.
+constexpr int kLocalThreads = 512;
+
+__device__ __forceinline__ int32_t sm_find(int32_t *par, int32_t v)
+{
+    while (true) {
+        int32_t p = par[v];
+        if (p == v) return v;
+        int32_t gp = par[p];
+        if (gp == p) return p;
+        par[v] = gp;
+        v = gp;
+    }
+}
+
+template <typename OffT>
+__global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restrict__ off,
+                                                            const int32_t *__restrict__ adj, int64_t n, int V,
+                                                            int32_t *uf, int32_t *te_u, int32_t *te_v, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    OffT *woff = reinterpret_cast<OffT *>(smem);                       // V+1 offsets
+    int32_t *par = reinterpret_cast<int32_t *>(smem + (size_t)(V + 1) * sizeof(OffT) + 8);
+    const int64_t nranges = (n + V - 1) / V;
+    for (int64_t g = blockIdx.x; g < nranges; g += gridDim.x) {
+        const int64_t v0 = g * V;
+        const int cnt = (int)((n - v0) < V ? (n - v0) : V);
+        __syncthreads();
+        for (int i = threadIdx.x; i <= cnt; i += kLocalThreads) {
+            woff[i] = off[v0 + i];
+            if (i < cnt) par[i] = i;
+        }
+        __syncthreads();
+        const int64_t a_beg = woff[0], a_end = woff[cnt];
+        // each thread takes runs of kItems consecutive arcs
+        for (int64_t a0 = a_beg + (int64_t)threadIdx.x * kItems; a0 < a_end; a0 += (int64_t)kLocalThreads * kItems) {
+            int lo = 0, hi = cnt - 1;   // the vertex whose list holds a0
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if ((int64_t)woff[mid] <= a0) lo = mid; else hi = mid - 1;
+            }
+            for (int64_t a = a0; a < a0 + kItems && a < a_end; ++a) {
+                while ((int64_t)woff[lo + 1] <= a) ++lo;
+                const int32_t w = adj[a];
+                const int64_t lw = (int64_t)w - v0;
+                if (lw <= lo || lw >= cnt) continue;   // u < w inside the range only
+                int32_t ru = sm_find(par, lo), rv = sm_find(par, (int32_t)lw);
+                for (int it = 0; it < kUniteCap && ru != rv; ++it) {
+                    const int32_t h = ru > rv ? ru : rv, l = ru > rv ? rv : ru;
+                    const int32_t old = atomicCAS(par + h, h, l);
+                    if (old == h) {
+                        te_u[v0 + h] = (int32_t)(v0 + lo);
+                        te_v[v0 + h] = w;
+                        break;
+                    }
+                    ru = sm_find(par, old);
+                    rv = sm_find(par, l);
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += kLocalThreads) {
+            int32_t r = i;
+            while (par[r] != r) r = par[r];
+            uf[v0 + i] = (int32_t)(v0 + r);
+        }
+    }
+    (void)err;
+}
+
+// Global hooks of the edges between ranges.
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restrict__ off,
+                                                            const int32_t *__restrict__ adj, int64_t nnz,
+                                                            const int32_t *__restrict__ tile_v, int64_t ntiles, int V,
+                                                            int32_t *uf, int32_t *te_u, int32_t *te_v, int *err,
+                                                            bool vec)
+{
+    __shared__ OffT win[kCtaWin];
+    ArcTile<OffT> at;
+    const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
+        arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
+        if (!at.cnt) continue;
+        int32_t d[kItems];
+        arc_tile_targets(adj, at.a0, at.cnt, vec, d);
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            if (j >= at.cnt || at.src[j] >= d[j] || at.src[j] / V == d[j] / V) continue;
+            int32_t r = uf_unite(uf, at.src[j], d[j], err);
+            if (r >= 0) {
+                te_u[r] = at.src[j];
+                te_v[r] = d[j];
+            }
+        }
+    }
+}
+
+size_t cc_local_smem(int V, bool off64) { return (size_t)(V + 1) * (off64 ? 8 : 4) + 8 + (size_t)V * 4; }
+
+cudaError_t prepare_cc_local(int V)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_cc_local<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cc_local_smem(V, false));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cc_local<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cc_local_smem(V, true));
+    return e;
+}
+
 template <typename OffT>
 cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                            int cc_sample, bool vec, const Launch &L)
+                            int cc_sample, int cc_local, bool vec, const Launch &L)
 {
-    const int64_t ntiles = ceil_div(nnz, kTile);
+    const int64_t ntiles = ceil_div(nnz, kWTile);
     const int gv = grid_for(L, ceil_div(n, kThreads));
-    const int ga = grid_for(L, ntiles);
+    const int ga = grid_for(L, ceil_div(ntiles, kWarpsPerCta));
     k_cc_init<OffT><<<gv, kThreads, 0, L.s>>>(off, n, nnz, d.tile_v, ntiles, d.uf, d.te_u);
     L.mark("k_cc_init");
     if (nnz > 0) {
-        if (cc_sample > 0) {
+        if (cc_local > 0) {
+            const int64_t nr = ceil_div(n, cc_local);
+            const int gl = (int)(nr < L.grid ? nr : L.grid);
+            k_cc_local<OffT><<<gl, kLocalThreads, cc_local_smem(cc_local, sizeof(OffT) == 8), L.s>>>(
+                off, adj, n, cc_local, d.uf, d.te_u, d.te_v, d.err);
+            L.mark("k_cc_local");
+            k_cc_hook_cross<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, cc_local, d.uf, d.te_u,
+                                                           d.te_v, d.err, vec);
+            L.mark("k_cc_hook_cross");
+        } else if (cc_sample > 0) {
             int32_t *big = reinterpret_cast<int32_t *>(d.counters + 8);
             k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, d.err);
             L.mark("k_cc_sample");
@@ -261,10 +386,11 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
                                                             const int32_t *__restrict__ vplab, int32_t *uf, int *err,
                                                             bool vec)
 {
-    __shared__ OffT win[kOffWin];
+    __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        arc_tile_sources(off, nnz, tile_v, t, win, at);
+    const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
+        arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
         if (!at.cnt) continue;
         uint32_t tb = arc_tile_treebits(tree_bits, at.a0);
         int32_t d[kItems];
@@ -331,7 +457,7 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
 {
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-    const int64_t ntiles = ceil_div(nnz, kTile);
+    const int64_t ntiles = ceil_div(nnz, kWTile);
     const int gv = grid_for(L, ceil_div(n, kThreads));
     long long *nq = d.counters + 2;
     CK(cudaMemsetAsync(nq, 0, sizeof(long long), L.s));
@@ -345,7 +471,7 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
     k_plain_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.ord, d.vplab, d.uf);
     L.mark("k_plain_label");
     if (nnz > 0) {
-        k_last_cc_cross<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
+        k_last_cc_cross<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
                                                                         d.first, d.last, d.vplab, d.uf, d.err, vec);
         L.mark("k_last_cc_cross");
     }
@@ -359,9 +485,9 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
 }
 
 template cudaError_t launch_first_cc<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
-                                              bool, const Launch &);
+                                              int, bool, const Launch &);
 template cudaError_t launch_first_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,
-                                              bool, const Launch &);
+                                              int, bool, const Launch &);
 template cudaError_t launch_last_cc<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, bool,
                                              const Launch &);
 template cudaError_t launch_last_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, bool,

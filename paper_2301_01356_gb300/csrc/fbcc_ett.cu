@@ -15,8 +15,8 @@
 //     chases pointers between them; the GPU takes many more rulers so that every
 //     thread has a short walk);
 //  4. preorder: an arc is a down arc iff it precedes its twin in the tour; a prefix
-//     count of down arcs over tour positions numbers the vertices in preorder, and
-//     the distance between a vertex's down and up arcs gives its subtree size.
+//     count of down arcs over tour positions numbers the vertices in preorder: the
+//     down arc into v gives first[v], the up arc leaving v gives last[v].
 // Tours are laid out at positions [2*base, 2*base + 2*size) of their component
 // (base = preorder number of the root); the last two slots are padding, one of
 // which counts 1 so that the prefix count restarts at each component's base.
@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(kThreads) k_tree_count(const OffT *__restrict_
 
 __global__ void __launch_bounds__(kThreads) k_tree_fill(int64_t n, const int32_t *__restrict__ te_u,
                                                         const int32_t *__restrict__ te_v, const int32_t *__restrict__ toff,
-                                                        int32_t *cursor, int32_t *tadj, int32_t *twin, int *err)
+                                                        int32_t *cursor, int32_t *tadj, int32_t *tsrc, int32_t *twin,
+                                                        int *err)
 {
     GRID_STRIDE(h, n)
     {
@@ -72,6 +73,8 @@ __global__ void __launch_bounds__(kThreads) k_tree_fill(int64_t n, const int32_t
         if (!in_range(su, toff[u + 1], err) || !in_range(sv, toff[v + 1], err)) continue;
         tadj[su] = v;
         tadj[sv] = u;
+        tsrc[su] = u;
+        tsrc[sv] = v;
         twin[su] = sv;
         twin[sv] = su;
     }
@@ -146,33 +149,156 @@ __global__ void __launch_bounds__(kThreads) k_rulers(const int32_t *__restrict__
     }
 }
 
-// Each ruler walks its successors until the next ruler or the tour's end.
+// Each ruler walks its successors until the next ruler or the tour's end. A
+// thread advances kChains rulers' walks in lock step, so it keeps that many
+// independent loads in flight (the walk is bound by load latency).
+template <int kChains>
 __global__ void __launch_bounds__(kThreads) k_chase(const int32_t *__restrict__ toff, int64_t n,
                                                     const long long *__restrict__ nr_p, const int32_t *__restrict__ relem,
-                                                    const int2 *__restrict__ link, int32_t *owner, int32_t *offs,
-                                                    int32_t *rnext, int32_t *rval, int32_t *rlen, int *err)
+                                                    const int2 *__restrict__ link, int2 *oo, int32_t *rnext,
+                                                    int32_t *rlen, int *err)
 {
     const int64_t A = toff[n];
     const int64_t nr = *nr_p;
-    GRID_STRIDE(r, nr)
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    for (int64_t r0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; r0 < nr; r0 += T * kChains) {
+        int32_t t[kChains], acc[kChains], nxr[kChains];
+        int64_t steps = 0;
+        unsigned live = 0;
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) {
+            const int64_t r = r0 + k * T;
+            acc[k] = 1;
+            nxr[k] = -1;
+            t[k] = -1;
+            if (r < nr) {
+                const int32_t s = relem[r];
+                oo[s] = make_int2((int32_t)r, 0);
+                t[k] = link[s].x;
+                if (t[k] >= 0) live |= 1u << k;
+            }
+        }
+        while (live) {
+            int2 lk[kChains];
+#pragma unroll
+            for (int k = 0; k < kChains; ++k)
+                if ((live >> k) & 1u) lk[k] = link[t[k]];
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) {
+                if (!((live >> k) & 1u)) continue;
+                if (lk[k].y >= 0) {
+                    nxr[k] = lk[k].y;
+                    live &= ~(1u << k);
+                    continue;
+                }
+                oo[t[k]] = make_int2((int32_t)(r0 + k * T), acc[k]++);
+                t[k] = lk[k].x;
+                if (t[k] < 0) live &= ~(1u << k);
+            }
+            if (++steps > A) {
+                atomicOr(err, kErrChase);
+                break;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) {
+            const int64_t r = r0 + k * T;
+            if (r < nr) {
+                rnext[r] = nxr[k];
+                rlen[r] = acc[k];
+            }
+        }
+    }
+}
+
+// Level 2 of the ranking: the ruler lists themselves are sampled again. A ruler
+// list of one ruler (a short tour) is finished already (marked -2); the others'
+// heads and every stride2-th ruler become level-2 rulers.
+__global__ void __launch_bounds__(kThreads) k_rulers2(const long long *__restrict__ nr_p, int stride2,
+                                                      const int32_t *__restrict__ relem,
+                                                      const uint8_t *__restrict__ is_head,
+                                                      const int32_t *__restrict__ rnext1, int2 *l2, int32_t *relem2,
+                                                      long long *nr2)
+{
+    __shared__ int32_t warp_cnt[kThreads / 32];
+    __shared__ long long block_base;
+    const int64_t nr = *nr_p;
+    const int64_t pad = (nr + kThreads - 1) / kThreads * kThreads;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t r = blockIdx.x * (int64_t)kThreads + threadIdx.x; r < pad; r += (int64_t)gridDim.x * kThreads) {
+        const bool in = r < nr;
+        bool single = false, ruler = false;
+        int32_t nx = -1;
+        if (in) {
+            const bool head = is_head[relem[r]];
+            nx = rnext1[r];
+            single = head && nx < 0;
+            ruler = !single && (head || (r & (stride2 - 1)) == 0);
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, ruler);
+        if (lane == 0) warp_cnt[wid] = __popc(mask);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t c = 0;
+            for (int w = 0; w < kThreads / 32; ++w) c += warp_cnt[w];
+            block_base = c ? (long long)atomicAdd((unsigned long long *)nr2, (unsigned long long)c) : 0;
+        }
+        __syncthreads();
+        int32_t before = 0;
+        for (int w = 0; w < wid; ++w) before += warp_cnt[w];
+        const long long base = block_base + before;
+        __syncthreads();
+        if (!in) continue;
+        int32_t id = single ? -2 : -1;
+        if (ruler) {
+            id = (int32_t)(base + __popc(mask & ((1u << lane) - 1u)));
+            relem2[id] = (int32_t)r;
+        }
+        l2[r] = make_int2(nx, id);
+    }
+}
+
+// Level-2 walks over the level-1 ruler lists, weighted by segment length.
+__global__ void __launch_bounds__(kThreads) k_chase2(const long long *__restrict__ nr_p,
+                                                     const long long *__restrict__ nr2_p,
+                                                     const int32_t *__restrict__ relem2, const int2 *__restrict__ l2,
+                                                     const int32_t *__restrict__ rw1, int32_t *owner2, int32_t *offs2,
+                                                     int32_t *rnext2, int32_t *rval2, int *err)
+{
+    const int64_t nr = *nr_p, nr2 = *nr2_p;
+    GRID_STRIDE(R, nr2)
     {
-        int32_t s = relem[r];
-        owner[s] = (int32_t)r;
-        offs[s] = 0;
-        int32_t acc = 1, nxr = -1;
-        int32_t t = link[s].x;
+        const int32_t r0 = relem2[R];
+        owner2[r0] = (int32_t)R;
+        offs2[r0] = 0;
+        int32_t acc = rw1[r0], nxr = -1;
+        int32_t t = l2[r0].x;
         int64_t steps = 0;
         while (t >= 0) {
-            int2 lk = link[t];
+            const int2 lk = l2[t];
             if (lk.y >= 0) { nxr = lk.y; break; }
-            owner[t] = (int32_t)r;
-            offs[t] = acc++;
+            owner2[t] = (int32_t)R;
+            offs2[t] = acc;
+            acc += rw1[t];
             t = lk.x;
-            if (++steps > A) { atomicOr(err, kErrChase); break; }
+            if (++steps > nr) { atomicOr(err, kErrChase); break; }
         }
-        rnext[r] = nxr;
-        rval[r] = acc;
-        rlen[r] = acc;
+        rnext2[R] = nxr;
+        rval2[R] = acc;
+    }
+}
+
+// Suffix weight of every level-1 ruler from the level-2 result.
+__global__ void __launch_bounds__(kThreads) k_expand2(const long long *__restrict__ nr_p, const int2 *__restrict__ l2,
+                                                      const int32_t *__restrict__ rw1,
+                                                      const int32_t *__restrict__ owner2,
+                                                      const int32_t *__restrict__ offs2,
+                                                      const int32_t *__restrict__ sd2, int32_t *sd1)
+{
+    const int64_t nr = *nr_p;
+    GRID_STRIDE(r, nr)
+    {
+        sd1[r] = l2[r].y == -2 ? rw1[r] : sd2[owner2[r]] - offs2[r];
     }
 }
 
@@ -219,100 +345,104 @@ __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t
 __global__ void __launch_bounds__(kThreads) k_place(const int32_t *__restrict__ toff, int64_t n,
                                                     const int32_t *__restrict__ tadj, const int32_t *__restrict__ uf,
                                                     const int32_t *__restrict__ csize, const int32_t *__restrict__ vbase,
-                                                    const int32_t *__restrict__ owner, const int32_t *__restrict__ offs,
-                                                    const int32_t *__restrict__ sd, int32_t *pos, int32_t *tour,
-                                                    int *err)
+                                                    const int2 *__restrict__ oo, const int32_t *__restrict__ sd,
+                                                    int32_t *pos, int *err)
 {
     const int64_t A = toff[n];
     GRID_STRIDE(s, A)
     {
-        int32_t r = uf[tadj[s]];
-        int32_t L = 2 * (csize[r] - 1);
-        int32_t dist = sd[owner[s]] - offs[s];
-        int32_t p = 2 * vbase[r] + L - dist;
-        pos[s] = p;
-        if (in_range(dist - 1, L, err)) tour[p] = (int32_t)s;
+        const int32_t r = uf[tadj[s]];
+        const int32_t L = 2 * (csize[r] - 1);
+        const int2 o = oo[s];
+        const int32_t dist = sd[o.x] - o.y;
+        pos[s] = in_range(dist - 1, L, err) ? 2 * vbase[r] + L - dist : -1;
+    }
+}
+
+// Tour record at every arc's position: a down arc (it precedes its reverse)
+// stores {child, parent}; an up arc stores {-1, the child it leaves}.
+__global__ void __launch_bounds__(kThreads) k_tour_records(const int32_t *__restrict__ toff, int64_t n,
+                                                           const int32_t *__restrict__ tadj,
+                                                           const int32_t *__restrict__ tsrc,
+                                                           const int32_t *__restrict__ twin,
+                                                           const int32_t *__restrict__ pos, int2 *rec)
+{
+    const int64_t A = toff[n];
+    GRID_STRIDE(s, A)
+    {
+        const int32_t p = pos[s], q = pos[twin[s]];
+        if (p < 0) continue;
+        rec[p] = p < q ? make_int2(tadj[s], tsrc[s]) : make_int2(-1, tsrc[s]);
     }
 }
 
 // Per component root: padding slots and the root's own tags.
 __global__ void __launch_bounds__(kThreads) k_root_tags(int64_t n, const int32_t *__restrict__ uf,
                                                         const int32_t *__restrict__ csize,
-                                                        const int32_t *__restrict__ vbase, int32_t *tour, int32_t *first,
-                                                        int32_t *last, int32_t *parent, int32_t *ord, int32_t *lastp,
-                                                        int32_t *porig, int32_t *w1, int32_t *w2)
+                                                        const int32_t *__restrict__ vbase, int2 *rec, int32_t *first,
+                                                        int32_t *last, int32_t *parent, int32_t *ord, int32_t *porig,
+                                                        int32_t *w1, int32_t *w2)
 {
     GRID_STRIDE(r, n)
     {
         if (uf[r] != r) continue;
         int32_t b = vbase[r], sz = csize[r];
-        tour[2 * b + 2 * sz - 2] = -2;
-        tour[2 * b + 2 * sz - 1] = -1;
+        rec[2 * b + 2 * sz - 2] = make_int2(-2, 0);   // counts: the prefix restarts at the next base
+        rec[2 * b + 2 * sz - 1] = make_int2(-3, 0);
         first[r] = b;
         last[r] = b + sz - 1;
         parent[r] = -1;
         ord[b] = (int32_t)r;
-        lastp[b] = b + sz - 1;
         porig[b] = -1;
         w1[b] = b;
         w2[b] = b;
     }
 }
 
-// Preorder from the tour (single-pass scan over the 2n tour positions).
-__global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int32_t *__restrict__ tour,
-                                                       const int32_t *__restrict__ pos, const int32_t *__restrict__ tadj,
-                                                       const int32_t *__restrict__ twin, int32_t *first, int32_t *last,
-                                                       int32_t *parent, int32_t *ord, int32_t *lastp, int32_t *porig,
+// Preorder from the tour (single-pass scan over the 2n tour positions). With S(p)
+// the number of counting positions before p: a down arc into v gives
+// first[v] = S(p) + 1, and the up arc leaving v gives last[v] = S(q).
+__global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *__restrict__ rec, int32_t *first,
+                                                       int32_t *last, int32_t *parent, int32_t *ord, int32_t *porig,
                                                        int32_t *w1, int32_t *w2, long long *ticket, uint64_t *status,
                                                        int *err)
 {
     const int64_t ntiles = (n2 + kTile - 1) / kTile;
+    const int64_t n = n2 / 2;
     while (true) {
         int64_t t = scan_ticket(ticket);
         if (t >= ntiles) return;
         const int64_t p0 = t * kTile + (int64_t)threadIdx.x * kItems;
         long long v[kItems];
-        int32_t arc[kItems], q[kItems];
+        int2 r[kItems];
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            int64_t p = p0 + j;
-            int32_t s = p < n2 ? tour[p] : -1;
-            if (s >= n2) { atomicOr(err, kErrIndex); s = -1; }
-            arc[j] = s;
-            q[j] = 0;
-            if (s >= 0) {
-                q[j] = pos[twin[s]];
-                v[j] = p < q[j];
-            } else {
-                v[j] = s == -2;
-            }
+            const int64_t p = p0 + j;
+            r[j] = p < n2 ? rec[p] : make_int2(-3, 0);
+            v[j] = r[j].x >= 0 || r[j].x == -2;
         }
         scan_tile_exclusive(v, t, status, err);
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            int64_t p = p0 + j;
-            int32_t s = arc[j];
-            if (s < 0 || p >= q[j]) continue;  // padding or an up arc
-            int32_t vtx = tadj[s], x = tadj[twin[s]];
-            int32_t fv = (int32_t)v[j] + 1;
-            int32_t lv = fv + (int32_t)((q[j] - p + 1) / 2) - 1;
-            if (!in_range(fv, n2 / 2, err) || !in_range(lv, n2 / 2, err)) continue;
-            first[vtx] = fv;
-            last[vtx] = lv;
-            parent[vtx] = x;
-            ord[fv] = vtx;
-            lastp[fv] = lv;
-            porig[fv] = x;
-            w1[fv] = fv;
-            w2[fv] = fv;
+            if (r[j].x >= 0) {
+                const int32_t vtx = r[j].x, x = r[j].y, fv = (int32_t)v[j] + 1;
+                if (!in_range(fv, n, err) || !in_range(vtx, n, err)) continue;
+                first[vtx] = fv;
+                parent[vtx] = x;
+                ord[fv] = vtx;
+                porig[fv] = x;
+                w1[fv] = fv;
+                w2[fv] = fv;
+            } else if (r[j].x == -1) {
+                if (in_range(r[j].y, n, err)) last[r[j].y] = (int32_t)v[j];
+            }
         }
     }
 }
 
 template <typename OffT>
 cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           int ruler_stride, const Launch &L)
+                           int ruler_stride, int chase_chains, const Launch &L)
 {
     (void)nnz;
     const int gv = grid_for(L, ceil_div(n, kThreads));
@@ -325,7 +455,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     CK(cudaGetLastError());
     CK(launch_scan_i32(d, d.tdeg, d.toff, n, L));
     CK(cudaMemsetAsync(d.tdeg, 0, (n + 1) * sizeof(int32_t), L.s));
-    k_tree_fill<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.toff, d.tdeg, d.tadj, d.twin, d.err);
+    k_tree_fill<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.toff, d.tdeg, d.tadj, d.tsrc, d.twin, d.err);
     L.mark("k_tree_fill");
     k_succ<<<ga, kThreads, 0, L.s>>>(2 * n, d.toff, n, d.tadj, d.twin, d.succ, d.is_head);
     L.mark("k_succ");
@@ -338,43 +468,59 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     // upper bound on the number of rulers: every tour head plus one per stride
     const int64_t rbound = n + ceil_div(2 * n, ruler_stride) + 1;
     const int gr = grid_for(L, ceil_div(rbound, kThreads));
-    k_chase<<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.owner, d.offs, d.rnext[0], d.rval[0],
-                                      d.rlen, d.err);
+    if (chase_chains >= 4)
+        k_chase<4><<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
+    else if (chase_chains == 2)
+        k_chase<2><<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
+    else
+        k_chase<1><<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
     L.mark("k_chase");
+    long long *nr2 = d.counters + 3;
+    CK(cudaMemsetAsync(nr2, 0, sizeof(long long), L.s));
+    k_rulers2<<<gr, kThreads, 0, L.s>>>(nr, kStride2, d.relem, d.is_head, d.rnx1, d.l2, d.relem2, nr2);
+    L.mark("k_rulers2");
+    // level-2 rulers: heads of lists with several rulers (each holds a stride
+    // sample, so at most 2n / stride of them) plus one in kStride2 rulers
+    const int64_t rbound2 = ceil_div(2 * n, ruler_stride) + ceil_div(rbound, kStride2) + 1;
+    const int gr2 = grid_for(L, ceil_div(rbound2, kThreads));
+    k_chase2<<<gr2, kThreads, 0, L.s>>>(nr, nr2, d.relem2, d.l2, d.rlen, d.owner2, d.offs2, d.rnext[0], d.rval[0],
+                                        d.err);
+    L.mark("k_chase2");
     int cur = 0;
-    const int rounds = jump_rounds(rbound);
+    const int rounds = jump_rounds(rbound2);
     for (int i = 0; i < rounds; ++i) {
-        k_jump<<<gr, kThreads, 0, L.s>>>(nr, d.rnext[cur], d.rval[cur], d.rnext[cur ^ 1], d.rval[cur ^ 1]);
+        k_jump<<<gr2, kThreads, 0, L.s>>>(nr2, d.rnext[cur], d.rval[cur], d.rnext[cur ^ 1], d.rval[cur ^ 1]);
         L.mark("k_jump");
         cur ^= 1;
     }
-    const int32_t *sd = d.rval[cur];
+    k_expand2<<<gr, kThreads, 0, L.s>>>(nr, d.l2, d.rlen, d.owner2, d.offs2, d.rval[cur], d.sd1);
+    L.mark("k_expand2");
+    const int32_t *sd = d.sd1;
     k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.toff, d.link, sd, nr, d.csize, d.err);
     L.mark("k_comp_size");
     CK(cudaGetLastError());
     CK(launch_scan_i32(d, d.csize, d.vbase, n, L));
-    CK(cudaMemsetAsync(d.tour, 0xff, 2 * n * sizeof(int32_t), L.s));
-    k_place<<<ga, kThreads, 0, L.s>>>(d.toff, n, d.tadj, d.uf, d.csize, d.vbase, d.owner, d.offs, sd, d.pos, d.tour,
-                                      d.err);
+    k_place<<<ga, kThreads, 0, L.s>>>(d.toff, n, d.tadj, d.uf, d.csize, d.vbase, d.oo, sd, d.pos, d.err);
     L.mark("k_place");
-    k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.tour, d.first, d.last, d.parent, d.ord,
-                                          d.lastp, d.porig, d.w1, d.w2);
+    k_tour_records<<<ga, kThreads, 0, L.s>>>(d.toff, n, d.tadj, d.tsrc, d.twin, d.pos, d.rec);
+    L.mark("k_tour_records");
+    k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.first, d.last, d.parent, d.ord,
+                                          d.porig, d.w1, d.w2);
     L.mark("k_root_tags");
     CK(cudaGetLastError());
     const int64_t ntiles = ceil_div(2 * n, kTile);
     CK(cudaMemsetAsync(d.counters, 0, sizeof(long long), L.s));
     CK(cudaMemsetAsync(d.scan_status, 0, ntiles * sizeof(uint64_t), L.s));
-    k_preorder<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(2 * n, d.tour, d.pos, d.tadj, d.twin, d.first, d.last,
-                                                           d.parent, d.ord, d.lastp, d.porig, d.w1, d.w2, d.counters,
-                                                           d.scan_status, d.err);
+    k_preorder<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(2 * n, d.rec, d.first, d.last, d.parent, d.ord, d.porig,
+                                                           d.w1, d.w2, d.counters, d.scan_status, d.err);
     L.mark("k_preorder");
 #undef CK
     return cudaGetLastError();
 }
 
 template cudaError_t launch_rooting<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
-                                             const Launch &);
+                                             int, const Launch &);
 template cudaError_t launch_rooting<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,
-                                             const Launch &);
+                                             int, const Launch &);
 
 }  // namespace fbcc

@@ -16,9 +16,9 @@ namespace fbcc {
 constexpr int kThreads = 256;                       // threads per CTA everywhere
 constexpr int kItems = 8;                           // consecutive items per thread
 constexpr int kTile = kThreads * kItems;            // 2048 items (arcs, positions) per CTA tile
-constexpr int kOffWin = kTile + 256;                // offsets cached in shared memory per arc tile
 constexpr int kRmqTile = 1024;                      // positions per low/high tile
 constexpr int kChunk = 32;                          // positions per in-tile RMQ chunk
+constexpr int kStride2 = 16;                        // level-2 ruler sampling stride
 
 // Device error bits (workspace error word); reported as FBCC_E_ITER_LIMIT.
 constexpr int kErrUnite = 1;      // union-find retry cap
@@ -50,21 +50,26 @@ struct Dev {
     int32_t *tdeg;            // tree degree, then fill cursor
     int32_t *toff;            // tree CSR offsets (n+1)
     int32_t *tadj, *twin;     // tree CSR targets and reverse-arc index (2n)
+    int32_t *tsrc;            // tree CSR source of every arc (2n)
     int32_t *succ;            // Euler-circuit successor (2n), -1 at a tour's end
     uint8_t *is_head;         // first arc of a tour (2n)
     int2 *link;               // {succ, ruler id or -1} per tree arc
     int32_t *relem;           // arc of ruler r
-    int32_t *owner, *offs;    // ruler owning each arc and the arc's distance from it
+    int2 *oo;                 // {ruler owning the arc, the arc's distance from it}
     int32_t *rnext[2], *rval[2];  // ruler list: next ruler and suffix weight (double buffered)
     int32_t *rlen;            // ruler segment length
+    int32_t *rnx1;            // next ruler in the tour (-1: last)
+    int2 *l2;                 // per ruler: {next ruler, level-2 ruler id, -1 none, -2 finished}
+    int32_t *relem2;          // level-1 ruler of level-2 ruler R
+    int32_t *owner2, *offs2;  // level-2 owner of every ruler and its weighted offset
+    int32_t *sd1;             // suffix length (arcs to the tour's end) from every ruler
     int32_t *csize;           // component size at its root, 0 elsewhere
     int32_t *vbase;           // first preorder number of the component at its root
     int32_t *pos;             // tour position of every tree arc
-    int32_t *tour;            // tree arc at every tour position (-1/-2: padding)
+    int2 *rec;                // tour record at every position (down/up arc, padding)
     // Tagging (first/last/parent indexed by vertex; the rest by preorder number)
     int32_t *first, *last, *parent;
     int32_t *ord;             // vertex at preorder number p
-    int32_t *lastp;           // last[] at preorder number p
     int32_t *porig;           // parent vertex of the vertex at preorder number p (-1 root)
     int32_t *w1, *w2;         // w1/w2 at preorder number p
     int32_t *pmin, *pmax;     // in-tile prefix min/max of w1/w2
@@ -283,32 +288,38 @@ __device__ __forceinline__ long long scan_tile_exclusive(long long (&v)[kItems],
 }
 
 // ---------------------------------------------------------------------------
-// Arc tiles: CTA tile t covers arcs [t*kTile, (t+1)*kTile); thread i covers the
-// kItems consecutive arcs starting at t*kTile + i*kItems. The source vertex of
-// every arc comes from the tile's window of offsets, staged in shared memory.
-// tile_v[t] is the source of the tile's first arc, tile_v[ntiles] that of the
-// graph's last arc.
+// Arc tiles, one per warp: warp tile w covers arcs [w*kWTile, (w+1)*kWTile); lane
+// i covers the kItems consecutive arcs starting at w*kWTile + i*kItems. The
+// source vertex of every arc comes from the tile's window of offsets, staged in
+// the warp's slice of shared memory. Warps never wait for each other, so a lane
+// stuck in a long union-find walk only holds back its own warp. tile_v[w] is the
+// source of the tile's first arc, tile_v[nwt] that of the graph's last arc.
 // ---------------------------------------------------------------------------
+constexpr int kWTile = 32 * kItems;                 // 256 arcs per warp tile
+constexpr int kWarpWin = kWTile + 32;               // offsets cached per warp tile
+constexpr int kWarpsPerCta = kThreads / 32;
+
 template <typename OffT>
 struct ArcTile {
-    int64_t a0;        // first arc of this thread
-    int cnt;           // arcs of this thread (0..kItems)
+    int64_t a0;        // first arc of this lane
+    int cnt;           // arcs of this lane (0..kItems)
     int32_t src[kItems];
 };
 
 template <typename OffT>
 __device__ __forceinline__ void arc_tile_sources(const OffT *__restrict__ off, int64_t nnz,
-                                                 const int32_t *__restrict__ tile_v, int64_t t,
+                                                 const int32_t *__restrict__ tile_v, int64_t w,
                                                  OffT *win, ArcTile<OffT> &at)
 {
-    const int32_t vlo = tile_v[t], vhi = tile_v[t + 1];
+    const int lane = threadIdx.x & 31;
+    const int32_t vlo = tile_v[w], vhi = tile_v[w + 1];
     const int64_t wn = (int64_t)vhi - vlo + 2;  // off[vlo .. vhi+1]
-    const bool sm = wn <= kOffWin;
-    __syncthreads();
+    const bool sm = wn <= kWarpWin;
+    __syncwarp();
     if (sm)
-        for (int64_t i = threadIdx.x; i < wn; i += kThreads) win[i] = off[vlo + i];
-    __syncthreads();
-    at.a0 = t * (int64_t)kTile + (int64_t)threadIdx.x * kItems;
+        for (int64_t i = lane; i < wn; i += 32) win[i] = off[vlo + i];
+    __syncwarp();
+    at.a0 = w * (int64_t)kWTile + (int64_t)lane * kItems;
     at.cnt = 0;
     if (at.a0 >= nnz) return;
     at.cnt = (int)((nnz - at.a0) < kItems ? (nnz - at.a0) : kItems);
@@ -332,6 +343,52 @@ __device__ __forceinline__ void arc_tile_sources(const OffT *__restrict__ off, i
         at.src[j] = vlo + (int32_t)lo;
     }
 }
+
+// The same for a whole CTA tile of kTile arcs (kWarpsPerCta consecutive warp
+// tiles): one shared window, loaded by the CTA. The union-find passes use it.
+constexpr int kCtaWin = kTile + 256;
+
+template <typename OffT>
+__device__ __forceinline__ void arc_cta_tile_sources(const OffT *__restrict__ off, int64_t nnz,
+                                                     const int32_t *__restrict__ tile_v, int64_t nwt, int64_t t,
+                                                     OffT *win, ArcTile<OffT> &at)
+{
+    const int64_t w0 = t * kWarpsPerCta, w1 = (w0 + kWarpsPerCta < nwt) ? w0 + kWarpsPerCta : nwt;
+    const int32_t vlo = tile_v[w0], vhi = tile_v[w1];
+    const int64_t wn = (int64_t)vhi - vlo + 2;
+    const bool sm = wn <= kCtaWin;
+    __syncthreads();
+    if (sm)
+        for (int64_t i = threadIdx.x; i < wn; i += kThreads) win[i] = off[vlo + i];
+    __syncthreads();
+    at.a0 = t * (int64_t)kTile + (int64_t)threadIdx.x * kItems;
+    at.cnt = 0;
+    if (at.a0 >= nnz) return;
+    at.cnt = (int)((nnz - at.a0) < kItems ? (nnz - at.a0) : kItems);
+    int64_t lo = 0, hi = wn - 2;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        int64_t x = sm ? (int64_t)win[mid] : (int64_t)off[vlo + mid];
+        if (x <= at.a0) lo = mid; else hi = mid - 1;
+    }
+    int64_t end = sm ? (int64_t)win[lo + 1] : (int64_t)off[vlo + lo + 1];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        int64_t a = at.a0 + j;
+        if (j < at.cnt) {
+            while (end <= a) {
+                ++lo;
+                end = sm ? (int64_t)win[lo + 1] : (int64_t)off[vlo + lo + 1];
+            }
+        }
+        at.src[j] = vlo + (int32_t)lo;
+    }
+}
+
+// Loop header of an arc pass: the calling warp's tiles, and its window slice.
+#define FOR_EACH_WARP_TILE(w, nwt)                                                          \
+    for (int64_t w = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; w < (nwt);      \
+         w += ((int64_t)gridDim.x * kThreads) >> 5)
 
 // The kItems neighbour ids of the thread's arcs (vector loads when aligned).
 __device__ __forceinline__ void arc_tile_targets(const int32_t *__restrict__ adj, int64_t a0, int cnt,
@@ -414,10 +471,12 @@ inline int grid_for(const Launch &L, int64_t items_per_cta_units)
 // Phase launchers (each returns the first launch error or cudaSuccess).
 template <typename OffT>
 cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                            int cc_sample, bool vec, const Launch &L);
+                            int cc_sample, int cc_local, bool vec, const Launch &L);
+// Allow the local-first First-CC kernel its shared memory for ranges of V vertices.
+cudaError_t prepare_cc_local(int V);
 template <typename OffT>
 cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           int ruler_stride, const Launch &L);
+                           int ruler_stride, int chase_chains, const Launch &L);
 template <typename OffT>
 cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, bool keep_low_high, const Launch &L);

@@ -102,9 +102,11 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
                                                        const int32_t *__restrict__ smin, unsigned long long *key,
                                                        bool vec)
 {
-    __shared__ OffT win[kOffWin];
+    __shared__ OffT win_all[kWarpsPerCta * kWarpWin];
+    OffT *win = win_all + (threadIdx.x >> 5) * kWarpWin;
     ArcTile<OffT> at;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    FOR_EACH_WARP_TILE(t, ntiles)
+    {
         arc_tile_sources(off, nnz, tile_v, t, win, at);
         if (!at.cnt) continue;
         bool any = false;
@@ -259,9 +261,11 @@ __global__ void __launch_bounds__(kThreads) k_edge_out(const OffT *__restrict__ 
                                                        const int2 *__restrict__ fo, int32_t *edge_bcc,
                                                        uint8_t *is_bridge, bool vec, bool vec_out)
 {
-    __shared__ OffT win[kOffWin];
+    __shared__ OffT win_all[kWarpsPerCta * kWarpWin];
+    OffT *win = win_all + (threadIdx.x >> 5) * kWarpWin;
     ArcTile<OffT> at;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    FOR_EACH_WARP_TILE(t, ntiles)
+    {
         arc_tile_sources(off, nnz, tile_v, t, win, at);
         if (!at.cnt) continue;
         const uint32_t tb = arc_tile_treebits(tree_bits, at.a0);
@@ -307,7 +311,7 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
     const int gv = grid_for(L, ceil_div(n, kThreads));
-    const int64_t ntiles = ceil_div(nnz, kTile);
+    const int64_t ntiles = ceil_div(nnz, kWTile);
     const int64_t nwords = ceil_div(nnz, 32);
     CK(cudaMemsetAsync(d.nh, 0, n * sizeof(int32_t), L.s));
     CK(cudaMemsetAsync(d.scanv, 0, n, L.s));
@@ -319,7 +323,7 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
-        k_key_scan<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.first,
+        k_key_scan<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.first,
                                                                    d.uf, d.head, d.smin, d.key, vec);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
@@ -336,7 +340,7 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
         k_fo<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.rank, d.first, d.vbits, d.fo, d.stats);
         L.mark("k_fo");
         const bool vec_out = ((uintptr_t)edge_bcc & 15) == 0 && ((uintptr_t)is_bridge & 7) == 0;
-        k_edge_out<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
+        k_edge_out<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
                                                                    d.fo, edge_bcc, is_bridge, vec, vec_out);
         L.mark("k_edge_out");
     } else if (B.G > 0) {

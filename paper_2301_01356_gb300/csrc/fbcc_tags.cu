@@ -28,9 +28,11 @@ __global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, 
                                                   const int32_t *__restrict__ first, int32_t *w1, int32_t *w2,
                                                   int64_t n, int *err, bool vec)
 {
-    __shared__ OffT win[kOffWin];
+    __shared__ OffT win_all[kWarpsPerCta * kWarpWin];
+    OffT *win = win_all + (threadIdx.x >> 5) * kWarpWin;
     ArcTile<OffT> at;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    FOR_EACH_WARP_TILE(t, ntiles)
+    {
         arc_tile_sources(off, nnz, tile_v, t, win, at);
         if (!at.cnt) continue;
         uint32_t tb = arc_tile_treebits(tree_bits, at.a0);
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                                                         const int32_t *__restrict__ w2, const int32_t *__restrict__ pmin,
                                                         const int32_t *__restrict__ pmax, const int32_t *__restrict__ tmin,
                                                         const int32_t *__restrict__ tmax, int64_t st_stride,
-                                                        const int32_t *__restrict__ ord, const int32_t *__restrict__ lastp,
+                                                        const int32_t *__restrict__ ord,
                                                         const int32_t *__restrict__ porig,
                                                         const int32_t *__restrict__ first,
                                                         const int32_t *__restrict__ last, uint8_t *vbits, int32_t *lp,
@@ -206,7 +208,8 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
             const int i = threadIdx.x + k * kThreads;
             const int64_t p = base + i;
             if (p >= n) continue;
-            int32_t e = lastp[p];
+            const int32_t vp = ord[p];
+            int32_t e = (uint32_t)vp < (uint64_t)n ? __ldg(last + vp) : (int32_t)p;
             if (e < p || e >= n) { atomicOr(err, kErrIndex); e = (int32_t)p; }
             int32_t lo, hi;
             const int ci = i / kChunk;
@@ -295,9 +298,9 @@ template <typename OffT>
 cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, bool keep_low_high, const Launch &L)
 {
-    const int64_t ntiles = ceil_div(nnz, kTile);
+    const int64_t ntiles = ceil_div(nnz, kWTile);
     if (nnz > 0) {
-        k_w12<OffT><<<grid_for(L, ntiles), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits, d.first,
+        k_w12<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits, d.first,
                                                               d.w1, d.w2, n, d.err, vec);
         L.mark("k_w12");
     }
@@ -313,7 +316,7 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
     cudaError_t e = cudaMemsetAsync(d.ext, 0, n, L.s);
     if (e != cudaSuccess) return e;
     k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax,
-                                                       d.rmq_tiles_max, d.ord, d.lastp, d.porig, d.first, d.last,
+                                                       d.rmq_tiles_max, d.ord, d.porig, d.first, d.last,
                                                        d.vbits, d.lp, d.ext, keep_low_high ? d.low : nullptr,
                                                        keep_low_high ? d.high : nullptr, d.err);
     L.mark("k_rmq_query");

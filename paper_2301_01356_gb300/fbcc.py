@@ -37,7 +37,8 @@ class fbcc_stats(ctypes.Structure):
 
 class fbcc_config(ctypes.Structure):
     _fields_ = [("ruler_stride", ctypes.c_int32), ("cc_sample", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("grid_ctas", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("chase_chains", ctypes.c_int32), ("cc_local", ctypes.c_int32)]
 
 
 class FbccError(RuntimeError):
@@ -132,8 +133,9 @@ def fbcc_workspace_destroy(ws: int) -> None:
     load().fbcc_workspace_destroy(ws)
 
 
-def fbcc_workspace_configure(ws: int, ruler_stride=0, cc_sample=0, grid_ctas=0, use_graph=0, profile=0) -> None:
-    cfg = fbcc_config(ruler_stride, cc_sample, grid_ctas, use_graph, profile)
+def fbcc_workspace_configure(ws: int, ruler_stride=0, cc_sample=0, grid_ctas=0, use_graph=0, profile=0,
+                             chase_chains=0, cc_local=0) -> None:
+    cfg = fbcc_config(ruler_stride, cc_sample, grid_ctas, use_graph, profile, chase_chains, cc_local)
     _check(load().fbcc_workspace_configure(ws, ctypes.byref(cfg)), "fbcc_workspace_configure")
 
 

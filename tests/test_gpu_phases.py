@@ -92,7 +92,7 @@ def phase_check(torch, g, cfg=None):
     assert np.array_equal((vb & 1).astype(bool), bridge), "bridge flags"
     fence = np.zeros(n, bool)
     fence[nr] = (first[p] <= low[nr]) & (last[p] >= high[nr])
-    assert np.array_equal(rd("ord"), ord_) and np.array_equal(rd("lastp"), last[ord_]), "preorder-indexed tags"
+    assert np.array_equal(rd("ord"), ord_), "vertex by preorder number"
     assert np.array_equal(rd("porig"), parent[ord_]), "parent by preorder number"
     assert np.array_equal((vb & 2).astype(bool), fence), "fence flags"
     assert int(fbcc.fbcc_debug_read(s.ws, "err", 1)[0]) == 0, "device error bits"
