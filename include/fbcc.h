@@ -67,7 +67,7 @@ typedef struct {
 
 /* Tuning knobs; zero in a field means "library default". */
 typedef struct {
-    int32_t ruler_stride;  /* list ranking: one ruler per this many tree arcs (power of 2) */
+    int32_t ruler_stride;  /* list ranking: one ruler per this many tree arcs (power of 2, >= 8) */
     int32_t cc_sample;     /* First-CC: neighbours per vertex hooked before the full pass (0 = off) */
     int32_t grid_ctas;     /* CTAs of the persistent grid-stride kernels */
     int32_t use_graph;     /* 1 = replay a captured CUDA graph for repeated identical calls (default), -1 = never */
@@ -192,7 +192,6 @@ fbcc_status fbcc_profile_get(const fbcc_workspace *ws, int32_t i, const char **n
  *   "w1", "w2"                 w1/w2 by preorder number
  *   "low", "high"              low/high by preorder number (only when the solve
  *                              ran with fbcc_config.profile = 1)
- *   "tree_u", "tree_v"         forest edge recorded at the vertex it hooked (-1: none)
  *   "ord", "porig"             vertex and parent vertex (-1: root) by preorder number
  *   "vbits" (uint8)            bit 0: the tree edge to the parent is a bridge;
  *                              bit 1: it is a fence edge

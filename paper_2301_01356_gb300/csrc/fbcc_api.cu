@@ -27,7 +27,7 @@ fbcc_status cuda_fail(cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(e_, where); \
     } while (0)
 
-constexpr int kMinStride = 4;
+constexpr int kMinStride = 8;
 
 struct GraphKey {
     const void *off, *adj, *edge_bcc, *bcc_head, *is_ap, *is_bridge;
@@ -65,30 +65,42 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     Carver c{base};
     d.n_max = N;
     d.nnz_max = Z;
-    d.ruler_max = N + ceil_div(2 * N, kMinStride) + 2;
+    // level-1 rulers: a head per tour (a tour spans >= 2 vertices) plus one per stride
+    d.ruler_max = N / 2 + ceil_div(2 * N, kMinStride) + 2;
     d.rmq_tiles_max = ceil_div(N, kRmqTile);
     d.st_levels = st_levels_for(d.rmq_tiles_max);
     const int64_t words = ceil_div(Z, 32) + 1;
     int64_t scan_items = 2 * N + 1;
     if (words + 1 > scan_items) scan_items = words + 1;
+    // arrays that live through the whole solve
     d.err = c.take<int>(4);
     d.counters = c.take<long long>(16);
     d.scan_status = c.take<uint64_t>(ceil_div(scan_items, kTile) + 2);
+    d.stats = c.take<fbcc_stats>(1);
     d.uf = c.take<int32_t>(N);
-    d.te_u = c.take<int32_t>(N);
-    d.te_v = c.take<int32_t>(N);
     d.tile_v = c.take<int32_t>(ceil_div(Z, kWTile) + 2);
     d.tree_bits = c.take<uint32_t>(words);
+    d.first = c.take<int32_t>(N);
+    d.last = c.take<int32_t>(N);
+    d.parent = c.take<int32_t>(N);
+    d.ord = c.take<int32_t>(N);
+    d.porig = c.take<int32_t>(N);
+    d.w1 = c.take<int32_t>(N);
+    d.w2 = c.take<int32_t>(N);
+    // First-CC and rooting scratch; the later phases reuse the same bytes
+    const size_t shared_from = c.used;
+    d.te_u = c.take<int32_t>(N);
+    d.te_v = c.take<int32_t>(N);
     d.tdeg = c.take<int32_t>(N + 1);
     d.toff = c.take<int32_t>(N + 1);
     d.tadj = c.take<int32_t>(2 * N);
     d.twin = c.take<int32_t>(2 * N);
+    d.tsrc = c.take<int32_t>(2 * N);
     d.succ = c.take<int32_t>(2 * N);
     d.is_head = c.take<uint8_t>(2 * N);
     d.link = c.take<int2>(2 * N);
     d.relem = c.take<int32_t>(d.ruler_max);
     d.oo = c.take<int2>(2 * N);
-    d.tsrc = c.take<int32_t>(2 * N);
     for (int i = 0; i < 2; ++i) {
         d.rnext[i] = c.take<int32_t>(d.ruler_max);
         d.rval[i] = c.take<int32_t>(d.ruler_max);
@@ -104,13 +116,9 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.vbase = c.take<int32_t>(N + 1);
     d.pos = c.take<int32_t>(2 * N);
     d.rec = c.take<int2>(2 * N);
-    d.first = c.take<int32_t>(N);
-    d.last = c.take<int32_t>(N);
-    d.parent = c.take<int32_t>(N);
-    d.ord = c.take<int32_t>(N);
-    d.porig = c.take<int32_t>(N);
-    d.w1 = c.take<int32_t>(N);
-    d.w2 = c.take<int32_t>(N);
+    const size_t rooting_end = c.used;
+    // tagging, Last-CC and output scratch (alive only after rooting has finished)
+    c.used = shared_from;
     d.pmin = c.take<int32_t>(N);
     d.pmax = c.take<int32_t>(N);
     d.tmin = c.take<int32_t>(d.st_levels * d.rmq_tiles_max);
@@ -133,7 +141,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.key_pre = c.take<int32_t>(words + 1);
     d.rank = c.take<int32_t>(N);
     d.fo = c.take<int2>(N);
-    d.stats = c.take<fbcc_stats>(1);
+    if (c.used < rooting_end) c.used = rooting_end;
     return c.used + 256;
 }
 
@@ -608,8 +616,6 @@ extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *nam
     else if (!strcmp(name, "w2")) src = d.w2;
     else if (!strcmp(name, "low")) src = d.low;
     else if (!strcmp(name, "high")) src = d.high;
-    else if (!strcmp(name, "tree_u")) src = d.te_u;
-    else if (!strcmp(name, "tree_v")) src = d.te_v;
     else if (!strcmp(name, "ord")) src = d.ord;
     else if (!strcmp(name, "porig")) src = d.porig;
     else if (!strcmp(name, "err")) { src = d.err; if (count > 1) return FBCC_E_INVALID; }

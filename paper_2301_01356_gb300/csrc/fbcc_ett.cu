@@ -465,8 +465,9 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     CK(cudaMemsetAsync(nr, 0, sizeof(long long), L.s));
     k_rulers<<<ga, kThreads, 0, L.s>>>(d.toff, n, ruler_stride, d.succ, d.is_head, d.link, d.relem, nr);
     L.mark("k_rulers");
-    // upper bound on the number of rulers: every tour head plus one per stride
-    const int64_t rbound = n + ceil_div(2 * n, ruler_stride) + 1;
+    // upper bound on the number of rulers: a head per tour (a tour spans at least
+    // two vertices) plus one per stride
+    const int64_t rbound = n / 2 + ceil_div(2 * n, ruler_stride) + 1;
     const int gr = grid_for(L, ceil_div(rbound, kThreads));
     if (chase_chains >= 4)
         k_chase<4><<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);

@@ -105,7 +105,7 @@ def test_repeated_solves_and_configs(torch_cuda, oracle):
     from paper_2301_01356_gb300 import fbcc
     g1, g2 = gg.grid(100, 120, p=0.6, seed=3), gg.uniform(9000, 20000, 4)
     e1, e2 = oracle.solve(g1.offsets, g1.adj), oracle.solve(g2.offsets, g2.adj)
-    for cfg in ({}, {"ruler_stride": 4}, {"ruler_stride": 256}, {"cc_sample": 2}, {"use_graph": -1},
+    for cfg in ({}, {"ruler_stride": 8}, {"ruler_stride": 256}, {"cc_sample": 2}, {"use_graph": -1},
                 {"grid_ctas": 3}, {"chase_chains": 4}, {"chase_chains": 2}, {"cc_local": 1024},
                 {"cc_local": 16384}):
         s = fbcc.Solver(20000, 50000, **cfg)

@@ -42,10 +42,10 @@ def phase_check(torch, g, cfg=None):
     A = csr_matrix((np.ones(g.nnz), g.adj, g.offsets), shape=(n, n))
     ncc, cc = connected_components(A, directed=False)
 
-    # --- First-CC: a spanning forest of G -------------------------------------
-    tu, tv = rd("tree_u"), rd("tree_v")
-    h = np.nonzero(tu >= 0)[0]
-    fu, fv = tu[h], tv[h]
+    # --- First-CC: the forest (as rooted by the next step) spans G ------------
+    parent0 = rd("parent")
+    h = np.nonzero(parent0 >= 0)[0]
+    fu, fv = h, parent0[h]
     assert fu.size == n - ncc, "forest has n - #CC edges"
     assert np.all(A[fu, fv].A1 == 1), "forest edges are graph edges"
     F = coo_matrix((np.ones(fu.size), (fu, fv)), shape=(n, n))
@@ -135,4 +135,4 @@ def test_phases(torch_cuda, family):
         "knn": lambda: gg.knn3(20000, 4, 3),
     }[family]()
     phase_check(torch_cuda, g)
-    phase_check(torch_cuda, g, {"ruler_stride": 4})
+    phase_check(torch_cuda, g, {"ruler_stride": 8, "cc_local": 4096})
