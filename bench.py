@@ -210,13 +210,26 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     from oracle import ht
-    fn, _, desc = WORKLOADS[args.workload]
-    g = fn()
+    if args.workload == "batch":
+        bt = gg.batch(args.batch_graphs, 4, 1000, 1000000)
+        # a bounded sample per step: the first 64 graphs of the batch
+        sample = [bt.graph(i) for i in range(min(64, bt.G))]
+
+        class _Sample:
+            m = sum(x.m for x in sample)
+            n = sum(x.n for x in sample)
+        g = _Sample()
+        desc = f"{bt.G} graphs of the config-4 recipe; each step solves the first {len(sample)}"
+        solve = lambda: [ht.solve(x.offsets, x.adj) for x in sample]
+    else:
+        fn, _, desc = WORKLOADS[args.workload]
+        g = fn()
+        solve = lambda: ht.solve(g.offsets, g.adj)
     ht.load()
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        ht.solve(g.offsets, g.adj)
+        solve()
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -237,6 +250,20 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+
+def tuned_config(args) -> dict:
+    """The autotuner's choice for this workload (tuning.json), overridden by any knob
+    given on the command line."""
+    from paper_2301_01356_gb300 import batch as B
+    cfg = dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0)
+    if args.config == "tuned":
+        cfg.update(B.load_tuning().get("graphs", {}).get(args.workload, {}).get("config", {}))
+    for k in ("ruler_stride", "cc_sample", "chase_chains", "cc_local"):
+        v = getattr(args, k)
+        if v is not None:
+            cfg[k] = v
+    return cfg
+
 
 def cpu_baseline(g, runs: int = 3):
     from oracle import ht
@@ -262,8 +289,7 @@ def run_gpu(args, world, rank, local):
     off_np = g.offsets.astype(np.int64 if off64 else np.int32)
     off = torch.from_numpy(off_np).cuda()
     adj = torch.from_numpy(g.adj).cuda()
-    cfg = dict(ruler_stride=args.ruler_stride, cc_sample=args.cc_sample, chase_chains=args.chase_chains,
-               cc_local=args.cc_local)
+    cfg = tuned_config(args)
     solver = fbcc.Solver(n, nnz, **cfg)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -321,7 +347,7 @@ def run_gpu(args, world, rank, local):
                    "ms_per_launch": t / c} for k, (t, c) in prof.items()}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     peak, peak_kind = measured_peak_gbs()
-    ab = algorithmic_bytes(dom, n, nnz, st["n_cc"], off_np.itemsize, args.ruler_stride)
+    ab = algorithmic_bytes(dom, n, nnz, st["n_cc"], off_np.itemsize, cfg["ruler_stride"])
     achieved = ab / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9 if ab else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": load_traffic(dom, args.workload),
@@ -363,8 +389,7 @@ def run_gpu(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {desc}", "n": n, "m": m, "parallelism": f"replicas{world}",
-                   "l2": "flushed between timed steps (256 MiB write)", "ruler_stride": args.ruler_stride,
-                   "cc_sample": args.cc_sample, "chase_chains": args.chase_chains, "cc_local": args.cc_local,
+                   "l2": "flushed between timed steps (256 MiB write)", "tuning": cfg,
                    "p50_ms": p50, "p99_ms": p99},
         "e2e": {"value": whole_job_rate(m, args.steps, world, e2e_max), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max * 1e3 / args.steps,
@@ -382,17 +407,157 @@ def run_gpu(args, world, rank, local):
     solver.close()
 
 
+def run_batch(args, world, rank, local):
+    """Config 4: thousands of graphs per launch vs a per-graph loop of the plain form."""
+    import torch
+    from paper_2301_01356_gb300 import batch as B, fbcc
+    from oracle import ht
+
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    bt = gg.batch(args.batch_graphs, 4, 1000, 1000000)
+    gen_s = time.perf_counter() - t0
+    m_total = bt.nnz_total // 2
+    runner = B.BatchRunner(bt)
+    for _ in range(args.warmup):
+        runner.run()
+    torch.cuda.synchronize()
+    st = runner.stats()
+    if np.any(st[:, 4] != 0):
+        raise SystemExit("device status set in the batched warm-up")
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record()
+        runner.run()
+        b.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    max_s = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = whole_job_rate(m_total, args.steps, world, max_s)
+    ms_sorted = sorted(step_ms)
+
+    # the plain form, graph by graph (same GPU, same graphs)
+    B.per_graph_loop(bt, graphs=range(min(64, bt.G)))
+    loop_s = B.per_graph_loop(bt)
+
+    # per-kernel times on the largest bucket (profiled solve) for the roofline
+    big = max(runner.buckets, key=lambda b: b.sub.n_total)
+    fbcc.fbcc_workspace_configure(big.ws, profile=1, **big.cfg)
+    big.launch()
+    rows = fbcc.fbcc_profile(big.ws)
+    torch.cuda.synchronize()
+    fbcc.fbcc_workspace_configure(big.ws, **big.cfg)
+    prof = {}
+    for name, ms in rows:
+        t, c = prof.get(name, (0.0, 0))
+        prof[name] = (t + ms, c + 1)
+    dom = max(prof, key=lambda k: prof[k][0])
+    n_cc_big = int(runner.stats()[big.idx, 3].sum())
+    ab = algorithmic_bytes(dom, big.sub.n_total, big.sub.nnz_total, n_cc_big, 8, big.cfg.get("ruler_stride", 16))
+    dom_ms = prof[dom][0] / prof[dom][1]
+    peak, peak_kind = measured_peak_gbs()
+    achieved = ab / (dom_ms / 1e3) / 1e9 if ab else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "algorithmic_bytes_per_launch": ab, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "ms_per_launch": dom_ms, "bucket_vertices": big.sub.n_total}
+
+    # end to end: packed inputs from pinned host memory, outputs back to pinned host memory
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_in = [(pin(b.sub.local_off), pin(b.sub.local_adj)) for b in runner.buckets]
+    h_out = [(torch.empty(b.edge_bcc.shape, dtype=torch.int32).pin_memory(),
+              torch.empty(b.is_bridge.shape, dtype=torch.uint8).pin_memory(),
+              torch.empty(b.is_ap.shape, dtype=torch.uint8).pin_memory(),
+              torch.empty(b.stats.shape, dtype=torch.int64).pin_memory()) for b in runner.buckets]
+    e2e_ts = []
+    for _ in range(max(2, args.steps // 4)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for b, (lo, la) in zip(runner.buckets, h_in):
+            b.loff.copy_(lo, non_blocking=True)
+            b.ladj.copy_(la, non_blocking=True)
+        runner.run()
+        for b, (eb, br, ap, sb) in zip(runner.buckets, h_out):
+            eb.copy_(b.edge_bcc, non_blocking=True)
+            br.copy_(b.is_bridge, non_blocking=True)
+            ap.copy_(b.is_ap, non_blocking=True)
+            sb.copy_(b.stats, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ts.append(time.perf_counter() - t1)
+    e2e_s = statistics.median(e2e_ts)
+    h2d = sum(lo.numel() * 4 + la.numel() * 4 for lo, la in h_in)
+    d2h = sum(eb.numel() * 4 + br.numel() + ap.numel() + sb.numel() * 8 for eb, br, ap, sb in h_out)
+
+    parity = cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(0)
+        sample = rng.choice(bt.G, size=min(48, bt.G), replace=False)
+        ok = True
+        for g in sample:
+            x = bt.graph(int(g))
+            e = ht.solve(x.offsets, x.adj)
+            r = runner.result(int(g))
+            ok &= all(np.array_equal(np.asarray(r[k]), np.asarray(e[k])) for k in
+                      ("edge_bcc", "bcc_head", "is_ap", "is_bridge", "n_bcc", "n_ap", "n_bridge", "n_cc"))
+        parity = {"graphs_checked": int(sample.size), "all_equal": bool(ok)}
+        t1 = time.perf_counter()
+        done_m = done_g = 0
+        for g in range(bt.G):
+            x = bt.graph(g)
+            ht.solve(x.offsets, x.adj)
+            done_m += x.m
+            done_g += 1
+            if time.perf_counter() - t1 > args.cpu_seconds:
+                break
+        cs = time.perf_counter() - t1
+        cpu = {"value": done_m / cs, "unit": UNIT, "cores": 1, "kind": "oracle", "graphs_per_s": done_g / cs,
+               "sample": f"the first {done_g} graphs of the batch, single-threaded Hopcroft-Tarjan"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batch{bt.G}: {bt.G} graphs, n log-uniform on [1e3, 1e6], uniform (degree 4-12) / "
+                               "thinned grid (p 0.55-0.75) / cycle chain families round-robin, seed 4",
+                   "graphs": bt.G, "n_total": bt.n_total, "m_total": m_total, "parallelism": f"replicas{world}",
+                   "l2": "inputs (packed CSR, %.1f GB) larger than L2" % ((bt.n_total + bt.nnz_total) * 4 / 1e9),
+                   "buckets": [{"n_range": [int(b.sub.sizes().min()), int(b.sub.sizes().max())],
+                                "graphs": b.sub.G, "config": b.cfg} for b in runner.buckets],
+                   "p50_ms": ms_sorted[len(ms_sorted) // 2], "p99_ms": ms_sorted[-1], "generate_s": round(gen_s, 1)},
+        "graphs_per_s": whole_job_rate(bt.G, args.steps, world, max_s),
+        "per_graph_loop": {"graphs_per_s": bt.G / loop_s, "value": m_total / loop_s, "unit": UNIT,
+                           "seconds": loop_s, "api": "fbcc_solve per graph, direct launches"},
+        "e2e": {"value": m_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3, "api": "pinned host copies + fbcc_solve_batch per bucket"},
+        "gpu_launches": len(rows) * len(runner.buckets) * args.steps,
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "parity_vs_oracle": parity,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    runner.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="grid4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="grid4096", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs in --workload batch")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle time budget of the batch baseline")
     ap.add_argument("--impl", default="fbcc", choices=("fbcc", "reference"))
-    ap.add_argument("--ruler-stride", type=int, default=16)
-    ap.add_argument("--cc-sample", type=int, default=0, help="First-CC: neighbours hooked per vertex before the full pass")
-    ap.add_argument("--chase-chains", type=int, default=1, help="list ranking: walks per thread (1, 2, 4)")
-    ap.add_argument("--cc-local", type=int, default=0, help="First-CC: shared-memory range in vertices (0 = off)")
+    ap.add_argument("--config", default="tuned", choices=("tuned", "default"),
+                    help="start from the autotuner's table (paper_2301_01356_gb300/tuning.json) or the defaults")
+    ap.add_argument("--ruler-stride", type=int, default=None)
+    ap.add_argument("--cc-sample", type=int, default=None, help="First-CC: neighbours hooked per vertex first")
+    ap.add_argument("--chase-chains", type=int, default=None, help="list ranking: walks per thread (1, 2, 4)")
+    ap.add_argument("--cc-local", type=int, default=None, help="First-CC: shared-memory range in vertices (0 = off)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
@@ -409,6 +574,8 @@ def main(argv=None):
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.workload == "batch":
+            run_batch(args, world, rank, local)
         else:
             run_gpu(args, world, rank, local)
     finally:

@@ -501,3 +501,120 @@ int gg_knn3(int64_t n, int64_t k, uint64_t seed, gg_csr *out)
     free(ev);
     return rc;
 }
+
+/* ---- packed batches of many graphs ------------------------------------------------ */
+
+typedef struct {
+    int64_t G;
+    int64_t *vtx_base, *arc_base;   /* G+1 each */
+    int32_t *loff;                  /* n_total: list starts relative to the graph's arc base */
+    int32_t *ladj;                  /* nnz_total: local neighbour ids */
+    int32_t *family;                /* G: 0 uniform, 1 grid, 2 cycle chain, 3 k-NN */
+    int64_t *truth_bcc, *truth_ap;  /* G: ground truth where the family fixes it, else -1 */
+} gg_batch;
+
+/*
+ * G graphs, vertex counts log-uniform on [nmin, nmax], families taken round-robin from
+ * the `fam_mask` bits (bit f = family f):
+ *   0 uniform random, average degree uniform on [4, 12];
+ *   1 thinned open grid floor(sqrt(n)) x ceil(n / floor(sqrt(n))), p uniform on [0.55, 0.75];
+ *   2 chain of k (2..64) cycles of lengths 3..5000, pendant trees for the rest;
+ *   3 k-NN (k = 5) of uniform points in the unit cube.
+ * Graph g uses seed `seed * 1000003 + g`. Returns 0, 1 for bad arguments, 3 on OOM.
+ */
+int gg_batch_make(int64_t G, uint64_t seed, int64_t nmin, int64_t nmax, int fam_mask, gg_batch *out)
+{
+    memset(out, 0, sizeof(*out));
+    if (G < 1 || nmin < 3 || nmax < nmin || !(fam_mask & 15)) return 1;
+    int fams[4], nf = 0;
+    for (int f = 0; f < 4; f++)
+        if (fam_mask >> f & 1) fams[nf++] = f;
+    int64_t *ns = malloc((size_t)G * sizeof(int64_t));
+    gg_csr *gs = calloc((size_t)G, sizeof(gg_csr));
+    int *fam = malloc((size_t)G * sizeof(int));
+    if (!ns || !gs || !fam) { free(ns); free(gs); free(fam); return 3; }
+    double lmin = log((double)nmin), lmax = log((double)nmax);
+    for (int64_t g = 0; g < G; g++) {
+        double x = lmin + (lmax - lmin) * unif(seed, 61, (uint64_t)g);
+        int64_t n = (int64_t)llround(exp(x));
+        ns[g] = n < nmin ? nmin : (n > nmax ? nmax : n);
+        fam[g] = fams[g % nf];
+    }
+    int fail = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t g = 0; g < G; g++) {
+        uint64_t sg = seed * 1000003ULL + (uint64_t)g;
+        int64_t n = ns[g];
+        int rc = 0;
+        switch (fam[g]) {
+        case 0: {
+            double d = 4.0 + 8.0 * unif(sg, 71, 0);
+            int64_t m = (int64_t)llround(n * d / 2);
+            if (m > n * (n - 1) / 2) m = n * (n - 1) / 2;
+            rc = gg_uniform(n, m, sg, &gs[g]);
+            break;
+        }
+        case 1: {
+            int64_t R = (int64_t)floor(sqrt((double)n));
+            if (R < 2) R = 2;
+            int64_t C = (n + R - 1) / R;
+            if (C < 2) C = 2;
+            double p = 0.55 + 0.20 * unif(sg, 72, 0);
+            rc = gg_grid(R, C, 0, p, 0.0, 1, sg, &gs[g]);
+            break;
+        }
+        case 2: {
+            int64_t k = 2 + (int64_t)below(sg, 73, 0, 63);
+            rc = gg_cycle_chain(n, k, 3, 5000, sg, &gs[g]);
+            break;
+        }
+        default:
+            rc = gg_knn3(n, 5, sg, &gs[g]);
+        }
+        if (rc) {
+#pragma omp atomic write
+            fail = rc;
+        }
+    }
+    if (fail) {
+        for (int64_t g = 0; g < G; g++) { free(gs[g].off); free(gs[g].adj); }
+        free(ns); free(gs); free(fam);
+        return fail;
+    }
+    out->G = G;
+    out->vtx_base = malloc((size_t)(G + 1) * sizeof(int64_t));
+    out->arc_base = malloc((size_t)(G + 1) * sizeof(int64_t));
+    out->family = malloc((size_t)G * sizeof(int32_t));
+    out->truth_bcc = malloc((size_t)G * sizeof(int64_t));
+    out->truth_ap = malloc((size_t)G * sizeof(int64_t));
+    if (!out->vtx_base || !out->arc_base || !out->family || !out->truth_bcc || !out->truth_ap) fail = 3;
+    if (!fail) {
+        out->vtx_base[0] = out->arc_base[0] = 0;
+        for (int64_t g = 0; g < G; g++) {
+            out->vtx_base[g + 1] = out->vtx_base[g] + gs[g].n;
+            out->arc_base[g + 1] = out->arc_base[g] + gs[g].nnz;
+            out->family[g] = fam[g];
+            out->truth_bcc[g] = gs[g].truth_bcc;
+            out->truth_ap[g] = gs[g].truth_ap;
+        }
+        out->loff = malloc((size_t)(out->vtx_base[G] > 0 ? out->vtx_base[G] : 1) * sizeof(int32_t));
+        out->ladj = malloc((size_t)(out->arc_base[G] > 0 ? out->arc_base[G] : 1) * sizeof(int32_t));
+        if (!out->loff || !out->ladj) fail = 3;
+    }
+    if (!fail) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t g = 0; g < G; g++) {
+            int32_t *lo = out->loff + out->vtx_base[g];
+            for (int64_t v = 0; v < gs[g].n; v++) lo[v] = (int32_t)gs[g].off[v];
+            memcpy(out->ladj + out->arc_base[g], gs[g].adj, (size_t)gs[g].nnz * sizeof(int32_t));
+        }
+    }
+    for (int64_t g = 0; g < G; g++) { free(gs[g].off); free(gs[g].adj); }
+    free(ns); free(gs); free(fam);
+    if (fail) {
+        free(out->vtx_base); free(out->arc_base); free(out->family); free(out->truth_bcc); free(out->truth_ap);
+        free(out->loff); free(out->ladj);
+        memset(out, 0, sizeof(*out));
+    }
+    return fail;
+}

@@ -140,14 +140,17 @@ def fbcc_workspace_configure(ws: int, ruler_stride=0, cc_sample=0, grid_ctas=0, 
 
 
 def fbcc_solve(offsets, adj, n: int, m: int, edge_bcc, bcc_head, is_ap, is_bridge, ws: int,
-               stream=None, stats: fbcc_stats | None = None) -> fbcc_stats:
-    """Enqueue one solve on device tensors; ``stats`` is valid after a stream sync."""
+               stream=None, stats: fbcc_stats | None = None, want_stats: bool = True) -> fbcc_stats | None:
+    """Enqueue one solve on device tensors; ``stats`` is valid after a stream sync.
+    With want_stats=False no stats copy is enqueued (nothing waits on the host)."""
     import torch
-    stats = stats if stats is not None else fbcc_stats()
+    if want_stats:
+        stats = stats if stats is not None else fbcc_stats()
     off64 = int(offsets.dtype == torch.int64)
     _check(load().fbcc_solve(_ptr(offsets), off64, _ptr(adj), n, m, _ptr(edge_bcc), _ptr(bcc_head), _ptr(is_ap),
-                             _ptr(is_bridge), ctypes.byref(stats), ws, _stream_handle(stream)), "fbcc_solve")
-    return stats
+                             _ptr(is_bridge), ctypes.byref(stats) if want_stats else None, ws,
+                             _stream_handle(stream)), "fbcc_solve")
+    return stats if want_stats else None
 
 
 def fbcc_solve_noalloc(offsets, adj, n: int, m: int, edge_bcc, bcc_head, is_ap, is_bridge, stats_dev=None,

@@ -48,10 +48,71 @@ class Graph:
         return self.nnz // 2
 
 
+@dataclasses.dataclass
+class Batch:
+    """Many graphs packed into one CSR with per-graph bases (local ids and offsets)."""
+    vtx_base: np.ndarray         # int64, G+1
+    arc_base: np.ndarray         # int64, G+1
+    local_off: np.ndarray        # int32, n_total: list start relative to the graph's arc base
+    local_adj: np.ndarray        # int32, nnz_total: neighbour ids local to the graph
+    family: np.ndarray           # int32, G: 0 uniform, 1 grid, 2 cycle chain, 3 k-NN
+    truth_bcc: np.ndarray        # int64, G (-1 where the family fixes none)
+    truth_ap: np.ndarray
+
+    FAMILIES = ("uniform", "grid", "chain", "knn")
+
+    @property
+    def G(self) -> int:
+        return int(self.vtx_base.size - 1)
+
+    @property
+    def n_total(self) -> int:
+        return int(self.vtx_base[-1])
+
+    @property
+    def nnz_total(self) -> int:
+        return int(self.arc_base[-1])
+
+    def sizes(self) -> np.ndarray:
+        return np.diff(self.vtx_base)
+
+    def graph(self, g: int) -> "Graph":
+        v0, v1 = int(self.vtx_base[g]), int(self.vtx_base[g + 1])
+        a0, a1 = int(self.arc_base[g]), int(self.arc_base[g + 1])
+        off = np.empty(v1 - v0 + 1, np.int64)
+        off[:-1] = self.local_off[v0:v1]
+        off[-1] = a1 - a0
+        return Graph(off, self.local_adj[a0:a1].copy(), f"batch[{g}]", int(self.truth_bcc[g]), int(self.truth_ap[g]))
+
+    def subset(self, idx) -> "Batch":
+        """A new packed batch of the graphs `idx` (in that order)."""
+        idx = np.asarray(idx, dtype=np.int64)
+        nv = np.diff(self.vtx_base)[idx]
+        na = np.diff(self.arc_base)[idx]
+        vb = np.zeros(idx.size + 1, np.int64)
+        ab = np.zeros(idx.size + 1, np.int64)
+        np.cumsum(nv, out=vb[1:])
+        np.cumsum(na, out=ab[1:])
+        loff = np.empty(int(vb[-1]), np.int32)
+        ladj = np.empty(int(ab[-1]), np.int32)
+        for i, g in enumerate(idx):
+            loff[vb[i]:vb[i + 1]] = self.local_off[self.vtx_base[g]:self.vtx_base[g + 1]]
+            ladj[ab[i]:ab[i + 1]] = self.local_adj[self.arc_base[g]:self.arc_base[g + 1]]
+        return Batch(vb, ab, loff, ladj, self.family[idx].copy(), self.truth_bcc[idx].copy(),
+                     self.truth_ap[idx].copy())
+
+
 class _CSR(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("off", ctypes.POINTER(ctypes.c_int64)), ("adj", ctypes.POINTER(ctypes.c_int32)),
                 ("truth_bcc", ctypes.c_int64), ("truth_ap", ctypes.c_int64)]
+
+
+class _BATCH(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_int64), ("vtx_base", ctypes.POINTER(ctypes.c_int64)),
+                ("arc_base", ctypes.POINTER(ctypes.c_int64)), ("loff", ctypes.POINTER(ctypes.c_int32)),
+                ("ladj", ctypes.POINTER(ctypes.c_int32)), ("family", ctypes.POINTER(ctypes.c_int32)),
+                ("truth_bcc", ctypes.POINTER(ctypes.c_int64)), ("truth_ap", ctypes.POINTER(ctypes.c_int64))]
 
 
 def build() -> str:
@@ -79,6 +140,7 @@ def _load():
             lib.gg_knn3.argtypes = [i64, i64, u64, p]
             lib.gg_build_csr.argtypes = [i64, i64, ctypes.c_void_p, ctypes.c_void_p, p]
             lib.gg_free.argtypes = [ctypes.c_void_p]
+            lib.gg_batch_make.argtypes = [i64, u64, i64, i64, ctypes.c_int, ctypes.POINTER(_BATCH)]
             _lib = lib
         return _lib
 
@@ -145,6 +207,24 @@ def knn3(n: int, k: int = 5, seed: int = 0) -> Graph:
     return _take(lib, lib.gg_knn3(n, k, seed, ctypes.byref(out)), out, f"knn3(n={n},k={k},seed={seed})")
 
 
+def batch(G: int, seed: int, nmin: int, nmax: int, families=("uniform", "grid", "chain")) -> Batch:
+    """G graphs with vertex counts log-uniform on [nmin, nmax], families round-robin."""
+    lib = _load()
+    mask = sum(1 << Batch.FAMILIES.index(f) for f in families)
+    out = _BATCH()
+    rc = lib.gg_batch_make(G, seed, nmin, nmax, mask, ctypes.byref(out))
+    if rc:
+        raise ValueError(f"batch generator failed with code {rc}")
+    take = lambda ptr, size: np.ctypeslib.as_array(ptr, shape=(max(size, 1),))[:size].copy()
+    vb = take(out.vtx_base, G + 1)
+    ab = take(out.arc_base, G + 1)
+    res = Batch(vb, ab, take(out.loff, int(vb[-1])), take(out.ladj, int(ab[-1])), take(out.family, G),
+                take(out.truth_bcc, G), take(out.truth_ap, G))
+    for ptr in (out.vtx_base, out.arc_base, out.loff, out.ladj, out.family, out.truth_bcc, out.truth_ap):
+        lib.gg_free(ctypes.cast(ptr, ctypes.c_void_p))
+    return res
+
+
 # ---- the benchmark workloads ------------------------------------------------------
 
 def workload_uniform_64k() -> Graph:
@@ -162,6 +242,12 @@ def workload_grid_2896() -> Graph:
     """The same recipe as workload_grid_4096 on a 2896 x 2896 grid (half the vertices);
     used for detailed profiler captures."""
     return grid(2896, 2896, p=0.62, extra_frac=0.001, max_l1=8, seed=2)
+
+
+def workload_batch_4096() -> Batch:
+    """4,096 graphs, n log-uniform on [10^3, 10^6], uniform / thinned grid / cycle chain
+    families round-robin, seed 4."""
+    return batch(4096, 4, 1000, 1000000)
 
 
 def workload_rmat_24() -> Graph:

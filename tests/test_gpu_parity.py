@@ -214,3 +214,28 @@ def test_grid_4096_full_size(torch_cuda, oracle):
     got = s.solve(off, adj)
     assert_same(got, oracle.solve(g.offsets, g.adj), "grid 4096")
     s.close()
+
+
+def test_bucketed_batch_runner(torch_cuda, oracle):
+    """The config-4 recipe at small scale: every graph's result in the bucketed
+    batch equals the oracle's and its result when solved alone."""
+    from paper_2301_01356_gb300 import batch as B, fbcc
+    bt = gg.batch(96, 7, 200, 30000, families=("uniform", "grid", "chain", "knn"))
+    runner = B.BatchRunner(bt, buckets=((0, 2000), (2000, 10000), (10000, 1 << 40)), tuning={},
+                           configs=[{}, {"cc_local": 4096}, {"ruler_stride": 32, "cc_sample": 2}])
+    runner.run()
+    torch_cuda.cuda.synchronize()
+    alone = fbcc.Solver(int(bt.sizes().max()), int(np.diff(bt.arc_base).max()))
+    for g in range(bt.G):
+        x = bt.graph(g)
+        e = oracle.solve(x.offsets, x.adj)
+        got = runner.result(g)
+        assert_same(got, e, f"batched graph {g}")
+        off, adj = to_dev(torch_cuda, x)
+        solo = alone.solve(off, adj)
+        for k in KEYS:
+            assert np.array_equal(np.asarray(solo[k]), np.asarray(got[k])), f"graph {g}: {k} alone vs batch"
+        if bt.truth_bcc[g] >= 0:
+            assert got["n_bcc"] == bt.truth_bcc[g] and got["n_ap"] == bt.truth_ap[g]
+    alone.close()
+    runner.close()
