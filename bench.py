@@ -174,6 +174,17 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_rank": 16 * n,
         "k_fo": 25 * n,
         "k_edge_out": B * (n + 1) + 4 * nnz + nnz // 8 + 8 * nnz + 4 * nnz + nnz,
+        "k_cc_local": B * (n + 1) + 4 * nnz + 12 * n,
+        "k_cc_hook_cross": B * (n + 1) + 4 * nnz + 8 * n,
+        "k_tour_records": 28 * A,
+        "k_rulers2": 17 * nr,
+        "k_chase2": 20 * nr,
+        "k_expand2": 28 * nr,
+        "k_ext_compact": n,
+        "k_ext_jump": 12 * (n // 64),
+        "k_plain_label": 16 * n,
+        "k_final_label": 20 * n,
+        "k_lab_out": 20 * n,
     }
     return table.get(kernel)
 
