@@ -554,14 +554,76 @@ def run_batch(args, world, rank, local):
     runner.close()
 
 
+def run_serve(args, world, rank, local):
+    """Config 5: Poisson arrivals, continuous batching, p50/p99 latency."""
+    import torch
+    from paper_2301_01356_gb300 import fbcc, serving
+
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    graphs = serving.make_pool(args.pool, 5, nmax_knn=args.knn_max)
+    gen_s = time.perf_counter() - t0
+    pool = serving.Pool(torch, graphs)
+    srv = serving.Server(pool, slots=args.slots, hbm_budget=150 << 30)
+    arrivals = serving.poisson_arrivals(args.rate, args.serve_seconds, 5)
+    ids = np.random.default_rng(5).integers(0, len(graphs), size=arrivals.size)
+    # warm-up: a short burst (first batches allocate the batch staging buffers)
+    wa = serving.poisson_arrivals(args.rate, 0.5, 6)
+    srv.run(wa, np.random.default_rng(6).integers(0, len(graphs), size=wa.size))
+    sampler = ClockSampler(local)
+    sampler.start()
+    rep = srv.run(arrivals, ids)
+    clocks = sampler.stop()
+    srv.close()
+    # each pool graph alone (plain form) vs in the mix: a verification run keeping outputs
+    check = None
+    if rank == 0:
+        vsrv = serving.Server(pool, slots=args.slots, keep_outputs=True)
+        va = serving.poisson_arrivals(args.rate, min(1.0, args.serve_seconds), 7)
+        vids = np.random.default_rng(7).integers(0, len(graphs), size=va.size)
+        vsrv.run(va, vids)
+        n_max = int(pool.n.max())
+        z_max = int(pool.nnz.max())
+        alone = fbcc.Solver(n_max, z_max)
+        solo = {}
+        ok = True
+        for r, out in vsrv.outputs.items():
+            g = out["graph"]
+            if g not in solo:
+                x = graphs[g]
+                solo[g] = alone.solve(torch.from_numpy(x.offsets).cuda(), torch.from_numpy(x.adj).cuda())
+            ok &= all(np.array_equal(np.asarray(out[k]), np.asarray(solo[g][k])) for k in
+                      ("edge_bcc", "bcc_head", "is_ap", "is_bridge", "n_bcc", "n_ap", "n_bridge", "n_cc"))
+        alone.close()
+        vsrv.close()
+        check = {"requests": len(vsrv.outputs), "graphs": len(solo), "equal_to_alone": bool(ok)}
+    line = {
+        "metric": METRIC, "value": rep["edges_per_s"], "unit": UNIT, "n_gpus": world, "steps": rep["requests"],
+        "warmup": 1, "ms_per_step": rep["p50_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"serve: Poisson {args.rate:g} req/s for {args.serve_seconds:g} s over a pool of "
+                               f"{len(graphs)} graphs (config-4 families on [1e3, 1e6] and k-NN k=5 on "
+                               f"[1e4, {args.knn_max:.0e}]), continuous batching, {rep['slots']} slots, "
+                               "HBM budget 150 GB", "pool_generate_s": round(gen_s, 1)},
+        "serving": rep, "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "mix_vs_alone": check, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="grid4096", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--workload", default="grid4096", choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs in --workload batch")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle time budget of the batch baseline")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve: length of the arrival stream")
+    ap.add_argument("--pool", type=int, default=128, help="serve: graphs in the request pool")
+    ap.add_argument("--knn-max", type=float, default=1e7, help="serve: largest k-NN graph in the pool")
+    ap.add_argument("--slots", type=int, default=6, help="serve: batches in flight")
     ap.add_argument("--impl", default="fbcc", choices=("fbcc", "reference"))
     ap.add_argument("--config", default="tuned", choices=("tuned", "default"),
                     help="start from the autotuner's table (paper_2301_01356_gb300/tuning.json) or the defaults")
@@ -587,6 +649,8 @@ def main(argv=None):
             run_reference(args, world, rank)
         elif args.workload == "batch":
             run_batch(args, world, rank, local)
+        elif args.workload == "serve":
+            run_serve(args, world, rank, local)
         else:
             run_gpu(args, world, rank, local)
     finally:

@@ -1,0 +1,49 @@
+"""The serving loop: requests arriving while others are on the GPU join later
+batches; every request's result equals the graph solved alone (and the oracle)."""
+import numpy as np
+import pytest
+
+from paper_2301_01356_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def test_serving_results_equal_alone(torch_cuda, oracle):
+    from paper_2301_01356_gb300 import fbcc, serving
+    graphs = [gg.uniform(3000, 8000, 1), gg.grid(60, 70, p=0.6, seed=2), gg.cycle_chain(5000, 9, 3, 400, 3),
+              gg.knn3(8000, 5, 4), gg.path(700), gg.from_edges(5, [], []), gg.uniform(20000, 60000, 5),
+              gg.grid(120, 90, p=0.7, seed=6)]
+    pool = serving.Pool(torch_cuda, graphs)
+    # small slots so that batches get cut and several are in flight
+    srv = serving.Server(pool, slots=3, max_n=40000, max_nnz=150000, max_graphs=16, keep_outputs=True)
+    arrivals = serving.poisson_arrivals(400.0, 1.0, 9)
+    rng = np.random.default_rng(9)
+    ids = rng.integers(0, len(graphs), size=arrivals.size)
+    rep = srv.run(arrivals, ids)
+    assert rep["requests"] == arrivals.size and rep["batches"] > 3 and rep["p99_ms"] >= rep["p50_ms"] > 0
+    alone = fbcc.Solver(40000, 150000)
+    exp = []
+    for g in graphs:
+        off = torch_cuda.from_numpy(g.offsets).cuda()
+        adj = torch_cuda.from_numpy(g.adj).cuda()
+        solo = alone.solve(off, adj)
+        orc = oracle.solve(g.offsets, g.adj)
+        for k in ("edge_bcc", "bcc_head", "is_ap", "is_bridge", "n_bcc", "n_ap", "n_bridge", "n_cc"):
+            assert np.array_equal(np.asarray(solo[k]), np.asarray(orc[k]))
+        exp.append(solo)
+    for r in range(arrivals.size):
+        got = srv.outputs[r]
+        e = exp[got["graph"]]
+        assert got["device_status"] == 0
+        for k in ("edge_bcc", "bcc_head", "is_ap", "is_bridge", "n_bcc", "n_ap", "n_bridge", "n_cc"):
+            assert np.array_equal(np.asarray(got[k]), np.asarray(e[k])), (r, k)
+    alone.close()
+    srv.close()
