@@ -46,6 +46,7 @@ WORKLOADS = {
                  "the grid4096 recipe on a 2896x2896 grid (profiler captures); int32 CSR"),
     "uniform64k": (gg.workload_uniform_64k, False,
                    "uniform random graph: n=65,536, m=196,608 distinct edges, seed 1; int32 CSR"),
+    "rmat22": (gg.workload_rmat_22, True, "the rmat24 recipe at scale 22 (profiler captures); int64 offsets"),
     "rmat24": (gg.workload_rmat_24, True,
                "power-law R-MAT scale 24, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, seed 3; "
                "int64 offsets, int32 adjacency"),
@@ -185,6 +186,9 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_plain_label": 16 * n,
         "k_final_label": 20 * n,
         "k_lab_out": 20 * n,
+        "k_lcc_sample": B * (n + 1) + 16 * n + 32 * n,
+        "k_pos_compress": 8 * n,
+        "k_last_cc_cross_skip": B * (n + 1) + 4 * nnz + 16 * n,
     }
     return table.get(kernel)
 
@@ -266,10 +270,10 @@ def tuned_config(args) -> dict:
     """The autotuner's choice for this workload (tuning.json), overridden by any knob
     given on the command line."""
     from paper_2301_01356_gb300 import batch as B
-    cfg = dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0)
+    cfg = dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0, lcc_sample=0)
     if args.config == "tuned":
         cfg.update(B.load_tuning().get("graphs", {}).get(args.workload, {}).get("config", {}))
-    for k in ("ruler_stride", "cc_sample", "chase_chains", "cc_local"):
+    for k in ("ruler_stride", "cc_sample", "chase_chains", "cc_local", "lcc_sample"):
         v = getattr(args, k)
         if v is not None:
             cfg[k] = v
@@ -631,6 +635,7 @@ def main(argv=None):
     ap.add_argument("--cc-sample", type=int, default=None, help="First-CC: neighbours hooked per vertex first")
     ap.add_argument("--chase-chains", type=int, default=None, help="list ranking: walks per thread (1, 2, 4)")
     ap.add_argument("--cc-local", type=int, default=None, help="First-CC: shared-memory range in vertices (0 = off)")
+    ap.add_argument("--lcc-sample", type=int, default=None, help="Last-CC: cross edges sampled per vertex (0 = off)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

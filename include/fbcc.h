@@ -75,6 +75,7 @@ typedef struct {
     int32_t chase_chains;  /* list ranking: walks a thread advances together (1, 2 or 4) */
     int32_t cc_local;      /* First-CC: unite inside ranges of this many consecutive vertex ids in
                               shared memory first (power of 2, 1024..16384; 0 = off) */
+    int32_t lcc_sample;    /* Last-CC: cross edges per vertex united before the full pass (0 = off) */
 } fbcc_config;
 
 /* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds. */

@@ -19,8 +19,8 @@ import numpy as np
 from . import batch as B
 from . import fbcc, graphgen as gg
 
-CANDIDATES = [dict(ruler_stride=s, cc_local=l, cc_sample=c)
-              for s in (8, 16, 32) for (l, c) in ((0, 0), (16384, 0), (0, 2))]
+CANDIDATES = [dict(ruler_stride=s, cc_local=l, cc_sample=c, lcc_sample=q)
+              for s in (8, 16, 32) for (l, c) in ((0, 0), (16384, 0), (0, 2)) for q in (0, 2)]
 
 
 def _time(fn, reps: int) -> float:
@@ -84,6 +84,7 @@ def main(argv=None):
     table["graphs"] = {
         "grid4096": tune_graph(gg.workload_grid_4096(), False, args.reps),
         "uniform64k": tune_graph(gg.workload_uniform_64k(), False, args.reps),
+        "rmat24": tune_graph(gg.workload_rmat_24(), True, args.reps),
     }
     table["seconds"] = round(time.time() - t0, 1)
     with open(args.out, "w") as f:

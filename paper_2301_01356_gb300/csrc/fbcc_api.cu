@@ -79,10 +79,10 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.stats = c.take<fbcc_stats>(1);
     d.uf = c.take<int32_t>(N);
     d.tile_v = c.take<int32_t>(ceil_div(Z, kWTile) + 2);
-    d.tree_bits = c.take<uint32_t>(words);
     d.first = c.take<int32_t>(N);
     d.last = c.take<int32_t>(N);
     d.parent = c.take<int32_t>(N);
+    d.fp = c.take<int2>(N);
     d.ord = c.take<int32_t>(N);
     d.porig = c.take<int32_t>(N);
     d.w1 = c.take<int32_t>(N);
@@ -129,7 +129,8 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.lp = c.take<int32_t>(N);
     d.ext = c.take<uint8_t>(N);
     d.qlist = c.take<int32_t>(N);
-    d.vplab = c.take<int32_t>(N);
+    d.cr = c.take<int4>(N);
+    d.lastp = c.take<int32_t>(N);
     d.fin = c.take<int32_t>(N);
     d.minorig = c.take<int32_t>(N);
     d.smin = c.take<int32_t>(N);
@@ -175,6 +176,7 @@ static fbcc_config default_config()
     c.profile = 0;
     c.chase_chains = 1;
     c.cc_local = 0;
+    c.lcc_sample = 0;
     return c;
 }
 
@@ -254,6 +256,8 @@ fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
             c.cc_local = cfg->cc_local;
         }
+        if (cfg->lcc_sample < 0 || cfg->lcc_sample > 64) return FBCC_E_INVALID;
+        c.lcc_sample = cfg->lcc_sample;
         if (cfg->chase_chains) {
             if (cfg->chase_chains != 1 && cfg->chase_chains != 2 && cfg->chase_chains != 4) return FBCC_E_INVALID;
             c.chase_chains = cfg->chase_chains;
@@ -327,11 +331,10 @@ cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *ad
     CK(cudaMemsetAsync(d.err, 0, sizeof(int), s));
     CK(cudaMemsetAsync(d.stats, 0, sizeof(fbcc_stats), s));
     if (n > 0) {
-        CK(cudaMemsetAsync(d.tree_bits, 0, (ceil_div(nnz, 32) + 1) * sizeof(uint32_t), s));
         CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, ws->cfg.cc_local, vec, L));
         CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, ws->cfg.chase_chains, L));
         CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, ws->cfg.profile != 0, L));
-        CK(launch_last_cc<OffT>(d, off, adj, n, nnz, vec, L));
+        CK(launch_last_cc<OffT>(d, off, adj, n, nnz, ws->cfg.lcc_sample, vec, L));
         CK(launch_outputs<OffT>(d, off, adj, n, nnz, vec, edge_bcc, bcc_head, is_ap, is_bridge, B, L));
     }
     k_finish<<<1, 1, 0, s>>>(d.err, d.stats);

@@ -46,12 +46,17 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook(const OffT *__restrict__ o
         if (!at.cnt) continue;
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
+        int32_t cur = -1, rs = -1;   // the source, and where its finds start (its set's root, or near it)
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             if (j >= at.cnt || at.src[j] >= d[j]) continue;
-            int32_t r = uf_unite(uf, at.src[j], d[j], err);
+            if (at.src[j] != cur) {
+                cur = at.src[j];
+                rs = cur;
+            }
+            int32_t r = uf_unite(uf, rs, d[j], err);
             if (r >= 0) {
-                te_u[r] = at.src[j];
+                te_u[r] = cur;
                 te_v[r] = d[j];
             }
         }
@@ -367,12 +372,15 @@ __device__ __forceinline__ int32_t plain_root(const int32_t *lp, int64_t p)
     return t < (p & ~(int64_t)(kRmqTile - 1)) ? lp[t] : t;
 }
 
-// Plain-component root of every vertex (by vertex), and a fresh union-find.
+// Per vertex {first, parent, plain-component root, last} for the cross-edge pass
+// (one gather gives all four), and a fresh union-find.
 __global__ void __launch_bounds__(kThreads) k_plain_label(int64_t n, const int32_t *__restrict__ lp,
-                                                          const int32_t *__restrict__ ord, int32_t *vplab, int32_t *uf)
+                                                          const int32_t *__restrict__ ord,
+                                                          const int32_t *__restrict__ porig,
+                                                          const int32_t *__restrict__ lastp, int4 *cr, int32_t *uf)
 {
     for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads) {
-        vplab[ord[p]] = plain_root(lp, p);
+        cr[ord[p]] = make_int4((int32_t)p, porig[p], plain_root(lp, p), lastp[p]);
         uf[p] = (int32_t)p;
     }
 }
@@ -380,11 +388,8 @@ __global__ void __launch_bounds__(kThreads) k_plain_label(int64_t n, const int32
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                             int64_t nnz, const int32_t *__restrict__ tile_v,
-                                                            int64_t ntiles, const uint32_t *__restrict__ tree_bits,
-                                                            const int32_t *__restrict__ first,
-                                                            const int32_t *__restrict__ last,
-                                                            const int32_t *__restrict__ vplab, int32_t *uf, int *err,
-                                                            bool vec)
+                                                            int64_t ntiles, const int4 *__restrict__ cr, int32_t *uf,
+                                                            int *err, bool vec)
 {
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
@@ -392,22 +397,125 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
     for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
         arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
         if (!at.cnt) continue;
-        uint32_t tb = arc_tile_treebits(tree_bits, at.a0);
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
-        int32_t cur = -1, ls = 0, ps = 0;
+        int32_t cur = -1;
+        int4 cs = make_int4(0, -1, 0, 0);
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            if (j >= at.cnt || ((tb >> j) & 1u)) continue;
+            if (j >= at.cnt) continue;
             if (at.src[j] != cur) {
                 cur = at.src[j];
-                ls = __ldg(last + cur);
-                ps = __ldg(vplab + cur);
+                cs = __ldg(cr + cur);
             }
-            const int32_t fd = __ldg(first + d[j]);
-            const int32_t pd = __ldg(vplab + d[j]);
-            if (fd > ls && pd != ps) uf_unite(uf, ps, pd, err);
+            const int4 cd = __ldg(cr + d[j]);
+            // same plain component: nothing to join (tree and back edges included)
+            if (cd.z == cs.z || is_tree_arc(cur, cs.y, d[j], cd.y)) continue;
+            if (cd.x > cs.w) uf_unite(uf, cs.z, cd.z, err);   // cross edge: d after T_cur
         }
+    }
+}
+
+// Sampling variant of the cross-edge pass (the Afforest idea applied to G'):
+// first every vertex unites along its first `k` cross edges, then the component
+// holding most sampled positions is found, and the full pass skips every source
+// already in it. A skipped arc still reaches its other endpoint's side, so the
+// full pass tests cross edges from both ends (u ancestor of w or w ancestor of u
+// from the two {first, last} intervals).
+__device__ __forceinline__ bool is_cross(const int4 &a, const int4 &b)
+{
+    return !(a.x <= b.x && b.x <= a.w) && !(b.x <= a.x && a.x <= b.w);
+}
+
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_lcc_sample(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
+                                                         int64_t n, int k, const int4 *__restrict__ cr, int32_t *uf,
+                                                         int *err)
+{
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
+        const int4 cs = cr[v];
+        if (cs.y < 0) continue;   // a root has no cross edges
+        int found = 0;
+        const int64_t b = off[v], e = off[v + 1];
+        for (int64_t a = b; a < e && a < b + 4 * k && found < k; ++a) {
+            const int32_t w = adj[a];
+            const int4 cd = __ldg(cr + w);
+            if (cd.z == cs.z || is_tree_arc((int32_t)v, cs.y, w, cd.y) || !is_cross(cs, cd)) continue;
+            uf_unite(uf, cs.z, cd.z, err);
+            ++found;
+        }
+    }
+}
+
+// Flatten the union-find over positions (roots only, see uf_root).
+__global__ void __launch_bounds__(kThreads) k_pos_compress(int32_t *uf, int64_t n)
+{
+    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads)
+        uf[p] = uf_root(uf, (int32_t)p);
+}
+
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_last_cc_cross_skip(const OffT *__restrict__ off,
+                                                                 const int32_t *__restrict__ adj, int64_t nnz,
+                                                                 const int32_t *__restrict__ tile_v, int64_t ntiles,
+                                                                 const int4 *__restrict__ cr, int32_t *uf,
+                                                                 const int32_t *big, int *err, bool vec)
+{
+    __shared__ OffT win[kCtaWin];
+    ArcTile<OffT> at;
+    const int32_t root = *big;
+    const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
+        arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
+        if (!at.cnt) continue;
+        int4 cs[kItems];
+        bool any = false;
+        int32_t cur = -1;
+        bool skip = true;
+        int4 c = make_int4(0, -1, 0, 0);
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            if (j < at.cnt && at.src[j] != cur) {
+                cur = at.src[j];
+                c = __ldg(cr + cur);
+                skip = c.y < 0 || uf_find(uf, c.z) == root;
+            }
+            cs[j] = c;
+            if (j < at.cnt && !skip) any = true;
+            else cs[j].y = -2;   // marks a skipped arc
+        }
+        if (!any) continue;
+        int32_t d[kItems];
+        arc_tile_targets(adj, at.a0, at.cnt, vec, d);
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            if (j >= at.cnt || cs[j].y == -2) continue;
+            const int4 cd = __ldg(cr + d[j]);
+            if (cd.z == cs[j].z || is_tree_arc(at.src[j], cs[j].y, d[j], cd.y) || !is_cross(cs[j], cd)) continue;
+            uf_unite(uf, cs[j].z, cd.z, err);
+        }
+    }
+}
+
+// The root holding most of a fixed sample of positions (a single CTA).
+__global__ void __launch_bounds__(kThreads) k_pos_pick_big(int32_t *uf, const int32_t *__restrict__ porig, int64_t n,
+                                                           int32_t *big)
+{
+    __shared__ int32_t cand[kThreads];
+    __shared__ int32_t cnt[kThreads];
+    const int64_t step = n / kThreads > 0 ? n / kThreads : 1;
+    const int64_t p = (int64_t)threadIdx.x * step;
+    cand[threadIdx.x] = (p < n && porig[p] >= 0) ? uf_find(uf, (int32_t)p) : -1;
+    __syncthreads();
+    int c = 0;
+    for (int i = 0; i < kThreads; ++i) c += cand[i] == cand[threadIdx.x];
+    cnt[threadIdx.x] = cand[threadIdx.x] >= 0 ? c : 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int best = 0;
+        for (int i = 1; i < kThreads; ++i)
+            if (cnt[i] > cnt[best]) best = i;
+        *big = cand[best];   // -1 when nothing was sampled: then nothing is skipped
     }
 }
 
@@ -453,7 +561,7 @@ __global__ void __launch_bounds__(kThreads) k_lab_out(int64_t n, const int32_t *
 
 template <typename OffT>
 cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           bool vec, const Launch &L)
+                           int lcc_sample, bool vec, const Launch &L)
 {
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
@@ -468,11 +576,22 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
         k_ext_jump<<<gv, kThreads, 0, L.s>>>(nq, d.qlist, d.lp);
         L.mark("k_ext_jump");
     }
-    k_plain_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.ord, d.vplab, d.uf);
+    k_plain_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.ord, d.porig, d.lastp, d.cr, d.uf);
     L.mark("k_plain_label");
-    if (nnz > 0) {
-        k_last_cc_cross<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
-                                                                        d.first, d.last, d.vplab, d.uf, d.err, vec);
+    if (nnz > 0 && lcc_sample > 0) {
+        int32_t *big = reinterpret_cast<int32_t *>(d.counters + 9);
+        k_lcc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, lcc_sample, d.cr, d.uf, d.err);
+        L.mark("k_lcc_sample");
+        k_pos_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
+        L.mark("k_pos_compress");
+        k_pos_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, d.porig, n, big);
+        L.mark("k_pos_pick_big");
+        k_last_cc_cross_skip<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
+            off, adj, nnz, d.tile_v, ntiles, d.cr, d.uf, big, d.err, vec);
+        L.mark("k_last_cc_cross_skip");
+    } else if (nnz > 0) {
+        k_last_cc_cross<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.cr,
+                                                                        d.uf, d.err, vec);
         L.mark("k_last_cc_cross");
     }
     CK(cudaMemsetAsync(d.minorig, 0x7f, n * sizeof(int32_t), L.s));
@@ -488,9 +607,9 @@ template cudaError_t launch_first_cc<int32_t>(const Dev &, const int32_t *, cons
                                               int, bool, const Launch &);
 template cudaError_t launch_first_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,
                                               int, bool, const Launch &);
-template cudaError_t launch_last_cc<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, bool,
-                                             const Launch &);
-template cudaError_t launch_last_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, bool,
-                                             const Launch &);
+template cudaError_t launch_last_cc<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
+                                             bool, const Launch &);
+template cudaError_t launch_last_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,
+                                             bool, const Launch &);
 
 }  // namespace fbcc

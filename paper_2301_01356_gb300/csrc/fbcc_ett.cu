@@ -4,7 +4,8 @@
 // number first[v] and last[v] = first[v] + |T_v| - 1.
 //
 //  1. tree CSR: both arcs of every forest edge, grouped by source (counting sort),
-//     with the index of each arc's reverse (twin);
+//     with the index of each arc's reverse (twin); the arc passes later recognise
+//     tree arcs by the parent relation, so the CSR itself is never marked;
 //  2. Euler circuit: the arc u->v is followed by the arc after v->u in v's list,
 //     cyclically (the paper's linking of u_i->v to v->u_{i+1}); each circuit is cut
 //     before the root's first arc, which becomes the tour's head;
@@ -27,34 +28,16 @@ namespace fbcc {
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
 
-template <typename OffT>
-__device__ __forceinline__ int64_t find_arc(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
-                                            int32_t from, int32_t to)
-{
-    int64_t lo = off[from], hi = off[from + 1];
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (adj[mid] < to) lo = mid + 1; else hi = mid;
-    }
-    return lo;  // the arc exists in a valid (symmetric, sorted) CSR
-}
-
-// Tree degrees, and the tree bit of both arcs of every forest edge.
-template <typename OffT>
-__global__ void __launch_bounds__(kThreads) k_tree_count(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
-                                                         int64_t n, const int32_t *__restrict__ te_u,
-                                                         const int32_t *__restrict__ te_v, int32_t *tdeg,
-                                                         uint32_t *tree_bits)
+// Tree degree of every vertex from the forest edges.
+__global__ void __launch_bounds__(kThreads) k_tree_count(int64_t n, const int32_t *__restrict__ te_u,
+                                                         const int32_t *__restrict__ te_v, int32_t *tdeg)
 {
     GRID_STRIDE(h, n)
     {
         int32_t u = te_u[h];
         if (u < 0) continue;
-        int32_t v = te_v[h];
         atomicAdd(tdeg + u, 1);
-        atomicAdd(tdeg + v, 1);
-        set_bit(tree_bits, find_arc(off, adj, u, v));
-        set_bit(tree_bits, find_arc(off, adj, v, u));
+        atomicAdd(tdeg + te_v[h], 1);
     }
 }
 
@@ -380,8 +363,8 @@ __global__ void __launch_bounds__(kThreads) k_tour_records(const int32_t *__rest
 __global__ void __launch_bounds__(kThreads) k_root_tags(int64_t n, const int32_t *__restrict__ uf,
                                                         const int32_t *__restrict__ csize,
                                                         const int32_t *__restrict__ vbase, int2 *rec, int32_t *first,
-                                                        int32_t *last, int32_t *parent, int32_t *ord, int32_t *porig,
-                                                        int32_t *w1, int32_t *w2)
+                                                        int32_t *last, int32_t *parent, int2 *fp, int32_t *ord,
+                                                        int32_t *porig, int32_t *w1, int32_t *w2)
 {
     GRID_STRIDE(r, n)
     {
@@ -392,6 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_root_tags(int64_t n, const int32_t
         first[r] = b;
         last[r] = b + sz - 1;
         parent[r] = -1;
+        fp[r] = make_int2(b, -1);
         ord[b] = (int32_t)r;
         porig[b] = -1;
         w1[b] = b;
@@ -403,9 +387,9 @@ __global__ void __launch_bounds__(kThreads) k_root_tags(int64_t n, const int32_t
 // the number of counting positions before p: a down arc into v gives
 // first[v] = S(p) + 1, and the up arc leaving v gives last[v] = S(q).
 __global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *__restrict__ rec, int32_t *first,
-                                                       int32_t *last, int32_t *parent, int32_t *ord, int32_t *porig,
-                                                       int32_t *w1, int32_t *w2, long long *ticket, uint64_t *status,
-                                                       int *err)
+                                                       int32_t *last, int32_t *parent, int2 *fp, int32_t *ord,
+                                                       int32_t *porig, int32_t *w1, int32_t *w2, long long *ticket,
+                                                       uint64_t *status, int *err)
 {
     const int64_t ntiles = (n2 + kTile - 1) / kTile;
     const int64_t n = n2 / 2;
@@ -429,6 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *_
                 if (!in_range(fv, n, err) || !in_range(vtx, n, err)) continue;
                 first[vtx] = fv;
                 parent[vtx] = x;
+                fp[vtx] = make_int2(fv, x);
                 ord[fv] = vtx;
                 porig[fv] = x;
                 w1[fv] = fv;
@@ -450,7 +435,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
     CK(cudaMemsetAsync(d.tdeg, 0, (n + 1) * sizeof(int32_t), L.s));
-    k_tree_count<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, d.te_u, d.te_v, d.tdeg, d.tree_bits);
+    k_tree_count<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.tdeg);
     L.mark("k_tree_count");
     CK(cudaGetLastError());
     CK(launch_scan_i32(d, d.tdeg, d.toff, n, L));
@@ -505,15 +490,15 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_place");
     k_tour_records<<<ga, kThreads, 0, L.s>>>(d.toff, n, d.tadj, d.tsrc, d.twin, d.pos, d.rec);
     L.mark("k_tour_records");
-    k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.first, d.last, d.parent, d.ord,
-                                          d.porig, d.w1, d.w2);
+    k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.first, d.last, d.parent, d.fp,
+                                          d.ord, d.porig, d.w1, d.w2);
     L.mark("k_root_tags");
     CK(cudaGetLastError());
     const int64_t ntiles = ceil_div(2 * n, kTile);
     CK(cudaMemsetAsync(d.counters, 0, sizeof(long long), L.s));
     CK(cudaMemsetAsync(d.scan_status, 0, ntiles * sizeof(uint64_t), L.s));
-    k_preorder<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(2 * n, d.rec, d.first, d.last, d.parent, d.ord, d.porig,
-                                                           d.w1, d.w2, d.counters, d.scan_status, d.err);
+    k_preorder<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(2 * n, d.rec, d.first, d.last, d.parent, d.fp, d.ord,
+                                                           d.porig, d.w1, d.w2, d.counters, d.scan_status, d.err);
     L.mark("k_preorder");
 #undef CK
     return cudaGetLastError();

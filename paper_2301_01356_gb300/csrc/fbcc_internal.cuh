@@ -45,7 +45,6 @@ struct Dev {
     int32_t *uf;              // union-find parent (First-CC, then Last-CC)
     int32_t *te_u, *te_v;     // tree edge recorded at the vertex it hooked (-1: none)
     int32_t *tile_v;          // source vertex of the first arc of every arc tile (+1 sentinel)
-    uint32_t *tree_bits;      // one bit per arc: tree arc
     // Rooting
     int32_t *tdeg;            // tree degree, then fill cursor
     int32_t *toff;            // tree CSR offsets (n+1)
@@ -69,6 +68,7 @@ struct Dev {
     int2 *rec;                // tour record at every position (down/up arc, padding)
     // Tagging (first/last/parent indexed by vertex; the rest by preorder number)
     int32_t *first, *last, *parent;
+    int2 *fp;                 // {first, parent} by vertex: one gather gives both (tree test)
     int32_t *ord;             // vertex at preorder number p
     int32_t *porig;           // parent vertex of the vertex at preorder number p (-1 root)
     int32_t *w1, *w2;         // w1/w2 at preorder number p
@@ -80,7 +80,8 @@ struct Dev {
     int32_t *lp;              // plain-component pointer (root: itself), flattened in place
     uint8_t *ext;             // position referenced across an RMQ tile
     int32_t *qlist;           // compacted positions with ext set
-    int32_t *vplab;           // plain-component root of every vertex (by vertex)
+    int4 *cr;                 // by vertex {first, parent, plain-component root, last} (Last-CC arc pass)
+    int32_t *lastp;           // last[] by preorder number
     int32_t *fin;             // final skeleton-component root of every position
     int32_t *minorig;         // smallest vertex id of the component rooted at position r
     int32_t *smin;            // by label vertex: smallest vertex id of its label class
@@ -405,12 +406,6 @@ __device__ __forceinline__ void arc_tile_targets(const int32_t *__restrict__ adj
     }
 }
 
-// The tree bits of the thread's kItems arcs (a0 is a multiple of kItems = 8, so
-// they sit in one 32-bit word).
-__device__ __forceinline__ uint32_t arc_tile_treebits(const uint32_t *__restrict__ bits, int64_t a0)
-{
-    return (__ldg(bits + (a0 >> 5)) >> (a0 & 31)) & 0xffu;
-}
 
 // ---------------------------------------------------------------------------
 // Batched solves: many graphs packed as one disjoint union with global ids.
@@ -432,6 +427,13 @@ __device__ __forceinline__ int32_t graph_of(const int64_t *__restrict__ vtx_base
         if (__ldg(vtx_base + mid) <= v) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// An arc u->w of a simple graph is a tree arc iff one endpoint is the other's
+// parent in the rooted spanning forest (no parallel edges).
+__device__ __forceinline__ bool is_tree_arc(int32_t u, int32_t pu, int32_t w, int32_t pw)
+{
+    return pu == w || pw == u;
 }
 
 // ---------------------------------------------------------------------------
@@ -482,7 +484,7 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
                            bool vec, bool keep_low_high, const Launch &L);
 template <typename OffT>
 cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           bool vec, const Launch &L);
+                           int lcc_sample, bool vec, const Launch &L);
 template <typename OffT>
 cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap,

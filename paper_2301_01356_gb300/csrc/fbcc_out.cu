@@ -13,6 +13,8 @@
 //    (the child for a tree edge, the descendant for a back edge, either endpoint
 //    for a cross edge, which lies in G' and so joins two equally labelled vertices);
 //  - a tree edge p(v)-v is a bridge iff no edge leaves T_v (flag from tagging);
+//    its BCC is {v, p(v)} and v's label class is {v}, so an arc is a bridge
+//    exactly when the vertex that labels it carries the flag;
 //  - canonical BCC numbers: the key of a BCC is its smallest arc id with
 //    src < dst, which orders BCCs exactly like their smallest edge ids. Its source
 //    is u0 = min(smin(l), head(l)) (the BCC's smallest vertex). If u0 lies in this BCC
@@ -257,7 +259,6 @@ __global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, co
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                        int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
-                                                       const uint32_t *__restrict__ tree_bits,
                                                        const int2 *__restrict__ fo, int32_t *edge_bcc,
                                                        uint8_t *is_bridge, bool vec, bool vec_out)
 {
@@ -268,7 +269,6 @@ __global__ void __launch_bounds__(kThreads) k_edge_out(const OffT *__restrict__ 
     {
         arc_tile_sources(off, nnz, tile_v, t, win, at);
         if (!at.cnt) continue;
-        const uint32_t tb = arc_tile_treebits(tree_bits, at.a0);
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
         int32_t lab8[kItems];
@@ -282,9 +282,12 @@ __global__ void __launch_bounds__(kThreads) k_edge_out(const OffT *__restrict__ 
             if (j >= at.cnt) continue;
             if (at.src[j] != cur) { cur = at.src[j]; fs = __ldg(fo + cur); }
             const int2 fd = __ldg(fo + d[j]);
+            // x = the endpoint with the larger preorder number. If x's parent edge is
+            // a bridge, x's label class is {x} and that bridge is the only edge of
+            // its BCC, so every arc labelled through x is the bridge itself.
             const int32_t w = fd.x > fs.x ? fd.y : fs.y;
             lab8[j] = w & 0x7fffffff;
-            br8[j] = ((tb >> j) & 1u) ? (uint8_t)((uint32_t)w >> 31) : 0;
+            br8[j] = (uint8_t)((uint32_t)w >> 31);
         }
         if (vec_out && at.cnt == kItems) {
             int4 *o = reinterpret_cast<int4 *>(edge_bcc + at.a0);
@@ -340,7 +343,7 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
         k_fo<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.rank, d.first, d.vbits, d.fo, d.stats);
         L.mark("k_fo");
         const bool vec_out = ((uintptr_t)edge_bcc & 15) == 0 && ((uintptr_t)is_bridge & 7) == 0;
-        k_edge_out<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits,
+        k_edge_out<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles,
                                                                    d.fo, edge_bcc, is_bridge, vec, vec_out);
         L.mark("k_edge_out");
     } else if (B.G > 0) {

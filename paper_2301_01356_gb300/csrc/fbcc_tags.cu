@@ -24,8 +24,7 @@ namespace fbcc {
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                   int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
-                                                  const uint32_t *__restrict__ tree_bits,
-                                                  const int32_t *__restrict__ first, int32_t *w1, int32_t *w2,
+                                                  const int2 *__restrict__ fp, int32_t *w1, int32_t *w2,
                                                   int64_t n, int *err, bool vec)
 {
     __shared__ OffT win_all[kWarpsPerCta * kWarpWin];
@@ -35,30 +34,28 @@ __global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, 
     {
         arc_tile_sources(off, nnz, tile_v, t, win, at);
         if (!at.cnt) continue;
-        uint32_t tb = arc_tile_treebits(tree_bits, at.a0);
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
         int32_t cur = -1, mn = INT32_MAX, mx = INT32_MIN;
+        int2 fc = make_int2(0, -1);
 #pragma unroll
         for (int j = 0; j <= kItems; ++j) {
             bool live = j < at.cnt;
             if (!live || at.src[j] != cur) {
-                if (cur >= 0 && mn != INT32_MAX) {
-                    int32_t fc = __ldg(first + cur);
-                    if (in_range(fc, n, err)) {
-                        if (mn < fc) atomicMin(w1 + fc, mn);
-                        if (mx > fc) atomicMax(w2 + fc, mx);
-                    }
+                if (cur >= 0 && mn != INT32_MAX && in_range(fc.x, n, err)) {
+                    if (mn < fc.x) atomicMin(w1 + fc.x, mn);
+                    if (mx > fc.x) atomicMax(w2 + fc.x, mx);
                 }
                 if (!live) break;
                 cur = at.src[j];
+                fc = __ldg(fp + cur);
                 mn = INT32_MAX;
                 mx = INT32_MIN;
             }
-            if ((tb >> j) & 1u) continue;
-            int32_t f = __ldg(first + d[j]);
-            mn = f < mn ? f : mn;
-            mx = f > mx ? f : mx;
+            const int2 fd = __ldg(fp + d[j]);
+            if (is_tree_arc(cur, fc.y, d[j], fd.y)) continue;
+            mn = fd.x < mn ? fd.x : mn;
+            mx = fd.x > mx ? fd.x : mx;
         }
     }
 }
@@ -158,7 +155,8 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                                                         const int32_t *__restrict__ porig,
                                                         const int32_t *__restrict__ first,
                                                         const int32_t *__restrict__ last, uint8_t *vbits, int32_t *lp,
-                                                        uint8_t *ext, int32_t *low_out, int32_t *high_out, int *err)
+                                                        uint8_t *ext, int32_t *lastp, int32_t *low_out,
+                                                        int32_t *high_out, int *err)
 {
     constexpr int kPer = kRmqTile / kThreads;
     constexpr int kNChunk = kRmqTile / kChunk;
@@ -211,6 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
             const int32_t vp = ord[p];
             int32_t e = (uint32_t)vp < (uint64_t)n ? __ldg(last + vp) : (int32_t)p;
             if (e < p || e >= n) { atomicOr(err, kErrIndex); e = (int32_t)p; }
+            lastp[p] = e;
             int32_t lo, hi;
             const int ci = i / kChunk;
             if (e < base + kRmqTile) {
@@ -300,7 +299,7 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
 {
     const int64_t ntiles = ceil_div(nnz, kWTile);
     if (nnz > 0) {
-        k_w12<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.tree_bits, d.first,
+        k_w12<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.fp,
                                                               d.w1, d.w2, n, d.err, vec);
         L.mark("k_w12");
     }
@@ -317,7 +316,7 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
     if (e != cudaSuccess) return e;
     k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax,
                                                        d.rmq_tiles_max, d.ord, d.porig, d.first, d.last,
-                                                       d.vbits, d.lp, d.ext, keep_low_high ? d.low : nullptr,
+                                                       d.vbits, d.lp, d.ext, d.lastp, keep_low_high ? d.low : nullptr,
                                                        keep_low_high ? d.high : nullptr, d.err);
     L.mark("k_rmq_query");
     return cudaGetLastError();

@@ -250,6 +250,11 @@ def workload_batch_4096() -> Batch:
     return batch(4096, 4, 1000, 1000000)
 
 
+def workload_rmat_22() -> Graph:
+    """The R-MAT recipe at scale 22 (a quarter of the vertices); profiler captures."""
+    return rmat(22, 16, 0.57, 0.19, 0.19, 3)
+
+
 def workload_rmat_24() -> Graph:
     """R-MAT scale 24, edge factor 16, (a,b,c) = (0.57, 0.19, 0.19), seed 3."""
     return rmat(24, 16, 0.57, 0.19, 0.19, 3)

@@ -107,7 +107,7 @@ def test_repeated_solves_and_configs(torch_cuda, oracle):
     e1, e2 = oracle.solve(g1.offsets, g1.adj), oracle.solve(g2.offsets, g2.adj)
     for cfg in ({}, {"ruler_stride": 8}, {"ruler_stride": 256}, {"cc_sample": 2}, {"use_graph": -1},
                 {"grid_ctas": 3}, {"chase_chains": 4}, {"chase_chains": 2}, {"cc_local": 1024},
-                {"cc_local": 16384}):
+                {"cc_local": 16384}, {"lcc_sample": 2}, {"lcc_sample": 1, "cc_sample": 2}):
         s = fbcc.Solver(20000, 50000, **cfg)
         for _ in range(2):
             for g, e in ((g1, e1), (g2, e2), (g1, e1)):

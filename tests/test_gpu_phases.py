@@ -136,3 +136,4 @@ def test_phases(torch_cuda, family):
     }[family]()
     phase_check(torch_cuda, g)
     phase_check(torch_cuda, g, {"ruler_stride": 8, "cc_local": 4096})
+    phase_check(torch_cuda, g, {"cc_sample": 2, "lcc_sample": 2})
