@@ -91,12 +91,8 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     const size_t shared_from = c.used;
     d.te_u = c.take<int32_t>(N);
     d.te_v = c.take<int32_t>(N);
-    d.tdeg = c.take<int32_t>(N + 1);
-    d.toff = c.take<int32_t>(N + 1);
-    d.tadj = c.take<int32_t>(2 * N);
-    d.twin = c.take<int32_t>(2 * N);
-    d.tsrc = c.take<int32_t>(2 * N);
-    d.succ = c.take<int32_t>(2 * N);
+    d.lhead = c.take<int32_t>(N);
+    d.nxt = c.take<int32_t>(2 * N);
     d.is_head = c.take<uint8_t>(2 * N);
     d.link = c.take<int2>(2 * N);
     d.relem = c.take<int32_t>(d.ruler_max);

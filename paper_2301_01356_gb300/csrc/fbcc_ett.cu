@@ -3,9 +3,10 @@
 // component's smallest vertex and derive, per vertex, its parent, its preorder
 // number first[v] and last[v] = first[v] + |T_v| - 1.
 //
-//  1. tree CSR: both arcs of every forest edge, grouped by source (counting sort),
-//     with the index of each arc's reverse (twin); the arc passes later recognise
-//     tree arcs by the parent relation, so the CSR itself is never marked;
+//  1. forest arcs: the edge recorded at hooked vertex h gives arcs 2h and 2h+1
+//     (reverse = a ^ 1, no sort needed), and each vertex's arcs are chained into a
+//     list (the paper semisorts the arcs by source instead); the arc passes later
+//     recognise tree arcs by the parent relation, so the CSR is never marked;
 //  2. Euler circuit: the arc u->v is followed by the arc after v->u in v's list,
 //     cyclically (the paper's linking of u_i->v to v->u_{i+1}); each circuit is cut
 //     before the root's first arc, which becomes the tour's head;
@@ -28,87 +29,61 @@ namespace fbcc {
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
 
-// Tree degree of every vertex from the forest edges.
-__global__ void __launch_bounds__(kThreads) k_tree_count(int64_t n, const int32_t *__restrict__ te_u,
-                                                         const int32_t *__restrict__ te_v, int32_t *tdeg)
+// Forest arcs: the edge recorded at hooked vertex h gives arcs 2h = u->v and
+// 2h+1 = v->u, so an arc's reverse is a ^ 1 and ids need no scan; ids of vertices
+// that hooked nothing are unused. Each vertex's arcs form a list threaded through
+// nxt[] (pushed with atomicExch, in arbitrary order), headed by lhead[].
+__device__ __forceinline__ int32_t arc_src(const int32_t *te_u, const int32_t *te_v, int64_t a)
+{
+    return (a & 1) ? te_v[a >> 1] : te_u[a >> 1];
+}
+
+__device__ __forceinline__ int32_t arc_dst(const int32_t *te_u, const int32_t *te_v, int64_t a)
+{
+    return (a & 1) ? te_u[a >> 1] : te_v[a >> 1];
+}
+
+__global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__restrict__ te_u,
+                                                   const int32_t *__restrict__ te_v, int32_t *lhead, int32_t *nxt)
 {
     GRID_STRIDE(h, n)
     {
-        int32_t u = te_u[h];
+        const int32_t u = te_u[h];
         if (u < 0) continue;
-        atomicAdd(tdeg + u, 1);
-        atomicAdd(tdeg + te_v[h], 1);
+        nxt[2 * h] = atomicExch(lhead + u, (int32_t)(2 * h));
+        nxt[2 * h + 1] = atomicExch(lhead + te_v[h], (int32_t)(2 * h + 1));
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_tree_fill(int64_t n, const int32_t *__restrict__ te_u,
-                                                        const int32_t *__restrict__ te_v, const int32_t *__restrict__ toff,
-                                                        int32_t *cursor, int32_t *tadj, int32_t *tsrc, int32_t *twin,
-                                                        int *err)
-{
-    GRID_STRIDE(h, n)
-    {
-        int32_t u = te_u[h];
-        if (u < 0) continue;
-        int32_t v = te_v[h];
-        int32_t su = toff[u] + atomicAdd(cursor + u, 1);
-        int32_t sv = toff[v] + atomicAdd(cursor + v, 1);
-        if (!in_range(su, toff[u + 1], err) || !in_range(sv, toff[v + 1], err)) continue;
-        tadj[su] = v;
-        tadj[sv] = u;
-        tsrc[su] = u;
-        tsrc[sv] = v;
-        twin[su] = sv;
-        twin[sv] = su;
-    }
-}
-
-// succ[s] for s = x->y: the arc after twin(s) = y->x in y's list, cyclically.
-__global__ void __launch_bounds__(kThreads) k_succ(int64_t n2, const int32_t *__restrict__ toff, int64_t n,
-                                                   const int32_t *__restrict__ tadj, const int32_t *__restrict__ twin,
-                                                   int32_t *succ, uint8_t *is_head)
-{
-    const int64_t A = toff[n];
-    (void)n2;
-    GRID_STRIDE(s, A)
-    {
-        int32_t y = tadj[s];
-        int32_t nx = twin[s] + 1;
-        succ[s] = nx < toff[y + 1] ? nx : toff[y];
-        is_head[s] = 0;
-    }
-}
-
-// Per component root r (uf[r] == r) with tree arcs: its first arc heads the tour;
-// the arc entering r just before that one (the twin of r's last arc) ends it.
-__global__ void __launch_bounds__(kThreads) k_tour_cut(int64_t n, const int32_t *__restrict__ uf,
-                                                       const int32_t *__restrict__ toff, const int32_t *__restrict__ twin,
-                                                       int32_t *succ, uint8_t *is_head)
-{
-    GRID_STRIDE(r, n)
-    {
-        if (uf[r] != r || toff[r + 1] == toff[r]) continue;
-        is_head[toff[r]] = 1;
-        succ[twin[toff[r + 1] - 1]] = -1;
-    }
-}
-
-// Rulers: tour heads and every arc whose index is a multiple of the stride.
-// link[s] = {succ[s], ruler id or -1}; relem[id] = s. Ids come from one atomic
-// per CTA and iteration (a per-warp atomic on a single counter serialises).
-__global__ void __launch_bounds__(kThreads) k_rulers(const int32_t *__restrict__ toff, int64_t n, int stride,
-                                                     const int32_t *__restrict__ succ,
-                                                     const uint8_t *__restrict__ is_head, int2 *link, int32_t *relem,
-                                                     long long *nr)
+// Euler successor of every arc and the rulers of the list ranking, in one pass.
+// succ(a) for a = x->y is the arc after a^1 in y's list, cyclically; when y is a
+// component root the wrap-around ends the tour instead, and the first arc of the
+// root's list heads it. Rulers: tour heads plus every arc id divisible by the
+// stride. link[a] = {succ, ruler id or -1}; relem[id] = a. Ids come from one
+// atomic per CTA and iteration.
+__global__ void __launch_bounds__(kThreads) k_succ_rulers(int64_t n, const int32_t *__restrict__ te_u,
+                                                          const int32_t *__restrict__ te_v,
+                                                          const int32_t *__restrict__ uf,
+                                                          const int32_t *__restrict__ lhead,
+                                                          const int32_t *__restrict__ nxt, int stride, int2 *link,
+                                                          uint8_t *is_head, int32_t *relem, long long *nr)
 {
     __shared__ int32_t warp_cnt[kThreads / 32];
     __shared__ long long block_base;
-    const int64_t A = toff[n];
+    const int64_t A = 2 * n;
     const int64_t A_pad = (A + kThreads - 1) / kThreads * kThreads;  // whole CTAs take part
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int64_t s = blockIdx.x * (int64_t)kThreads + threadIdx.x; s < A_pad; s += (int64_t)gridDim.x * kThreads) {
-        const bool in = s < A;
-        const bool ruler = in && (is_head[s] || (s & (stride - 1)) == 0);
+    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < A_pad; a += (int64_t)gridDim.x * kThreads) {
+        const bool in = a < A && te_u[a >> 1] >= 0;
+        int32_t sc = -1;
+        bool head = false;
+        if (in) {
+            const int32_t x = arc_src(te_u, te_v, a), y = arc_dst(te_u, te_v, a);
+            const int32_t nx = nxt[a ^ 1];
+            sc = nx >= 0 ? nx : (uf[y] == y ? -1 : lhead[y]);
+            head = uf[x] == x && lhead[x] == a;
+        }
+        const bool ruler = in && (head || (a & (stride - 1)) == 0);
         const unsigned mask = __ballot_sync(0xffffffffu, ruler);
         if (lane == 0) warp_cnt[wid] = __popc(mask);
         __syncthreads();
@@ -126,9 +101,10 @@ __global__ void __launch_bounds__(kThreads) k_rulers(const int32_t *__restrict__
         int32_t id = -1;
         if (ruler) {
             id = (int32_t)(base + __popc(mask & ((1u << lane) - 1u)));
-            relem[id] = (int32_t)s;
+            relem[id] = (int32_t)a;
         }
-        link[s] = make_int2(succ[s], id);
+        link[a] = make_int2(sc, id);
+        is_head[a] = head;
     }
 }
 
@@ -136,12 +112,12 @@ __global__ void __launch_bounds__(kThreads) k_rulers(const int32_t *__restrict__
 // thread advances kChains rulers' walks in lock step, so it keeps that many
 // independent loads in flight (the walk is bound by load latency).
 template <int kChains>
-__global__ void __launch_bounds__(kThreads) k_chase(const int32_t *__restrict__ toff, int64_t n,
+__global__ void __launch_bounds__(kThreads) k_chase(int64_t n,
                                                     const long long *__restrict__ nr_p, const int32_t *__restrict__ relem,
                                                     const int2 *__restrict__ link, int2 *oo, int32_t *rnext,
                                                     int32_t *rlen, int *err)
 {
-    const int64_t A = toff[n];
+    const int64_t A = 2 * n;
     const int64_t nr = *nr_p;
     const int64_t T = (int64_t)gridDim.x * kThreads;
     for (int64_t r0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; r0 < nr; r0 += T * kChains) {
@@ -305,9 +281,9 @@ __global__ void __launch_bounds__(kThreads) k_jump(const long long *__restrict__
 
 // Component size at its root: 1 for an isolated root, else tour length / 2 + 1.
 __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t *__restrict__ uf,
-                                                        const int32_t *__restrict__ toff, const int2 *__restrict__ link,
-                                                        const int32_t *__restrict__ sd, const long long *nr_p,
-                                                        int32_t *csize, int *err)
+                                                        const int32_t *__restrict__ lhead,
+                                                        const int2 *__restrict__ link, const int32_t *__restrict__ sd,
+                                                        const long long *nr_p, int32_t *csize, int *err)
 {
     const int64_t nr = *nr_p;
     GRID_STRIDE(v, n)
@@ -315,8 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t
         int32_t c = 0;
         if (uf[v] == v) {
             c = 1;
-            if (toff[v + 1] != toff[v]) {
-                const int32_t id = link[toff[v]].y;
+            if (lhead[v] >= 0) {
+                const int32_t id = link[lhead[v]].y;
                 if (in_range(id, nr, err)) c = sd[id] / 2 + 1;
             }
         }
@@ -325,16 +301,16 @@ __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t
 }
 
 // Tour position of every tree arc: 2*base + L - (arcs from it to the tour's end).
-__global__ void __launch_bounds__(kThreads) k_place(const int32_t *__restrict__ toff, int64_t n,
-                                                    const int32_t *__restrict__ tadj, const int32_t *__restrict__ uf,
+__global__ void __launch_bounds__(kThreads) k_place(int64_t n, const int32_t *__restrict__ te_u,
+                                                    const int32_t *__restrict__ te_v, const int32_t *__restrict__ uf,
                                                     const int32_t *__restrict__ csize, const int32_t *__restrict__ vbase,
                                                     const int2 *__restrict__ oo, const int32_t *__restrict__ sd,
                                                     int32_t *pos, int *err)
 {
-    const int64_t A = toff[n];
-    GRID_STRIDE(s, A)
+    GRID_STRIDE(s, 2 * n)
     {
-        const int32_t r = uf[tadj[s]];
+        if (te_u[s >> 1] < 0) continue;
+        const int32_t r = uf[arc_dst(te_u, te_v, s)];
         const int32_t L = 2 * (csize[r] - 1);
         const int2 o = oo[s];
         const int32_t dist = sd[o.x] - o.y;
@@ -344,18 +320,17 @@ __global__ void __launch_bounds__(kThreads) k_place(const int32_t *__restrict__ 
 
 // Tour record at every arc's position: a down arc (it precedes its reverse)
 // stores {child, parent}; an up arc stores {-1, the child it leaves}.
-__global__ void __launch_bounds__(kThreads) k_tour_records(const int32_t *__restrict__ toff, int64_t n,
-                                                           const int32_t *__restrict__ tadj,
-                                                           const int32_t *__restrict__ tsrc,
-                                                           const int32_t *__restrict__ twin,
+__global__ void __launch_bounds__(kThreads) k_tour_records(int64_t n, const int32_t *__restrict__ te_u,
+                                                           const int32_t *__restrict__ te_v,
                                                            const int32_t *__restrict__ pos, int2 *rec)
 {
-    const int64_t A = toff[n];
-    GRID_STRIDE(s, A)
+    GRID_STRIDE(s, 2 * n)
     {
-        const int32_t p = pos[s], q = pos[twin[s]];
+        if (te_u[s >> 1] < 0) continue;
+        const int32_t p = pos[s], q = pos[s ^ 1];
         if (p < 0) continue;
-        rec[p] = p < q ? make_int2(tadj[s], tsrc[s]) : make_int2(-1, tsrc[s]);
+        const int32_t x = arc_src(te_u, te_v, s);
+        rec[p] = p < q ? make_int2(arc_dst(te_u, te_v, s), x) : make_int2(-1, x);
     }
 }
 
@@ -434,32 +409,24 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     const int ga = grid_for(L, ceil_div(2 * n, kThreads));
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-    CK(cudaMemsetAsync(d.tdeg, 0, (n + 1) * sizeof(int32_t), L.s));
-    k_tree_count<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.tdeg);
-    L.mark("k_tree_count");
-    CK(cudaGetLastError());
-    CK(launch_scan_i32(d, d.tdeg, d.toff, n, L));
-    CK(cudaMemsetAsync(d.tdeg, 0, (n + 1) * sizeof(int32_t), L.s));
-    k_tree_fill<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.toff, d.tdeg, d.tadj, d.tsrc, d.twin, d.err);
-    L.mark("k_tree_fill");
-    k_succ<<<ga, kThreads, 0, L.s>>>(2 * n, d.toff, n, d.tadj, d.twin, d.succ, d.is_head);
-    L.mark("k_succ");
-    k_tour_cut<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.toff, d.twin, d.succ, d.is_head);
-    L.mark("k_tour_cut");
+    CK(cudaMemsetAsync(d.lhead, 0xff, n * sizeof(int32_t), L.s));
+    k_link<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.lhead, d.nxt);
+    L.mark("k_link");
     long long *nr = d.counters + 1;
     CK(cudaMemsetAsync(nr, 0, sizeof(long long), L.s));
-    k_rulers<<<ga, kThreads, 0, L.s>>>(d.toff, n, ruler_stride, d.succ, d.is_head, d.link, d.relem, nr);
-    L.mark("k_rulers");
+    k_succ_rulers<<<ga, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.lhead, d.nxt, ruler_stride, d.link, d.is_head,
+                                            d.relem, nr);
+    L.mark("k_succ_rulers");
     // upper bound on the number of rulers: a head per tour (a tour spans at least
     // two vertices) plus one per stride
     const int64_t rbound = n / 2 + ceil_div(2 * n, ruler_stride) + 1;
     const int gr = grid_for(L, ceil_div(rbound, kThreads));
     if (chase_chains >= 4)
-        k_chase<4><<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
+        k_chase<4><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
     else if (chase_chains == 2)
-        k_chase<2><<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
+        k_chase<2><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
     else
-        k_chase<1><<<gr, kThreads, 0, L.s>>>(d.toff, n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
+        k_chase<1><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
     L.mark("k_chase");
     long long *nr2 = d.counters + 3;
     CK(cudaMemsetAsync(nr2, 0, sizeof(long long), L.s));
@@ -482,13 +449,13 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     k_expand2<<<gr, kThreads, 0, L.s>>>(nr, d.l2, d.rlen, d.owner2, d.offs2, d.rval[cur], d.sd1);
     L.mark("k_expand2");
     const int32_t *sd = d.sd1;
-    k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.toff, d.link, sd, nr, d.csize, d.err);
+    k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.lhead, d.link, sd, nr, d.csize, d.err);
     L.mark("k_comp_size");
     CK(cudaGetLastError());
     CK(launch_scan_i32(d, d.csize, d.vbase, n, L));
-    k_place<<<ga, kThreads, 0, L.s>>>(d.toff, n, d.tadj, d.uf, d.csize, d.vbase, d.oo, sd, d.pos, d.err);
+    k_place<<<ga, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.csize, d.vbase, d.oo, sd, d.pos, d.err);
     L.mark("k_place");
-    k_tour_records<<<ga, kThreads, 0, L.s>>>(d.toff, n, d.tadj, d.tsrc, d.twin, d.pos, d.rec);
+    k_tour_records<<<ga, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.pos, d.rec);
     L.mark("k_tour_records");
     k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.first, d.last, d.parent, d.fp,
                                           d.ord, d.porig, d.w1, d.w2);

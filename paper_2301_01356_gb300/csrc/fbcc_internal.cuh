@@ -46,11 +46,8 @@ struct Dev {
     int32_t *te_u, *te_v;     // tree edge recorded at the vertex it hooked (-1: none)
     int32_t *tile_v;          // source vertex of the first arc of every arc tile (+1 sentinel)
     // Rooting
-    int32_t *tdeg;            // tree degree, then fill cursor
-    int32_t *toff;            // tree CSR offsets (n+1)
-    int32_t *tadj, *twin;     // tree CSR targets and reverse-arc index (2n)
-    int32_t *tsrc;            // tree CSR source of every arc (2n)
-    int32_t *succ;            // Euler-circuit successor (2n), -1 at a tour's end
+    int32_t *lhead;           // first forest arc of every vertex's list (-1: none)
+    int32_t *nxt;             // next arc in its source's list (2n ids; -1: last)
     uint8_t *is_head;         // first arc of a tour (2n)
     int2 *link;               // {succ, ruler id or -1} per tree arc
     int32_t *relem;           // arc of ruler r
