@@ -150,29 +150,26 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_cc_init": B * (n + 1) + 8 * n,
         "k_cc_hook": B * (n + 1) + 4 * nnz + 2 * nnz + 8 * (n - n_cc),
         "k_uf_compress": 8 * n,
-        "k_tree_count": 8 * n + 16 * (n - n_cc),
         "k_scan_i32": 8 * n,
-        "k_tree_fill": 8 * n + 8 * A + 16 * A,
-        "k_succ": 21 * A,
-        "k_tour_cut": 12 * n,
-        "k_rulers": 13 * A + 4 * nr,
+        "k_link": 12 * n + 4 * A,
+        "k_succ_rulers": 16 * n + 13 * A + 4 * nr,
         "k_chase": 16 * A + 16 * nr,
         "k_jump": 24 * nr,
         "k_comp_size": 16 * n,
         "k_place": 36 * A,
         "k_root_tags": 12 * n_cc,
-        "k_preorder": 8 * n + 8 * A + 32 * n,
+        "k_preorder": 16 * n + 28 * n,
         "k_w12": B * (n + 1) + 4 * nnz + nnz // 8 + 4 * nnz + 8 * n,
         "k_rmq_prefix": 16 * n,
         "k_iota": 4 * n,
-        "k_rmq_query": 45 * n,
+        "k_rmq_query": 41 * n,
         "k_last_cc_cross": B * (n + 1) + 8 * nnz + nnz // 8 + 8 * n,
-        "k_heads": 12 * n,
-        "k_label_count": 12 * n,
-        "k_ap_keys": 13 * n,
-        "k_key_bits": 16 * n,
+        "k_heads": 16 * n,
+        "k_label_count": 16 * n,
+        "k_ap_keys": 17 * n,
+        "k_key_bits": 20 * n,
         "k_scan_popc": nnz // 4,
-        "k_rank": 16 * n,
+        "k_rank": 20 * n,
         "k_fo": 25 * n,
         "k_edge_out": B * (n + 1) + 4 * nnz + nnz // 8 + 8 * nnz + 4 * nnz + nnz,
         "k_cc_local": B * (n + 1) + 4 * nnz + 12 * n,
@@ -189,6 +186,11 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_lcc_sample": B * (n + 1) + 16 * n + 32 * n,
         "k_pos_compress": 8 * n,
         "k_last_cc_cross_skip": B * (n + 1) + 4 * nnz + 16 * n,
+        # sampled variants (two sampled neighbours per vertex) and the key scan
+        # (offsets and selection flags; the scanned lists are few)
+        "k_cc_sample": B * (n + 1) + 8 * n + 8 * n,
+        "k_cc_hook_skip": B * (n + 1) + 4 * nnz + 8 * n,
+        "k_key_scan": B * (n + 1) + n,
     }
     return table.get(kernel)
 
@@ -422,6 +424,31 @@ def run_gpu(args, world, rank, local):
     solver.close()
 
 
+def run_single(args, rank, local):
+    """One solve with direct launches (no graph replay, no timing loop): the
+    command profilers wrap, so that every launch of one solve is captured once."""
+    import torch
+    from paper_2301_01356_gb300 import fbcc
+
+    torch.cuda.set_device(local)
+    fn, off64, desc = WORKLOADS[args.workload]
+    g = fn()
+    off = torch.from_numpy(g.offsets.astype(np.int64 if off64 else np.int32)).cuda()
+    adj = torch.from_numpy(g.adj).cuda()
+    cfg = dict(tuned_config(args), use_graph=-1, profile=1)
+    solver = fbcc.Solver(g.n, g.nnz, **cfg)
+    solver.enqueue(off, adj)
+    torch.cuda.synchronize()
+    rows = fbcc.fbcc_profile(solver.ws)
+    st = solver.stats.as_dict()
+    solver.close()
+    if st["device_status"] != 0:
+        raise SystemExit(f"device status {st['device_status']}")
+    if rank == 0:
+        print(json.dumps({"workload": args.workload, "n": g.n, "m": g.m, "tuning": tuned_config(args),
+                          "launches": len(rows), "kernels": [name for name, _ in rows]}), flush=True)
+
+
 def run_batch(args, world, rank, local):
     """Config 4: thousands of graphs per launch vs a per-graph loop of the plain form."""
     import torch
@@ -638,6 +665,8 @@ def main(argv=None):
     ap.add_argument("--lcc-sample", type=int, default=None, help="Last-CC: cross edges sampled per vertex (0 = off)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-solve", action="store_true",
+                    help="run one solve with direct launches and exit (for profilers; no timing)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -656,6 +685,8 @@ def main(argv=None):
             run_batch(args, world, rank, local)
         elif args.workload == "serve":
             run_serve(args, world, rank, local)
+        elif args.single_solve:
+            run_single(args, rank, local)
         else:
             run_gpu(args, world, rank, local)
     finally:

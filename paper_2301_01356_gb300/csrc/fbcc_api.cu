@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 #include <new>
 
 #include "fbcc_internal.cuh"
@@ -79,10 +80,8 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.stats = c.take<fbcc_stats>(1);
     d.uf = c.take<int32_t>(N);
     d.tile_v = c.take<int32_t>(ceil_div(Z, kWTile) + 2);
-    d.first = c.take<int32_t>(N);
-    d.last = c.take<int32_t>(N);
-    d.parent = c.take<int32_t>(N);
     d.fp = c.take<int2>(N);
+    d.lastp = c.take<int32_t>(N);
     d.ord = c.take<int32_t>(N);
     d.porig = c.take<int32_t>(N);
     d.w1 = c.take<int32_t>(N);
@@ -126,7 +125,6 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.ext = c.take<uint8_t>(N);
     d.qlist = c.take<int32_t>(N);
     d.cr = c.take<int4>(N);
-    d.lastp = c.take<int32_t>(N);
     d.fin = c.take<int32_t>(N);
     d.minorig = c.take<int32_t>(N);
     d.smin = c.take<int32_t>(N);
@@ -607,10 +605,28 @@ extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *nam
     const Dev &d = ws->d;
     const void *src = nullptr;
     size_t elem = 4;
-    if (!strcmp(name, "first")) src = d.first;
-    else if (!strcmp(name, "last")) src = d.last;
-    else if (!strcmp(name, "parent")) src = d.parent;
-    else if (!strcmp(name, "label")) src = d.uf;
+    const bool f = !strcmp(name, "first"), pa = !strcmp(name, "parent"), la = !strcmp(name, "last");
+    if (f || pa || la) {
+        // by vertex, from fp = {first, parent}; last[v] = lastp[first[v]]
+        std::vector<int2> fp(size_t(count) + 1);
+        std::vector<int32_t> lastp;
+        API_CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+        API_CK(cudaMemcpy(fp.data(), d.fp, size_t(count) * sizeof(int2), cudaMemcpyDeviceToHost), "debug copy");
+        if (la) {
+            lastp.resize(size_t(count) + 1);
+            API_CK(cudaMemcpy(lastp.data(), d.lastp, size_t(count) * sizeof(int32_t), cudaMemcpyDeviceToHost),
+                   "debug copy");
+        }
+        int32_t *out = static_cast<int32_t *>(host_dst);
+        for (int64_t v = 0; v < count; ++v) {
+            const int32_t fv = fp[size_t(v)].x;
+            if (f) out[v] = fv;
+            else if (pa) out[v] = fp[size_t(v)].y;
+            else out[v] = fv >= 0 && fv < count ? lastp[size_t(fv)] : -1;
+        }
+        return FBCC_OK;
+    }
+    if (!strcmp(name, "label")) src = d.uf;
     else if (!strcmp(name, "w1")) src = d.w1;
     else if (!strcmp(name, "w2")) src = d.w2;
     else if (!strcmp(name, "low")) src = d.low;

@@ -329,17 +329,17 @@ __global__ void __launch_bounds__(kThreads) k_tour_records(int64_t n, const int3
         if (te_u[s >> 1] < 0) continue;
         const int32_t p = pos[s], q = pos[s ^ 1];
         if (p < 0) continue;
-        const int32_t x = arc_src(te_u, te_v, s);
-        rec[p] = p < q ? make_int2(arc_dst(te_u, te_v, s), x) : make_int2(-1, x);
+        // down arc x->y: {y, x}; up arc: {-1, distance back to its down arc}
+        rec[p] = p < q ? make_int2(arc_dst(te_u, te_v, s), arc_src(te_u, te_v, s)) : make_int2(-1, p - q);
     }
 }
 
 // Per component root: padding slots and the root's own tags.
 __global__ void __launch_bounds__(kThreads) k_root_tags(int64_t n, const int32_t *__restrict__ uf,
                                                         const int32_t *__restrict__ csize,
-                                                        const int32_t *__restrict__ vbase, int2 *rec, int32_t *first,
-                                                        int32_t *last, int32_t *parent, int2 *fp, int32_t *ord,
-                                                        int32_t *porig, int32_t *w1, int32_t *w2)
+                                                        const int32_t *__restrict__ vbase, int2 *rec, int2 *fp,
+                                                        int32_t *lastp, int32_t *ord, int32_t *porig, int32_t *w1,
+                                                        int32_t *w2)
 {
     GRID_STRIDE(r, n)
     {
@@ -347,10 +347,8 @@ __global__ void __launch_bounds__(kThreads) k_root_tags(int64_t n, const int32_t
         int32_t b = vbase[r], sz = csize[r];
         rec[2 * b + 2 * sz - 2] = make_int2(-2, 0);   // counts: the prefix restarts at the next base
         rec[2 * b + 2 * sz - 1] = make_int2(-3, 0);
-        first[r] = b;
-        last[r] = b + sz - 1;
-        parent[r] = -1;
         fp[r] = make_int2(b, -1);
+        lastp[b] = b + sz - 1;
         ord[b] = (int32_t)r;
         porig[b] = -1;
         w1[b] = b;
@@ -360,11 +358,13 @@ __global__ void __launch_bounds__(kThreads) k_root_tags(int64_t n, const int32_t
 
 // Preorder from the tour (single-pass scan over the 2n tour positions). With S(p)
 // the number of counting positions before p: a down arc into v gives
-// first[v] = S(p) + 1, and the up arc leaving v gives last[v] = S(q).
-__global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *__restrict__ rec, int32_t *first,
-                                                       int32_t *last, int32_t *parent, int2 *fp, int32_t *ord,
-                                                       int32_t *porig, int32_t *w1, int32_t *w2, long long *ticket,
-                                                       uint64_t *status, int *err)
+// first[v] = S(p) + 1, and the up arc leaving v gives last[v] = S(q). The tour
+// of T_v spans positions p..q, two per vertex, so size(v) = (q - p + 1) / 2 and
+// the up arc also knows first[v] = S(q) - (q - p - 1) / 2: it stores last by
+// preorder number. Only fp is written by vertex id.
+__global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *__restrict__ rec, int2 *fp,
+                                                       int32_t *lastp, int32_t *ord, int32_t *porig, int32_t *w1,
+                                                       int32_t *w2, long long *ticket, uint64_t *status, int *err)
 {
     const int64_t ntiles = (n2 + kTile - 1) / kTile;
     const int64_t n = n2 / 2;
@@ -386,15 +386,14 @@ __global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *_
             if (r[j].x >= 0) {
                 const int32_t vtx = r[j].x, x = r[j].y, fv = (int32_t)v[j] + 1;
                 if (!in_range(fv, n, err) || !in_range(vtx, n, err)) continue;
-                first[vtx] = fv;
-                parent[vtx] = x;
                 fp[vtx] = make_int2(fv, x);
                 ord[fv] = vtx;
                 porig[fv] = x;
                 w1[fv] = fv;
                 w2[fv] = fv;
             } else if (r[j].x == -1) {
-                if (in_range(r[j].y, n, err)) last[r[j].y] = (int32_t)v[j];
+                const int32_t e = (int32_t)v[j], fv = e - (r[j].y - 1) / 2;
+                if (in_range(fv, n, err) && fv <= e) lastp[fv] = e;
             }
         }
     }
@@ -457,15 +456,15 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_place");
     k_tour_records<<<ga, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.pos, d.rec);
     L.mark("k_tour_records");
-    k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.first, d.last, d.parent, d.fp,
-                                          d.ord, d.porig, d.w1, d.w2);
+    k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.fp, d.lastp, d.ord, d.porig, d.w1,
+                                          d.w2);
     L.mark("k_root_tags");
     CK(cudaGetLastError());
     const int64_t ntiles = ceil_div(2 * n, kTile);
     CK(cudaMemsetAsync(d.counters, 0, sizeof(long long), L.s));
     CK(cudaMemsetAsync(d.scan_status, 0, ntiles * sizeof(uint64_t), L.s));
-    k_preorder<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(2 * n, d.rec, d.first, d.last, d.parent, d.fp, d.ord,
-                                                           d.porig, d.w1, d.w2, d.counters, d.scan_status, d.err);
+    k_preorder<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(2 * n, d.rec, d.fp, d.lastp, d.ord, d.porig, d.w1, d.w2,
+                                                           d.counters, d.scan_status, d.err);
     L.mark("k_preorder");
 #undef CK
     return cudaGetLastError();

@@ -63,9 +63,8 @@ struct Dev {
     int32_t *vbase;           // first preorder number of the component at its root
     int32_t *pos;             // tour position of every tree arc
     int2 *rec;                // tour record at every position (down/up arc, padding)
-    // Tagging (first/last/parent indexed by vertex; the rest by preorder number)
-    int32_t *first, *last, *parent;
-    int2 *fp;                 // {first, parent} by vertex: one gather gives both (tree test)
+    // Tagging (fp indexed by vertex; the rest by preorder number)
+    int2 *fp;                 // {first, parent} by vertex (parent -1 at a root): one gather gives both
     int32_t *ord;             // vertex at preorder number p
     int32_t *porig;           // parent vertex of the vertex at preorder number p (-1 root)
     int32_t *w1, *w2;         // w1/w2 at preorder number p
@@ -78,7 +77,7 @@ struct Dev {
     uint8_t *ext;             // position referenced across an RMQ tile
     int32_t *qlist;           // compacted positions with ext set
     int4 *cr;                 // by vertex {first, parent, plain-component root, last} (Last-CC arc pass)
-    int32_t *lastp;           // last[] by preorder number
+    int32_t *lastp;           // last[] by preorder number (written by the preorder scan)
     int32_t *fin;             // final skeleton-component root of every position
     int32_t *minorig;         // smallest vertex id of the component rooted at position r
     int32_t *smin;            // by label vertex: smallest vertex id of its label class

@@ -29,12 +29,12 @@ namespace fbcc {
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
 
-__global__ void __launch_bounds__(kThreads) k_heads(int64_t n, const int32_t *__restrict__ parent,
+__global__ void __launch_bounds__(kThreads) k_heads(int64_t n, const int2 *__restrict__ fp,
                                                     const int32_t *__restrict__ lab, int32_t *head)
 {
     GRID_STRIDE(v, n)
     {
-        int32_t x = parent[v];
+        int32_t x = fp[v].y;
         if (x < 0) continue;
         int32_t l = lab[v];
         if (lab[x] != l) head[l] = x;
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_heads(int64_t n, const int32_t *__
 }
 
 // Labels: non-root v with lab[v] == v. Count them and how many each vertex heads.
-__global__ void __launch_bounds__(kThreads) k_label_count(int64_t n, const int32_t *__restrict__ parent,
+__global__ void __launch_bounds__(kThreads) k_label_count(int64_t n, const int2 *__restrict__ fp,
                                                           const int32_t *__restrict__ lab,
                                                           const int32_t *__restrict__ head, int32_t *nh,
                                                           fbcc_stats *stats, int *err)
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_label_count(int64_t n, const int32
     long long c = 0;
     GRID_STRIDE(v, n)
     {
-        if (parent[v] < 0 || lab[v] != v) continue;
+        if (fp[v].y < 0 || lab[v] != v) continue;
         if (in_range(head[v], n, err)) atomicAdd(nh + head[v], 1);
         ++c;
     }
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) k_label_count(int64_t n, const int32
 // Articulation points, component count, and the keys that need no list scan.
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__restrict__ off,
-                                                      const int32_t *__restrict__ parent, const int32_t *__restrict__ lab,
+                                                      const int2 *__restrict__ fp, const int32_t *__restrict__ lab,
                                                       const int32_t *__restrict__ head, const int32_t *__restrict__ nh,
                                                       const int32_t *__restrict__ smin,
                                                       uint8_t *is_ap, unsigned long long *key, uint8_t *scanv,
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
     long long nap = 0, ncc = 0;
     GRID_STRIDE(v, n)
     {
-        const bool root = parent[v] < 0;
+        const bool root = fp[v].y < 0;
         const int32_t h = nh[v];
         const uint8_t ap = root ? h >= 2 : h >= 1;
         is_ap[v] = ap;
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
         if (!in_range(hd, n, err)) continue;
         const int32_t sm = smin[v];
         const int32_t u0 = hd < sm ? hd : sm;
-        const int32_t in_bccs = (parent[u0] >= 0) + nh[u0];
+        const int32_t in_bccs = (fp[u0].y >= 0) + nh[u0];
         if (in_bccs == 1) {
             key[v] = (unsigned long long)off[u0];
         } else {
@@ -98,7 +98,7 @@ template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                        int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
                                                        const uint8_t *__restrict__ scanv,
-                                                       const int32_t *__restrict__ first,
+                                                       const int2 *__restrict__ fp,
                                                        const int32_t *__restrict__ lab,
                                                        const int32_t *__restrict__ head,
                                                        const int32_t *__restrict__ smin, unsigned long long *key,
@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
             if (!((sel >> j) & 1u)) continue;
             const int32_t u = at.src[j], w = d[j];
             if (w < u) continue;
-            if (u != cur) { cur = u; fcur = __ldg(first + u); last_l = -1; }
-            const int32_t x = __ldg(first + w) > fcur ? w : u;
+            if (u != cur) { cur = u; fcur = __ldg(&fp[u].x); last_l = -1; }
+            const int32_t x = __ldg(&fp[w].x) > fcur ? w : u;
             const int32_t l = __ldg(lab + x);
             if (l == last_l) continue;  // a later arc of the same BCC cannot be smaller
             last_l = l;
@@ -144,21 +144,21 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const int32_t *__restrict__ parent,
+__global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const int2 *__restrict__ fp,
                                                        const int32_t *__restrict__ lab,
                                                        const unsigned long long *__restrict__ key, uint32_t *key_bits,
                                                        int64_t nnz, int *err)
 {
     GRID_STRIDE(v, n)
     {
-        if (parent[v] < 0 || lab[v] != v) continue;
+        if (fp[v].y < 0 || lab[v] != v) continue;
         if (in_range((int64_t)key[v], nnz, err)) set_bit(key_bits, (int64_t)key[v]);
     }
 }
 
 // Rank of every label's key among all keys; heads go to their canonical slot. In
 // a batch, ranks and heads are made local to the label's graph.
-__global__ void __launch_bounds__(kThreads) k_rank(int64_t n, const int32_t *__restrict__ parent,
+__global__ void __launch_bounds__(kThreads) k_rank(int64_t n, const int2 *__restrict__ fp,
                                                    const int32_t *__restrict__ lab,
                                                    const unsigned long long *__restrict__ key,
                                                    const uint32_t *__restrict__ key_bits,
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_rank(int64_t n, const int32_t *__r
 {
     GRID_STRIDE(v, n)
     {
-        if (parent[v] < 0 || lab[v] != v) continue;
+        if (fp[v].y < 0 || lab[v] != v) continue;
         const int64_t k = (int64_t)key[v];
         if (!in_range(k, nnz, err)) continue;
         int32_t r = key_pre[k >> 5] + __popc(key_bits[k >> 5] & ((1u << (k & 31)) - 1u));
@@ -197,28 +197,28 @@ __global__ void __launch_bounds__(kThreads) k_bcc_base(Batch B, const uint32_t *
 }
 
 // Per vertex {first, output word}: word = BCC index of its label | bridge << 31.
-__global__ void __launch_bounds__(kThreads) k_fo(int64_t n, const int32_t *__restrict__ parent,
+__global__ void __launch_bounds__(kThreads) k_fo(int64_t n, const int2 *__restrict__ fp,
                                                  const int32_t *__restrict__ lab, const int32_t *__restrict__ rank,
-                                                 const int32_t *__restrict__ first, const uint8_t *__restrict__ vbits,
-                                                 int2 *fo, fbcc_stats *stats)
+                                                 const uint8_t *__restrict__ vbits, int2 *fo, fbcc_stats *stats)
 {
     long long nb = 0;
     GRID_STRIDE(v, n)
     {
         int32_t w = 0;
-        if (parent[v] >= 0) {
+        const int2 f = fp[v];
+        if (f.y >= 0) {
             const uint32_t br = vbits[v] & 1u;
             w = (int32_t)((uint32_t)rank[lab[v]] | (br << 31));
             nb += br;
         }
-        fo[v] = make_int2(first[v], w);
+        fo[v] = make_int2(f.x, w);
     }
     block_count((long long *)&stats->n_bridge, nb);
 }
 
 // Per-graph counts of a batch. A warp's vertices mostly belong to one graph:
 // lanes of the same graph reduce together and one lane adds.
-__global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, const int32_t *__restrict__ parent,
+__global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, const int2 *__restrict__ fp,
                                                           const uint8_t *__restrict__ is_ap,
                                                           const uint8_t *__restrict__ vbits, const int *err)
 {
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, co
         const int32_t g = in ? graph_of(B.vtx_base, B.G, v) : -1;
         unsigned long long ap = 0, cc = 0, br = 0;
         if (in) {
-            const bool root = parent[v] < 0;
+            const bool root = fp[v].y < 0;
             ap = is_ap[v];
             cc = root;
             br = !root && (vbits[v] & 1u);
@@ -318,19 +318,19 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     const int64_t nwords = ceil_div(nnz, 32);
     CK(cudaMemsetAsync(d.nh, 0, n * sizeof(int32_t), L.s));
     CK(cudaMemsetAsync(d.scanv, 0, n, L.s));
-    k_heads<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.head);
+    k_heads<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.head);
     L.mark("k_heads");
-    k_label_count<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.head, d.nh, d.stats, d.err);
+    k_label_count<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.head, d.nh, d.stats, d.err);
     L.mark("k_label_count");
-    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.parent, d.uf, d.head, d.nh, d.smin, is_ap, d.key, d.scanv, d.stats, d.err);
+    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.uf, d.head, d.nh, d.smin, is_ap, d.key, d.scanv, d.stats, d.err);
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
-        k_key_scan<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.first,
+        k_key_scan<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.fp,
                                                                    d.uf, d.head, d.smin, d.key, vec);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
-        k_key_bits<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.key, d.key_bits, nnz, d.err);
+        k_key_bits<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.key, d.key_bits, nnz, d.err);
         L.mark("k_key_bits");
         CK(cudaGetLastError());
         CK(launch_scan_popc(d, d.key_bits, d.key_pre, nwords, L));
@@ -338,9 +338,9 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
             k_bcc_base<<<grid_for(L, ceil_div(B.G + 1, kThreads)), kThreads, 0, L.s>>>(B, d.key_bits, d.key_pre);
             L.mark("k_bcc_base");
         }
-        k_rank<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.key, d.key_bits, d.key_pre, d.head, d.rank, bcc_head, B, nnz, d.err);
+        k_rank<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.key, d.key_bits, d.key_pre, d.head, d.rank, bcc_head, B, nnz, d.err);
         L.mark("k_rank");
-        k_fo<<<gv, kThreads, 0, L.s>>>(n, d.parent, d.uf, d.rank, d.first, d.vbits, d.fo, d.stats);
+        k_fo<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.rank, d.vbits, d.fo, d.stats);
         L.mark("k_fo");
         const bool vec_out = ((uintptr_t)edge_bcc & 15) == 0 && ((uintptr_t)is_bridge & 7) == 0;
         k_edge_out<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles,
@@ -351,7 +351,7 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     }
     if (B.G > 0) {
         CK(cudaMemsetAsync(B.stats, 0, B.G * sizeof(fbcc_stats), L.s));
-        k_batch_stats<<<gv, kThreads, 0, L.s>>>(n, B, d.parent, is_ap, d.vbits, d.err);
+        k_batch_stats<<<gv, kThreads, 0, L.s>>>(n, B, d.fp, is_ap, d.vbits, d.err);
         L.mark("k_batch_stats");
     }
 #undef CK

@@ -153,10 +153,9 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                                                         const int32_t *__restrict__ tmax, int64_t st_stride,
                                                         const int32_t *__restrict__ ord,
                                                         const int32_t *__restrict__ porig,
-                                                        const int32_t *__restrict__ first,
-                                                        const int32_t *__restrict__ last, uint8_t *vbits, int32_t *lp,
-                                                        uint8_t *ext, int32_t *lastp, int32_t *low_out,
-                                                        int32_t *high_out, int *err)
+                                                        const int2 *__restrict__ fp,
+                                                        const int32_t *__restrict__ lastp, uint8_t *vbits, int32_t *lp,
+                                                        uint8_t *ext, int32_t *low_out, int32_t *high_out, int *err)
 {
     constexpr int kPer = kRmqTile / kThreads;
     constexpr int kNChunk = kRmqTile / kChunk;
@@ -206,10 +205,8 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
             const int i = threadIdx.x + k * kThreads;
             const int64_t p = base + i;
             if (p >= n) continue;
-            const int32_t vp = ord[p];
-            int32_t e = (uint32_t)vp < (uint64_t)n ? __ldg(last + vp) : (int32_t)p;
+            int32_t e = lastp[p];
             if (e < p || e >= n) { atomicOr(err, kErrIndex); e = (int32_t)p; }
-            lastp[p] = e;
             int32_t lo, hi;
             const int ci = i / kChunk;
             if (e < base + kRmqTile) {
@@ -258,8 +255,8 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                 uint8_t bits = 0;
                 if (x >= 0) {
                     if (lo == (int32_t)p && hi <= e) bits |= 1;  // bridge: nothing leaves T_v
-                    const int32_t fx = __ldg(first + x);
-                    const bool fence = fx <= lo && __ldg(last + x) >= hi;
+                    const int32_t fx = __ldg(&fp[x].x);
+                    const bool fence = fx <= lo && (uint32_t)fx < (uint64_t)n && __ldg(lastp + fx) >= hi;
                     if (fence) bits |= 2;
                     else ptr = fx;                                // plain tree edge: in G'
                 }
@@ -315,8 +312,8 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
     cudaError_t e = cudaMemsetAsync(d.ext, 0, n, L.s);
     if (e != cudaSuccess) return e;
     k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax,
-                                                       d.rmq_tiles_max, d.ord, d.porig, d.first, d.last,
-                                                       d.vbits, d.lp, d.ext, d.lastp, keep_low_high ? d.low : nullptr,
+                                                       d.rmq_tiles_max, d.ord, d.porig, d.fp, d.lastp,
+                                                       d.vbits, d.lp, d.ext, keep_low_high ? d.low : nullptr,
                                                        keep_low_high ? d.high : nullptr, d.err);
     L.mark("k_rmq_query");
     return cudaGetLastError();

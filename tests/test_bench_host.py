@@ -25,8 +25,7 @@ def test_algorithmic_bytes_cover_every_kernel():
             src = open(os.path.join(ROOT, "paper_2301_01356_gb300", "csrc", f)).read()
             names |= set(re.findall(r'L\.mark\("(k_[a-z0-9_]+)"\)', src))
     assert len(names) > 30
-    skip = {"k_cc_sample", "k_cc_pick_big", "k_cc_hook_skip", "k_rmq_level", "k_bcc_base", "k_batch_stats", "k_pos_pick_big",
-            "k_finish", "k_key_scan"}
+    skip = {"k_cc_pick_big", "k_rmq_level", "k_bcc_base", "k_batch_stats", "k_pos_pick_big", "k_finish"}
     missing = [k for k in sorted(names - skip) if bench.algorithmic_bytes(k, 1000, 4000, 10, 4, 16) is None]
     assert not missing, missing
 
