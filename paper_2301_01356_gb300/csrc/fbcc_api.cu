@@ -90,6 +90,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     const size_t shared_from = c.used;
     d.te_u = c.take<int32_t>(N);
     d.te_v = c.take<int32_t>(N);
+    const size_t xl_from = c.used;
     d.lhead = c.take<int32_t>(N);
     d.nxt = c.take<int32_t>(2 * N);
     d.is_head = c.take<uint8_t>(2 * N);
@@ -112,6 +113,11 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.pos = c.take<int32_t>(2 * N);
     d.rec = c.take<int2>(2 * N);
     const size_t rooting_end = c.used;
+    {
+        const size_t at = (xl_from + 255) & ~size_t(255);
+        d.xl = base ? reinterpret_cast<int2 *>(base + at) : nullptr;
+        d.xl_cap = (int64_t)((rooting_end - at) / sizeof(int2));
+    }
     // tagging, Last-CC and output scratch (alive only after rooting has finished)
     c.used = shared_from;
     d.pmin = c.take<int32_t>(N);

@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_skip(const OffT *__restric
 // threads cannot leave a vertex pointing at a non-root (see uf_root).
 __global__ void __launch_bounds__(kThreads) k_uf_compress(int32_t *uf, int64_t n)
 {
-    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads)
-        uf[v] = uf_root(uf, (int32_t)v);
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads)
+        uf_flatten_warp(uf, v, v < n);
 }
 
 // The root of the component holding most sampled vertices: a vote over a fixed
@@ -162,9 +163,18 @@ __global__ void __launch_bounds__(kThreads) k_cc_pick_big(int32_t *uf, int64_t n
 // Local-first variant: each CTA owns a range of V consecutive vertex ids and
 // unites the edges inside the range in shared memory (graphs whose ids follow
 // their geometry, such as grids or meshes, keep most edges inside a range); the
-// range's sets then enter the global union-find flattened, and only edges
-// between ranges are hooked globally.
+// range's sets then enter the global union-find flattened.
+//
+// Edges between ranges (u < w) are gathered into a list on the way and hooked
+// level by level: an edge between ranges r and r' belongs to level
+// floor(log2(r xor r')), the level at which a binary merge tree over the ranges
+// first puts r and r' together. Hooking every boundary at once would let a
+// component that crosses R ranges hang its ranges' roots in a chain of length R
+// (each root hooked under its lower neighbour's while that one is hooked in
+// turn); in level order the chains stay within the number of levels. When the
+// list outgrows its space the global pass falls back to one full arc scan.
 constexpr int kLocalThreads = 512;
+constexpr int kXBuf = 4096;   // per-CTA staging of edges between ranges
 
 __device__ __forceinline__ int32_t sm_find(int32_t *par, int32_t v)
 {
@@ -181,11 +191,15 @@ __device__ __forceinline__ int32_t sm_find(int32_t *par, int32_t v)
 template <typename OffT>
 __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restrict__ off,
                                                             const int32_t *__restrict__ adj, int64_t n, int V,
-                                                            int32_t *uf, int32_t *te_u, int32_t *te_v, int *err)
+                                                            int32_t *uf, int32_t *te_u, int32_t *te_v, int2 *xl,
+                                                            int64_t xl_cap, long long *nxl, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    OffT *woff = reinterpret_cast<OffT *>(smem);                       // V+1 offsets
-    int32_t *par = reinterpret_cast<int32_t *>(smem + (size_t)(V + 1) * sizeof(OffT) + 8);
+    int2 *xbuf = reinterpret_cast<int2 *>(smem);                                    // kXBuf staged edges
+    OffT *woff = reinterpret_cast<OffT *>(smem + kXBuf * sizeof(int2));             // V+1 offsets
+    int32_t *par = reinterpret_cast<int32_t *>(smem + kXBuf * sizeof(int2) + (size_t)(V + 1) * sizeof(OffT) + 8);
+    __shared__ int xcount;
+    __shared__ long long xbase;
     const int64_t nranges = (n + V - 1) / V;
     for (int64_t g = blockIdx.x; g < nranges; g += gridDim.x) {
         const int64_t v0 = g * V;
@@ -195,6 +209,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
             woff[i] = off[v0 + i];
             if (i < cnt) par[i] = i;
         }
+        if (threadIdx.x == 0) xcount = 0;
         __syncthreads();
         const int64_t a_beg = woff[0], a_end = woff[cnt];
         // each thread takes runs of kItems consecutive arcs
@@ -208,7 +223,17 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
                 while ((int64_t)woff[lo + 1] <= a) ++lo;
                 const int32_t w = adj[a];
                 const int64_t lw = (int64_t)w - v0;
-                if (lw <= lo || lw >= cnt) continue;   // u < w inside the range only
+                if (lw <= lo) continue;                // each edge once, from its smaller end
+                if (lw >= cnt) {                       // to a later range: the global pass
+                    const int k = atomicAdd(&xcount, 1);
+                    if (k < kXBuf) {
+                        xbuf[k] = make_int2((int32_t)(v0 + lo), w);
+                    } else {
+                        const long long q = (long long)atomicAdd((unsigned long long *)nxl, 1ull);
+                        if (q < xl_cap) xl[q] = make_int2((int32_t)(v0 + lo), w);
+                    }
+                    continue;
+                }
                 int32_t ru = sm_find(par, lo), rv = sm_find(par, (int32_t)lw);
                 for (int it = 0; it < kUniteCap && ru != rv; ++it) {
                     const int32_t h = ru > rv ? ru : rv, l = ru > rv ? rv : ru;
@@ -224,23 +249,47 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
             }
         }
         __syncthreads();
+        const int staged = xcount < kXBuf ? xcount : kXBuf;
+        if (threadIdx.x == 0)
+            xbase = staged ? (long long)atomicAdd((unsigned long long *)nxl, (unsigned long long)staged) : 0;
         for (int i = threadIdx.x; i < cnt; i += kLocalThreads) {
             int32_t r = i;
             while (par[r] != r) r = par[r];
             uf[v0 + i] = (int32_t)(v0 + r);
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < staged; i += kLocalThreads)
+            if (xbase + i < xl_cap) xl[xbase + i] = xbuf[i];
     }
     (void)err;
 }
 
-// Global hooks of the edges between ranges.
+// Global hooks of the gathered edges of one level; when the list did not fit,
+// the level-0 launch hooks every edge between ranges from a full arc scan and
+// the other levels do nothing.
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restrict__ off,
                                                             const int32_t *__restrict__ adj, int64_t nnz,
                                                             const int32_t *__restrict__ tile_v, int64_t ntiles, int V,
-                                                            int32_t *uf, int32_t *te_u, int32_t *te_v, int *err,
-                                                            bool vec)
+                                                            const int2 *__restrict__ xl, int64_t xl_cap,
+                                                            const long long *__restrict__ nxl, int level, int32_t *uf,
+                                                            int32_t *te_u, int32_t *te_v, int *err, bool vec)
 {
+    const long long nx = *nxl;
+    if (nx <= xl_cap) {
+        for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nx; i += (int64_t)gridDim.x * kThreads) {
+            const int2 e = xl[i];
+            const uint32_t x = (uint32_t)(e.x / V) ^ (uint32_t)(e.y / V);
+            if (x == 0 || 31 - __clz(x) != level) continue;
+            const int32_t r = uf_unite(uf, e.x, e.y, err);
+            if (r >= 0) {
+                te_u[r] = e.x;
+                te_v[r] = e.y;
+            }
+        }
+        return;
+    }
+    if (level != 0) return;
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
     const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -261,7 +310,10 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restri
     }
 }
 
-size_t cc_local_smem(int V, bool off64) { return (size_t)(V + 1) * (off64 ? 8 : 4) + 8 + (size_t)V * 4; }
+size_t cc_local_smem(int V, bool off64)
+{
+    return (size_t)kXBuf * sizeof(int2) + (size_t)(V + 1) * (off64 ? 8 : 4) + 8 + (size_t)V * 4;
+}
 
 cudaError_t prepare_cc_local(int V)
 {
@@ -286,12 +338,19 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
         if (cc_local > 0) {
             const int64_t nr = ceil_div(n, cc_local);
             const int gl = (int)(nr < L.grid ? nr : L.grid);
+            long long *nxl = d.counters + 4;
+            const cudaError_t e = cudaMemsetAsync(nxl, 0, sizeof(long long), L.s);
+            if (e != cudaSuccess) return e;
             k_cc_local<OffT><<<gl, kLocalThreads, cc_local_smem(cc_local, sizeof(OffT) == 8), L.s>>>(
-                off, adj, n, cc_local, d.uf, d.te_u, d.te_v, d.err);
+                off, adj, n, cc_local, d.uf, d.te_u, d.te_v, d.xl, d.xl_cap, nxl, d.err);
             L.mark("k_cc_local");
-            k_cc_hook_cross<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, cc_local, d.uf, d.te_u,
-                                                           d.te_v, d.err, vec);
-            L.mark("k_cc_hook_cross");
+            int levels = 0;   // ranges r < r' < nr differ first at bit <= floor(log2(nr - 1))
+            while ((1ll << levels) < nr) ++levels;
+            for (int lv = 0; lv < levels; ++lv) {
+                k_cc_hook_cross<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, cc_local, d.xl,
+                                                               d.xl_cap, nxl, lv, d.uf, d.te_u, d.te_v, d.err, vec);
+                L.mark("k_cc_hook_cross");
+            }
         } else if (cc_sample > 0) {
             int32_t *big = reinterpret_cast<int32_t *>(d.counters + 8);
             k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, d.err);
@@ -450,8 +509,9 @@ __global__ void __launch_bounds__(kThreads) k_lcc_sample(const OffT *__restrict_
 // Flatten the union-find over positions (roots only, see uf_root).
 __global__ void __launch_bounds__(kThreads) k_pos_compress(int32_t *uf, int64_t n)
 {
-    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads)
-        uf[p] = uf_root(uf, (int32_t)p);
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * kThreads)
+        uf_flatten_warp(uf, p, p < n);
 }
 
 template <typename OffT>

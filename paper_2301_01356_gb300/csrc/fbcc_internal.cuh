@@ -44,6 +44,8 @@ struct Dev {
     // First-CC
     int32_t *uf;              // union-find parent (First-CC, then Last-CC)
     int32_t *te_u, *te_v;     // tree edge recorded at the vertex it hooked (-1: none)
+    int2 *xl;                 // local-first First-CC: edges between vertex ranges {u, w}, u < w
+    int64_t xl_cap;           // (aliases the rooting scratch, which is dead during First-CC)
     int32_t *tile_v;          // source vertex of the first arc of every arc tile (+1 sentinel)
     // Rooting
     int32_t *lhead;           // first forest arc of every vertex's list (-1: none)
@@ -118,13 +120,16 @@ __device__ __forceinline__ void set_bit(uint32_t *bits, int64_t i)
 
 // Union-find root with path halving. Parents only ever point to smaller ids
 // (larger roots are hooked under smaller ones), so the walk strictly decreases
-// and the root of a set is its smallest member. Reads bypass L1 (other SMs write).
+// and the root of a set is its smallest member. Loads may be served from L1
+// although other SMs write the array: an entry only ever moves to a higher
+// ancestor, so a stale copy still names an ancestor (the walk is longer, never
+// wrong), and every hook is a CAS, which L2 decides on the current value.
 __device__ __forceinline__ int32_t uf_find(int32_t *uf, int32_t v)
 {
     while (true) {
-        int32_t p = ld_cg(uf + v);
+        int32_t p = uf[v];
         if (p == v) return v;
-        int32_t gp = ld_cg(uf + p);
+        int32_t gp = uf[p];
         if (gp == p) return p;
         uf[v] = gp;  // halving: gp is an ancestor of v, so the store is always safe
         v = gp;
@@ -136,12 +141,26 @@ __device__ __forceinline__ int32_t uf_find(int32_t *uf, int32_t v)
 // already stored the root into the same slot and leave a non-root behind.
 __device__ __forceinline__ int32_t uf_root(const int32_t *uf, int32_t v)
 {
-    int32_t p = ld_cg(uf + v);
+    int32_t p = uf[v];
     while (p != v) {
         v = p;
-        p = ld_cg(uf + v);
+        p = uf[v];
     }
     return v;
+}
+
+// uf[v] = root of v for one vertex per lane (lanes with in == false take part
+// but change nothing). Lanes whose parents agree walk once: a warp's vertices
+// mostly share a set.
+__device__ __forceinline__ void uf_flatten_warp(int32_t *uf, int64_t v, bool in)
+{
+    const int32_t p = in ? uf[v] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, p);
+    const int leader = __ffs(peers) - 1;
+    int32_t r = -1;
+    if (in && (int)(threadIdx.x & 31) == leader) r = uf_root(uf, p);
+    r = __shfl_sync(0xffffffffu, r, leader);
+    if (in && r != p) uf[v] = r;
 }
 
 // Union of the sets of u and v by CAS-hooking the larger root under the smaller.

@@ -116,6 +116,21 @@ def test_repeated_solves_and_configs(torch_cuda, oracle):
         s.close()
 
 
+def test_local_first_cross_edge_list_and_overflow(torch_cuda, oracle):
+    """Local-first First-CC: edges between ranges go through a gathered list; a dense
+    graph whose list outgrows the space it borrows takes the full-scan fallback."""
+    from paper_2301_01356_gb300 import fbcc
+    for g in (gg.grid(300, 280, p=0.62, extra_frac=0.001, seed=4),    # list: a few edges per range boundary
+              gg.uniform(3000, 200000, 5),                            # ~2/3 of 200k edges cross: overflow
+              gg.uniform(2500, 2600, 6)):                             # sparse, many components
+        e = oracle.solve(g.offsets, g.adj)
+        s = fbcc.Solver(g.n, g.nnz, cc_local=1024)
+        off, adj = to_dev(torch_cuda, g)
+        for _ in range(2):
+            assert_same(s.solve(off, adj), e, g.name)
+        s.close()
+
+
 def test_host_entry_point(torch_cuda, oracle):
     from paper_2301_01356_gb300 import fbcc
     g = gg.uniform(5000, 12000, 8)
