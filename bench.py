@@ -159,19 +159,20 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_place": 36 * A,
         "k_root_tags": 12 * n_cc,
         "k_preorder": 16 * n + 28 * n,
-        "k_w12": B * (n + 1) + 4 * nnz + nnz // 8 + 4 * nnz + 8 * n,
+        "k_first_of": 12 * n,
+        "k_w12": B * (n + 1) + 4 * nnz + 4 * nnz + nnz // 8 + 8 * n,
         "k_rmq_prefix": 16 * n,
         "k_iota": 4 * n,
         "k_rmq_query": 41 * n,
-        "k_last_cc_cross": B * (n + 1) + 8 * nnz + nnz // 8 + 8 * n,
+        "k_last_cc_cross": B * (n + 1) + nnz // 8 + (4 * nnz + 8 * nnz) // 2 + 12 * n,
         "k_heads": 16 * n,
         "k_label_count": 16 * n,
         "k_ap_keys": 17 * n,
         "k_key_bits": 20 * n,
         "k_scan_popc": nnz // 4,
         "k_rank": 20 * n,
-        "k_fo": 25 * n,
-        "k_edge_out": B * (n + 1) + 4 * nnz + nnz // 8 + 8 * nnz + 4 * nnz + nnz,
+        "k_fo": 21 * n,
+        "k_edge_out": B * (n + 1) + 4 * nnz + nnz // 8 + 4 * nnz // 2 + 4 * n + 4 * nnz + nnz,
         "k_cc_local": B * (n + 1) + 4 * nnz + 12 * n,
         "k_cc_hook_cross": B * (n + 1) + 4 * nnz + 8 * n,
         "k_tour_records": 28 * A,
@@ -180,12 +181,12 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_expand2": 28 * nr,
         "k_ext_compact": n,
         "k_ext_jump": 12 * (n // 64),
-        "k_plain_label": 16 * n,
+        "k_plain_label": 20 * n,
         "k_final_label": 20 * n,
         "k_lab_out": 20 * n,
-        "k_lcc_sample": B * (n + 1) + 16 * n + 32 * n,
+        "k_lcc_sample": B * (n + 1) + 16 * n + 24 * n,
         "k_pos_compress": 8 * n,
-        "k_last_cc_cross_skip": B * (n + 1) + 4 * nnz + 16 * n,
+        "k_last_cc_cross_skip": B * (n + 1) + 4 * nnz + nnz // 8 + 16 * n,
         # sampled variants (two sampled neighbours per vertex) and the key scan
         # (offsets and selection flags; the scanned lists are few)
         "k_cc_sample": B * (n + 1) + 8 * n + 8 * n,

@@ -190,14 +190,20 @@ fbcc_status fbcc_profile_get(const fbcc_workspace *ws, int32_t i, const char **n
  *   "first", "last", "parent"  preorder number, last preorder number in the
  *                              subtree, tree parent (-1 for a root), by vertex
  *   "label"                    Last-CC label by vertex (a root is its own label)
- *   "w1", "w2"                 w1/w2 by preorder number
+ *   "w1", "w2"                 w1/w2 by preorder number; w2 may also hold the
+ *                              preorder numbers of tree children (they leave
+ *                              high unchanged), w1 is exactly its definition
  *   "low", "high"              low/high by preorder number (only when the solve
  *                              ran with fbcc_config.profile = 1)
  *   "ord", "porig"             vertex and parent vertex (-1: root) by preorder number
  *   "vbits" (uint8)            bit 0: the tree edge to the parent is a bridge;
  *                              bit 1: it is a fence edge
  *   "err" (count 1)            the device error bits of the last solve
- * Returns FBCC_E_INVALID for an unknown name or count > workspace n_max.
+ *   "dirb" (uint8, count up to ceil(nnz_max / 8))  one bit per arc, least
+ *                              significant first: the target's preorder number
+ *                              exceeds the source's
+ * Returns FBCC_E_INVALID for an unknown name or a count above those limits
+ * (n_max for the per-vertex arrays).
  */
 fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *name, void *host_dst, int64_t count);
 

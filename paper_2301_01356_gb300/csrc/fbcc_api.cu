@@ -82,6 +82,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.tile_v = c.take<int32_t>(ceil_div(Z, kWTile) + 2);
     d.fp = c.take<int2>(N);
     d.lastp = c.take<int32_t>(N);
+    d.dirb = c.take<uint8_t>(ceil_div(Z, 8) + 8);
     d.ord = c.take<int32_t>(N);
     d.porig = c.take<int32_t>(N);
     d.w1 = c.take<int32_t>(N);
@@ -130,7 +131,8 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.lp = c.take<int32_t>(N);
     d.ext = c.take<uint8_t>(N);
     d.qlist = c.take<int32_t>(N);
-    d.cr = c.take<int4>(N);
+    d.first4 = c.take<int32_t>(N);
+    d.cr = c.take<int2>(N);
     d.fin = c.take<int32_t>(N);
     d.minorig = c.take<int32_t>(N);
     d.smin = c.take<int32_t>(N);
@@ -141,7 +143,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.key_bits = c.take<uint32_t>(words);
     d.key_pre = c.take<int32_t>(words + 1);
     d.rank = c.take<int32_t>(N);
-    d.fo = c.take<int2>(N);
+    d.word = c.take<int32_t>(N);
     if (c.used < rooting_end) c.used = rooting_end;
     return c.used + 256;
 }
@@ -607,8 +609,15 @@ extern "C" fbcc_status fbcc_profile_get(const fbcc_workspace *ws, int32_t i, con
 
 extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *name, void *host_dst, int64_t count)
 {
-    if (!ws || !name || !host_dst || count < 0 || count > ws->d.n_max) return FBCC_E_INVALID;
+    if (!ws || !name || !host_dst || count < 0) return FBCC_E_INVALID;
     const Dev &d = ws->d;
+    if (!strcmp(name, "dirb")) {   // one bit per arc, bytes
+        if (count > ceil_div(d.nnz_max, 8)) return FBCC_E_INVALID;
+        API_CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+        API_CK(cudaMemcpy(host_dst, d.dirb, size_t(count), cudaMemcpyDeviceToHost), "debug copy");
+        return FBCC_OK;
+    }
+    if (count > d.n_max) return FBCC_E_INVALID;
     const void *src = nullptr;
     size_t elem = 4;
     const bool f = !strcmp(name, "first"), pa = !strcmp(name, "parent"), la = !strcmp(name, "last");

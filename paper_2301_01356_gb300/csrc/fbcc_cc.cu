@@ -219,9 +219,15 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
                 int mid = (lo + hi + 1) >> 1;
                 if ((int64_t)woff[mid] <= a0) lo = mid; else hi = mid - 1;
             }
-            for (int64_t a = a0; a < a0 + kItems && a < a_end; ++a) {
+            int32_t dw[kItems];       // the run's targets, loaded together
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) dw[j] = a0 + j < a_end ? __ldcs(adj + a0 + j) : 0;
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) {
+                const int64_t a = a0 + j;
+                if (a >= a_end) break;
                 while ((int64_t)woff[lo + 1] <= a) ++lo;
-                const int32_t w = adj[a];
+                const int32_t w = dw[j];
                 const int64_t lw = (int64_t)w - v0;
                 if (lw <= lo) continue;                // each edge once, from its smaller end
                 if (lw >= cnt) {                       // to a later range: the global pass
@@ -431,24 +437,29 @@ __device__ __forceinline__ int32_t plain_root(const int32_t *lp, int64_t p)
     return t < (p & ~(int64_t)(kRmqTile - 1)) ? lp[t] : t;
 }
 
-// Per vertex {first, parent, plain-component root, last} for the cross-edge pass
-// (one gather gives all four), and a fresh union-find.
+// Per vertex {first, plain-component root} for the cross-edge passes (one 8-byte
+// gather gives both), and a fresh union-find.
 __global__ void __launch_bounds__(kThreads) k_plain_label(int64_t n, const int32_t *__restrict__ lp,
-                                                          const int32_t *__restrict__ ord,
-                                                          const int32_t *__restrict__ porig,
-                                                          const int32_t *__restrict__ lastp, int4 *cr, int32_t *uf)
+                                                          const int32_t *__restrict__ ord, int2 *cr, int32_t *uf)
 {
     for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads) {
-        cr[ord[p]] = make_int4((int32_t)p, porig[p], plain_root(lp, p), lastp[p]);
+        cr[ord[p]] = make_int2((int32_t)p, plain_root(lp, p));
         uf[p] = (int32_t)p;
     }
 }
 
+// Cross edges from their earlier endpoint: arc u->w with w later in preorder (its
+// direction bit) is a cross edge iff first[w] > last[u], i.e. w lies after T_u;
+// a tree arc to a child and a back edge to a descendant both fail that test, and
+// arcs to earlier vertices are left to the reverse arc, so only half of the arcs
+// gather anything.
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                             int64_t nnz, const int32_t *__restrict__ tile_v,
-                                                            int64_t ntiles, const int4 *__restrict__ cr, int32_t *uf,
-                                                            int *err, bool vec)
+                                                            int64_t ntiles, const int2 *__restrict__ cr,
+                                                            const int32_t *__restrict__ lastp,
+                                                            const uint8_t *__restrict__ dirb, int32_t *uf, int *err,
+                                                            bool vec)
 {
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
@@ -456,21 +467,22 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
     for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
         arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
         if (!at.cnt) continue;
+        const uint32_t bits = __ldg(dirb + (at.a0 >> 3));
+        if (!bits) continue;
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
-        int32_t cur = -1;
-        int4 cs = make_int4(0, -1, 0, 0);
+        int32_t cur = -1, lastu = 0;
+        int2 cs = make_int2(0, 0);
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            if (j >= at.cnt) continue;
+            if (j >= at.cnt || !((bits >> j) & 1u)) continue;
             if (at.src[j] != cur) {
                 cur = at.src[j];
                 cs = __ldg(cr + cur);
+                lastu = __ldg(lastp + cs.x);
             }
-            const int4 cd = __ldg(cr + d[j]);
-            // same plain component: nothing to join (tree and back edges included)
-            if (cd.z == cs.z || is_tree_arc(cur, cs.y, d[j], cd.y)) continue;
-            if (cd.x > cs.w) uf_unite(uf, cs.z, cd.z, err);   // cross edge: d after T_cur
+            const int2 cd = __ldg(cr + d[j]);
+            if (cd.y != cs.y && cd.x > lastu) uf_unite(uf, cs.y, cd.y, err);
         }
     }
 }
@@ -478,29 +490,33 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
 // Sampling variant of the cross-edge pass (the Afforest idea applied to G'):
 // first every vertex unites along its first `k` cross edges, then the component
 // holding most sampled positions is found, and the full pass skips every source
-// already in it. A skipped arc still reaches its other endpoint's side, so the
-// full pass tests cross edges from both ends (u ancestor of w or w ancestor of u
-// from the two {first, last} intervals).
-__device__ __forceinline__ bool is_cross(const int4 &a, const int4 &b)
+// already in it. A skipped arc still reaches its other endpoint's side, so here
+// cross edges are tested from both ends: towards a later vertex w as above, and
+// towards an earlier one iff first[u] > last[w] (u after T_w; a parent arc and a
+// back edge to an ancestor fail it).
+__device__ __forceinline__ bool cross_from(int32_t fu, int32_t lastu, int32_t fw, bool later,
+                                           const int32_t *__restrict__ lastp)
 {
-    return !(a.x <= b.x && b.x <= a.w) && !(b.x <= a.x && a.x <= b.w);
+    return later ? fw > lastu : fu > __ldg(lastp + fw);
 }
 
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_lcc_sample(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
-                                                         int64_t n, int k, const int4 *__restrict__ cr, int32_t *uf,
-                                                         int *err)
+                                                         int64_t n, int k, const int2 *__restrict__ fp,
+                                                         const int2 *__restrict__ cr, const int32_t *__restrict__ lastp,
+                                                         const uint8_t *__restrict__ dirb, int32_t *uf, int *err)
 {
     for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
-        const int4 cs = cr[v];
-        if (cs.y < 0) continue;   // a root has no cross edges
+        if (fp[v].y < 0) continue;   // a root has no cross edges
+        const int2 cs = cr[v];
+        const int32_t lastu = __ldg(lastp + cs.x);
         int found = 0;
         const int64_t b = off[v], e = off[v + 1];
         for (int64_t a = b; a < e && a < b + 4 * k && found < k; ++a) {
             const int32_t w = adj[a];
-            const int4 cd = __ldg(cr + w);
-            if (cd.z == cs.z || is_tree_arc((int32_t)v, cs.y, w, cd.y) || !is_cross(cs, cd)) continue;
-            uf_unite(uf, cs.z, cd.z, err);
+            const int2 cd = __ldg(cr + w);
+            if (cd.y == cs.y || !cross_from(cs.x, lastu, cd.x, dir_bit(dirb, a), lastp)) continue;
+            uf_unite(uf, cs.y, cd.y, err);
             ++found;
         }
     }
@@ -518,7 +534,9 @@ template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_last_cc_cross_skip(const OffT *__restrict__ off,
                                                                  const int32_t *__restrict__ adj, int64_t nnz,
                                                                  const int32_t *__restrict__ tile_v, int64_t ntiles,
-                                                                 const int4 *__restrict__ cr, int32_t *uf,
+                                                                 const int2 *__restrict__ cr,
+                                                                 const int32_t *__restrict__ lastp,
+                                                                 const uint8_t *__restrict__ dirb, int32_t *uf,
                                                                  const int32_t *big, int *err, bool vec)
 {
     __shared__ OffT win[kCtaWin];
@@ -528,31 +546,36 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross_skip(const OffT *__r
     for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
         arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
         if (!at.cnt) continue;
-        int4 cs[kItems];
+        int2 cs[kItems];
+        int32_t lu[kItems];
         bool any = false;
         int32_t cur = -1;
         bool skip = true;
-        int4 c = make_int4(0, -1, 0, 0);
+        int2 c = make_int2(0, 0);
+        int32_t lastu = 0;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             if (j < at.cnt && at.src[j] != cur) {
                 cur = at.src[j];
                 c = __ldg(cr + cur);
-                skip = c.y < 0 || uf_find(uf, c.z) == root;
+                skip = uf_find(uf, c.y) == root;
+                if (!skip) lastu = __ldg(lastp + c.x);
             }
             cs[j] = c;
+            lu[j] = lastu;
             if (j < at.cnt && !skip) any = true;
-            else cs[j].y = -2;   // marks a skipped arc
+            else lu[j] = -1;   // marks a skipped arc
         }
         if (!any) continue;
+        const uint32_t bits = __ldg(dirb + (at.a0 >> 3));
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            if (j >= at.cnt || cs[j].y == -2) continue;
-            const int4 cd = __ldg(cr + d[j]);
-            if (cd.z == cs[j].z || is_tree_arc(at.src[j], cs[j].y, d[j], cd.y) || !is_cross(cs[j], cd)) continue;
-            uf_unite(uf, cs[j].z, cd.z, err);
+            if (j >= at.cnt || lu[j] < 0) continue;
+            const int2 cd = __ldg(cr + d[j]);
+            if (cd.y == cs[j].y || !cross_from(cs[j].x, lu[j], cd.x, (bits >> j) & 1u, lastp)) continue;
+            uf_unite(uf, cs[j].y, cd.y, err);
         }
     }
 }
@@ -636,22 +659,23 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
         k_ext_jump<<<gv, kThreads, 0, L.s>>>(nq, d.qlist, d.lp);
         L.mark("k_ext_jump");
     }
-    k_plain_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.ord, d.porig, d.lastp, d.cr, d.uf);
+    k_plain_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.ord, d.cr, d.uf);
     L.mark("k_plain_label");
     if (nnz > 0 && lcc_sample > 0) {
         int32_t *big = reinterpret_cast<int32_t *>(d.counters + 9);
-        k_lcc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, lcc_sample, d.cr, d.uf, d.err);
+        k_lcc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, lcc_sample, d.fp, d.cr, d.lastp, d.dirb, d.uf,
+                                                     d.err);
         L.mark("k_lcc_sample");
         k_pos_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
         L.mark("k_pos_compress");
         k_pos_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, d.porig, n, big);
         L.mark("k_pos_pick_big");
         k_last_cc_cross_skip<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
-            off, adj, nnz, d.tile_v, ntiles, d.cr, d.uf, big, d.err, vec);
+            off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, big, d.err, vec);
         L.mark("k_last_cc_cross_skip");
     } else if (nnz > 0) {
-        k_last_cc_cross<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.cr,
-                                                                        d.uf, d.err, vec);
+        k_last_cc_cross<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
+            off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, d.err, vec);
         L.mark("k_last_cc_cross");
     }
     CK(cudaMemsetAsync(d.minorig, 0x7f, n * sizeof(int32_t), L.s));

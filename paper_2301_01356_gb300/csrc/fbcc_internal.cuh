@@ -66,7 +66,9 @@ struct Dev {
     int32_t *pos;             // tour position of every tree arc
     int2 *rec;                // tour record at every position (down/up arc, padding)
     // Tagging (fp indexed by vertex; the rest by preorder number)
-    int2 *fp;                 // {first, parent} by vertex (parent -1 at a root): one gather gives both
+    int2 *fp;                 // {first, parent} by vertex (parent -1 at a root)
+    int32_t *first4;          // first by vertex alone (the arc passes gather it: half of fp's bytes)
+    uint8_t *dirb;            // one bit per arc: the target's preorder number exceeds the source's
     int32_t *ord;             // vertex at preorder number p
     int32_t *porig;           // parent vertex of the vertex at preorder number p (-1 root)
     int32_t *w1, *w2;         // w1/w2 at preorder number p
@@ -78,7 +80,7 @@ struct Dev {
     int32_t *lp;              // plain-component pointer (root: itself), flattened in place
     uint8_t *ext;             // position referenced across an RMQ tile
     int32_t *qlist;           // compacted positions with ext set
-    int4 *cr;                 // by vertex {first, parent, plain-component root, last} (Last-CC arc pass)
+    int2 *cr;                 // by vertex {first, plain-component root} (Last-CC arc passes)
     int32_t *lastp;           // last[] by preorder number (written by the preorder scan)
     int32_t *fin;             // final skeleton-component root of every position
     int32_t *minorig;         // smallest vertex id of the component rooted at position r
@@ -91,7 +93,7 @@ struct Dev {
     uint32_t *key_bits;       // one bit per arc: arc is the key of its BCC
     int32_t *key_pre;         // exclusive popcount prefix per 32-bit word of key_bits
     int32_t *rank;            // canonical BCC index of label L at [L]
-    int2 *fo;                 // {first, output word} per vertex
+    int32_t *word;            // per vertex: BCC index of its label | bridge << 31
     fbcc_stats *stats;        // device-side counts
 };
 
@@ -444,11 +446,10 @@ __device__ __forceinline__ int32_t graph_of(const int64_t *__restrict__ vtx_base
     return lo;
 }
 
-// An arc u->w of a simple graph is a tree arc iff one endpoint is the other's
-// parent in the rooted spanning forest (no parallel edges).
-__device__ __forceinline__ bool is_tree_arc(int32_t u, int32_t pu, int32_t w, int32_t pw)
+// Direction bit of arc a: the target comes later in preorder than the source.
+__device__ __forceinline__ bool dir_bit(const uint8_t *dirb, int64_t a)
 {
-    return pu == w || pw == u;
+    return (__ldg(dirb + (a >> 3)) >> (a & 7)) & 1u;
 }
 
 // ---------------------------------------------------------------------------

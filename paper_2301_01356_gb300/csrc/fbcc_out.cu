@@ -98,7 +98,7 @@ template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                        int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
                                                        const uint8_t *__restrict__ scanv,
-                                                       const int2 *__restrict__ fp,
+                                                       const uint8_t *__restrict__ dirb,
                                                        const int32_t *__restrict__ lab,
                                                        const int32_t *__restrict__ head,
                                                        const int32_t *__restrict__ smin, unsigned long long *key,
@@ -127,14 +127,15 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
         if (!any) continue;
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
-        int32_t cur = -1, fcur = 0, last_l = -1;
+        const uint32_t bits = __ldg(dirb + (at.a0 >> 3));
+        int32_t cur = -1, last_l = -1;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             if (!((sel >> j) & 1u)) continue;
             const int32_t u = at.src[j], w = d[j];
             if (w < u) continue;
-            if (u != cur) { cur = u; fcur = __ldg(&fp[u].x); last_l = -1; }
-            const int32_t x = __ldg(&fp[w].x) > fcur ? w : u;
+            if (u != cur) { cur = u; last_l = -1; }
+            const int32_t x = (bits >> j) & 1u ? w : u;   // the endpoint later in preorder
             const int32_t l = __ldg(lab + x);
             if (l == last_l) continue;  // a later arc of the same BCC cannot be smaller
             last_l = l;
@@ -196,10 +197,10 @@ __global__ void __launch_bounds__(kThreads) k_bcc_base(Batch B, const uint32_t *
     }
 }
 
-// Per vertex {first, output word}: word = BCC index of its label | bridge << 31.
+// Per vertex output word: BCC index of its label | bridge << 31.
 __global__ void __launch_bounds__(kThreads) k_fo(int64_t n, const int2 *__restrict__ fp,
                                                  const int32_t *__restrict__ lab, const int32_t *__restrict__ rank,
-                                                 const uint8_t *__restrict__ vbits, int2 *fo, fbcc_stats *stats)
+                                                 const uint8_t *__restrict__ vbits, int32_t *word, fbcc_stats *stats)
 {
     long long nb = 0;
     GRID_STRIDE(v, n)
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(kThreads) k_fo(int64_t n, const int2 *__restri
             w = (int32_t)((uint32_t)rank[lab[v]] | (br << 31));
             nb += br;
         }
-        fo[v] = make_int2(f.x, w);
+        word[v] = w;
     }
     block_count((long long *)&stats->n_bridge, nb);
 }
@@ -259,7 +260,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, co
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                        int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
-                                                       const int2 *__restrict__ fo, int32_t *edge_bcc,
+                                                       const int32_t *__restrict__ word,
+                                                       const uint8_t *__restrict__ dirb, int32_t *edge_bcc,
                                                        uint8_t *is_bridge, bool vec, bool vec_out)
 {
     __shared__ OffT win_all[kWarpsPerCta * kWarpWin];
@@ -271,21 +273,21 @@ __global__ void __launch_bounds__(kThreads) k_edge_out(const OffT *__restrict__ 
         if (!at.cnt) continue;
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
+        const uint32_t bits = __ldg(dirb + (at.a0 >> 3));
         int32_t lab8[kItems];
         uint8_t br8[kItems];
-        int32_t cur = -1;
-        int2 fs = make_int2(0, 0);
+        int32_t cur = -1, ws = 0;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             lab8[j] = 0;
             br8[j] = 0;
             if (j >= at.cnt) continue;
-            if (at.src[j] != cur) { cur = at.src[j]; fs = __ldg(fo + cur); }
-            const int2 fd = __ldg(fo + d[j]);
-            // x = the endpoint with the larger preorder number. If x's parent edge is
-            // a bridge, x's label class is {x} and that bridge is the only edge of
-            // its BCC, so every arc labelled through x is the bridge itself.
-            const int32_t w = fd.x > fs.x ? fd.y : fs.y;
+            if (at.src[j] != cur) { cur = at.src[j]; ws = __ldg(word + cur); }
+            // x = the endpoint with the larger preorder number (the direction bit).
+            // If x's parent edge is a bridge, x's label class is {x} and that bridge
+            // is the only edge of its BCC, so every arc labelled through x is the
+            // bridge itself.
+            const int32_t w = (bits >> j) & 1u ? __ldg(word + d[j]) : ws;
             lab8[j] = w & 0x7fffffff;
             br8[j] = (uint8_t)((uint32_t)w >> 31);
         }
@@ -326,7 +328,7 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
-        k_key_scan<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.fp,
+        k_key_scan<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.dirb,
                                                                    d.uf, d.head, d.smin, d.key, vec);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
@@ -340,11 +342,11 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
         }
         k_rank<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.key, d.key_bits, d.key_pre, d.head, d.rank, bcc_head, B, nnz, d.err);
         L.mark("k_rank");
-        k_fo<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.rank, d.vbits, d.fo, d.stats);
+        k_fo<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.rank, d.vbits, d.word, d.stats);
         L.mark("k_fo");
         const bool vec_out = ((uintptr_t)edge_bcc & 15) == 0 && ((uintptr_t)is_bridge & 7) == 0;
         k_edge_out<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles,
-                                                                   d.fo, edge_bcc, is_bridge, vec, vec_out);
+                                                                   d.word, d.dirb, edge_bcc, is_bridge, vec, vec_out);
         L.mark("k_edge_out");
     } else if (B.G > 0) {
         CK(cudaMemsetAsync(B.bcc_base, 0, (B.G + 1) * sizeof(int64_t), L.s));

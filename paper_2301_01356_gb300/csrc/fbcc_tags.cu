@@ -20,42 +20,83 @@ namespace fbcc {
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
 
-// w1/w2 over the non-tree arcs; one atomic per run of equal sources per thread.
+// first by vertex as a compact array for the arc passes' gathers.
+__global__ void __launch_bounds__(kThreads) k_first_of(int64_t n, const int2 *__restrict__ fp, int32_t *first4)
+{
+    GRID_STRIDE(v, n) first4[v] = fp[v].x;
+}
+
+// w1/w2 over the arcs, one atomic per run of equal sources per thread, and the
+// direction bit of every arc (target later in preorder than the source).
+//
+// Only the parent arc is left out. The arcs to children may enter: a child c of
+// u has first[u] < first[c] <= last[u], so it cannot lower w1[u] (which holds
+// first[u]), and although it can raise w2[u], every value it adds lies inside
+// T_v for each ancestor v of u, where high[v] >= last[v] already (w2 of T_v's
+// last vertex is at least its own first). low and high, the only consumers, stay
+// exactly as defined, and no parent of a neighbour has to be gathered.
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                   int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
-                                                  const int2 *__restrict__ fp, int32_t *w1, int32_t *w2,
-                                                  int64_t n, int *err, bool vec)
+                                                  const int2 *__restrict__ fp, const int32_t *__restrict__ first4,
+                                                  int32_t *w1, int32_t *w2, uint8_t *dirb, int64_t n, int *err,
+                                                  bool vec)
 {
     __shared__ OffT win_all[kWarpsPerCta * kWarpWin];
     OffT *win = win_all + (threadIdx.x >> 5) * kWarpWin;
+    const int lane = threadIdx.x & 31;
     ArcTile<OffT> at;
     FOR_EACH_WARP_TILE(t, ntiles)
     {
         arc_tile_sources(off, nnz, tile_v, t, win, at);
-        if (!at.cnt) continue;
-        int32_t d[kItems];
-        arc_tile_targets(adj, at.a0, at.cnt, vec, d);
+        // A lane whose arcs all leave one source keeps that run for a warp-wide
+        // reduction: the lanes of a long list then add one atomic per warp.
+        const bool single = at.cnt > 0 && at.src[0] == at.src[at.cnt - 1];
         int32_t cur = -1, mn = INT32_MAX, mx = INT32_MIN;
         int2 fc = make_int2(0, -1);
+        uint32_t bits = 0;
+        if (at.cnt) {
+            int32_t d[kItems];
+            arc_tile_targets(adj, at.a0, at.cnt, vec, d);
 #pragma unroll
-        for (int j = 0; j <= kItems; ++j) {
-            bool live = j < at.cnt;
-            if (!live || at.src[j] != cur) {
-                if (cur >= 0 && mn != INT32_MAX && in_range(fc.x, n, err)) {
-                    if (mn < fc.x) atomicMin(w1 + fc.x, mn);
-                    if (mx > fc.x) atomicMax(w2 + fc.x, mx);
+            for (int j = 0; j <= kItems; ++j) {
+                bool live = j < at.cnt;
+                if (!live || at.src[j] != cur) {
+                    if (!live && single) break;   // flushed below, with the warp
+                    if (cur >= 0 && mn != INT32_MAX && in_range(fc.x, n, err)) {
+                        if (mn < fc.x) atomicMin(w1 + fc.x, mn);
+                        if (mx > fc.x) atomicMax(w2 + fc.x, mx);
+                    }
+                    if (!live) break;
+                    cur = at.src[j];
+                    fc = __ldg(fp + cur);
+                    mn = INT32_MAX;
+                    mx = INT32_MIN;
                 }
-                if (!live) break;
-                cur = at.src[j];
-                fc = __ldg(fp + cur);
-                mn = INT32_MAX;
-                mx = INT32_MIN;
+                if (d[j] == fc.y) continue;   // the parent arc: earlier in preorder
+                const int32_t fw = __ldg(first4 + d[j]);
+                if (fw > fc.x) bits |= 1u << j;
+                mn = fw < mn ? fw : mn;
+                mx = fw > mx ? fw : mx;
             }
-            const int2 fd = __ldg(fp + d[j]);
-            if (is_tree_arc(cur, fc.y, d[j], fd.y)) continue;
-            mn = fd.x < mn ? fd.x : mn;
-            mx = fd.x > mx ? fd.x : mx;
+            dirb[at.a0 >> 3] = (uint8_t)bits;   // a0 is a multiple of kItems = 8
+        }
+        // segmented min/max over runs of lanes with the same single source (such
+        // lanes are consecutive: arcs are in CSR order); the run's first lane adds
+        const int32_t key = single ? cur : -1 - lane;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t ko = __shfl_down_sync(0xffffffffu, key, o);
+            const int32_t a = __shfl_down_sync(0xffffffffu, mn, o), b = __shfl_down_sync(0xffffffffu, mx, o);
+            if (lane + o < 32 && ko == key) {
+                mn = a < mn ? a : mn;
+                mx = b > mx ? b : mx;
+            }
+        }
+        const int32_t kp = __shfl_up_sync(0xffffffffu, key, 1);
+        if (single && (lane == 0 || kp != key) && mn != INT32_MAX && in_range(fc.x, n, err)) {
+            if (mn < fc.x) atomicMin(w1 + fc.x, mn);
+            if (mx > fc.x) atomicMax(w2 + fc.x, mx);
         }
     }
 }
@@ -153,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                                                         const int32_t *__restrict__ tmax, int64_t st_stride,
                                                         const int32_t *__restrict__ ord,
                                                         const int32_t *__restrict__ porig,
-                                                        const int2 *__restrict__ fp,
+                                                        const int32_t *__restrict__ first4,
                                                         const int32_t *__restrict__ lastp, uint8_t *vbits, int32_t *lp,
                                                         uint8_t *ext, int32_t *low_out, int32_t *high_out, int *err)
 {
@@ -255,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                 uint8_t bits = 0;
                 if (x >= 0) {
                     if (lo == (int32_t)p && hi <= e) bits |= 1;  // bridge: nothing leaves T_v
-                    const int32_t fx = __ldg(&fp[x].x);
+                    const int32_t fx = __ldg(first4 + x);
                     const bool fence = fx <= lo && (uint32_t)fx < (uint64_t)n && __ldg(lastp + fx) >= hi;
                     if (fence) bits |= 2;
                     else ptr = fx;                                // plain tree edge: in G'
@@ -295,9 +336,11 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
                            bool vec, bool keep_low_high, const Launch &L)
 {
     const int64_t ntiles = ceil_div(nnz, kWTile);
+    k_first_of<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(n, d.fp, d.first4);
+    L.mark("k_first_of");
     if (nnz > 0) {
-        k_w12<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.fp,
-                                                              d.w1, d.w2, n, d.err, vec);
+        k_w12<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
+            off, adj, nnz, d.tile_v, ntiles, d.fp, d.first4, d.w1, d.w2, d.dirb, n, d.err, vec);
         L.mark("k_w12");
     }
     const int64_t rt = ceil_div(n, kRmqTile);
@@ -312,7 +355,7 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
     cudaError_t e = cudaMemsetAsync(d.ext, 0, n, L.s);
     if (e != cudaSuccess) return e;
     k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax,
-                                                       d.rmq_tiles_max, d.ord, d.porig, d.fp, d.lastp,
+                                                       d.rmq_tiles_max, d.ord, d.porig, d.first4, d.lastp,
                                                        d.vbits, d.lp, d.ext, keep_low_high ? d.low : nullptr,
                                                        keep_low_high ? d.high : nullptr, d.err);
     L.mark("k_rmq_query");

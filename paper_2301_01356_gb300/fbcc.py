@@ -189,7 +189,7 @@ def fbcc_profile(ws: int) -> list:
 
 def fbcc_debug_read(ws: int, name: str, n: int) -> np.ndarray:
     """Host copy of an internal per-vertex array of the last solve (see include/fbcc.h)."""
-    out = np.empty(max(n, 1), np.uint8 if name == "vbits" else np.int32)
+    out = np.empty(max(n, 1), np.uint8 if name in ("vbits", "dirb") else np.int32)
     _check(load().fbcc_debug_read(ws, name.encode(), out.ctypes.data, n), "fbcc_debug_read")
     return out[:n]
 
