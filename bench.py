@@ -165,8 +165,6 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_iota": 4 * n,
         "k_rmq_query": 41 * n,
         "k_last_cc_cross": B * (n + 1) + nnz // 8 + (4 * nnz + 8 * nnz) // 2 + 12 * n,
-        "k_heads": 16 * n,
-        "k_label_count": 16 * n,
         "k_ap_keys": 17 * n,
         "k_key_bits": 20 * n,
         "k_scan_popc": nnz // 4,
@@ -183,13 +181,14 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_ext_jump": 12 * (n // 64),
         "k_plain_label": 20 * n,
         "k_final_label": 20 * n,
-        "k_lab_out": 20 * n,
+        "k_lab_out": 24 * n,
         "k_lcc_sample": B * (n + 1) + 16 * n + 24 * n,
         "k_pos_compress": 8 * n,
         "k_last_cc_cross_skip": B * (n + 1) + 4 * nnz + nnz // 8 + 16 * n,
         # sampled variants (two sampled neighbours per vertex) and the key scan
         # (offsets and selection flags; the scanned lists are few)
         "k_cc_sample": B * (n + 1) + 8 * n + 8 * n,
+        "k_mark_big": 4 * n + n // 8,
         "k_cc_hook_skip": B * (n + 1) + 4 * nnz + 8 * n,
         "k_key_scan": B * (n + 1) + n,
     }

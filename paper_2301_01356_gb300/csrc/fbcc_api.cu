@@ -83,6 +83,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.fp = c.take<int2>(N);
     d.lastp = c.take<int32_t>(N);
     d.dirb = c.take<uint8_t>(ceil_div(Z, 8) + 8);
+    d.bigb = c.take<uint32_t>(ceil_div(N, 32) + 2);
     d.ord = c.take<int32_t>(N);
     d.porig = c.take<int32_t>(N);
     d.w1 = c.take<int32_t>(N);
@@ -136,7 +137,6 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.fin = c.take<int32_t>(N);
     d.minorig = c.take<int32_t>(N);
     d.smin = c.take<int32_t>(N);
-    d.head = c.take<int32_t>(N);
     d.nh = c.take<int32_t>(N);
     d.key = c.take<unsigned long long>(N);
     d.scanv = c.take<uint8_t>(N);

@@ -82,36 +82,47 @@ __global__ void __launch_bounds__(kThreads) k_cc_sample(const OffT *__restrict__
     }
 }
 
-// Full pass after sampling: arcs whose source already sits in the component of
-// `big` are skipped (the same edge is still seen from its other endpoint, unless
-// both endpoints are in that component, where it cannot join anything new).
+// Full pass after sampling: arcs whose source sat in the sampled largest
+// component are skipped (the same edge is still seen from its other endpoint,
+// unless both endpoints are in that component, where it cannot join anything
+// new). Membership is a bitmap taken before the pass: the component's root can
+// change during the pass (a component with a smaller id joins it), and a test
+// against the live root would then stop skipping.
+__global__ void __launch_bounds__(kThreads) k_mark_big(const int32_t *__restrict__ uf, int64_t n,
+                                                       const int32_t *__restrict__ big, uint32_t *bigb)
+{
+    const int32_t root = *big;
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
+        const unsigned m = __ballot_sync(0xffffffffu, v < n && uf[v] == root);
+        if ((threadIdx.x & 31) == 0) bigb[v >> 5] = m;
+    }
+}
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_hook_skip(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                            int64_t nnz, const int32_t *__restrict__ tile_v,
                                                            int64_t ntiles, int32_t *uf, int32_t *te_u, int32_t *te_v,
-                                                           const int32_t *big, int *err, bool vec)
+                                                           const uint32_t *__restrict__ bigb, int *err, bool vec)
 {
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
-    const int32_t root = *big;
     const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
     for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
         arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
         if (!at.cnt) continue;
         bool any = false;
-        int32_t rs[kItems];
-        int32_t last_src = -1, last_root = root;
+        uint32_t sk = 0;   // arcs whose source was in the sampled component
+        int32_t last_src = -1;
+        bool last_skip = true;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             if (j < at.cnt) {
                 if (at.src[j] != last_src) {
                     last_src = at.src[j];
-                    last_root = uf_find(uf, last_src);
+                    last_skip = test_bit(bigb, last_src);
                 }
-                rs[j] = last_root;
-                any |= last_root != root;
-            } else {
-                rs[j] = root;
+                if (last_skip) sk |= 1u << j;
+                any |= !last_skip;
             }
         }
         if (!any) continue;
@@ -119,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_skip(const OffT *__restric
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            if (j >= at.cnt || rs[j] == root) continue;
+            if (j >= at.cnt || ((sk >> j) & 1u)) continue;
             int32_t r = uf_unite(uf, at.src[j], d[j], err);
             if (r >= 0) {
                 te_u[r] = at.src[j];
@@ -174,16 +185,16 @@ __global__ void __launch_bounds__(kThreads) k_cc_pick_big(int32_t *uf, int64_t n
 // turn); in level order the chains stay within the number of levels. When the
 // list outgrows its space the global pass falls back to one full arc scan.
 constexpr int kLocalThreads = 512;
-constexpr int kXBuf = 4096;   // per-CTA staging of edges between ranges
 
-__device__ __forceinline__ int32_t sm_find(int32_t *par, int32_t v)
+// Local union-find in shared memory with 16-bit parents (range-local ids < 2^15).
+__device__ __forceinline__ int32_t sm_find(uint16_t *par, int32_t v)
 {
     while (true) {
         int32_t p = par[v];
         if (p == v) return v;
         int32_t gp = par[p];
         if (gp == p) return p;
-        par[v] = gp;
+        par[v] = (uint16_t)gp;
         v = gp;
     }
 }
@@ -195,11 +206,9 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
                                                             int64_t xl_cap, long long *nxl, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    int2 *xbuf = reinterpret_cast<int2 *>(smem);                                    // kXBuf staged edges
-    OffT *woff = reinterpret_cast<OffT *>(smem + kXBuf * sizeof(int2));             // V+1 offsets
-    int32_t *par = reinterpret_cast<int32_t *>(smem + kXBuf * sizeof(int2) + (size_t)(V + 1) * sizeof(OffT) + 8);
-    __shared__ int xcount;
-    __shared__ long long xbase;
+    OffT *woff = reinterpret_cast<OffT *>(smem);                                   // V+1 offsets
+    uint16_t *par = reinterpret_cast<uint16_t *>(smem + (size_t)(V + 1) * sizeof(OffT) + 8);
+    const int lane = threadIdx.x & 31;
     const int64_t nranges = (n + V - 1) / V;
     for (int64_t g = blockIdx.x; g < nranges; g += gridDim.x) {
         const int64_t v0 = g * V;
@@ -207,46 +216,66 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
         __syncthreads();
         for (int i = threadIdx.x; i <= cnt; i += kLocalThreads) {
             woff[i] = off[v0 + i];
-            if (i < cnt) par[i] = i;
+            if (i < cnt) par[i] = (uint16_t)i;
         }
-        if (threadIdx.x == 0) xcount = 0;
         __syncthreads();
         const int64_t a_beg = woff[0], a_end = woff[cnt];
-        // each thread takes runs of kItems consecutive arcs
-        for (int64_t a0 = a_beg + (int64_t)threadIdx.x * kItems; a0 < a_end; a0 += (int64_t)kLocalThreads * kItems) {
-            int lo = 0, hi = cnt - 1;   // the vertex whose list holds a0
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if ((int64_t)woff[mid] <= a0) lo = mid; else hi = mid - 1;
-            }
-            int32_t dw[kItems];       // the run's targets, loaded together
+        const int64_t rounds = (a_end - a_beg + (int64_t)kLocalThreads * kItems - 1) / ((int64_t)kLocalThreads * kItems);
+        // each thread takes runs of kItems consecutive arcs; every lane runs every
+        // round (warp-wide reservation of the list slots below)
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            const int64_t a0 = a_beg + (rd * kLocalThreads + threadIdx.x) * kItems;
+            int32_t dw[kItems], su[kItems];
+            uint32_t xmask = 0;   // arcs to a later range
+            if (a0 < a_end) {
+                int lo = 0, hi = cnt - 1;   // the vertex whose list holds a0
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if ((int64_t)woff[mid] <= a0) lo = mid; else hi = mid - 1;
+                }
 #pragma unroll
-            for (int j = 0; j < kItems; ++j) dw[j] = a0 + j < a_end ? __ldcs(adj + a0 + j) : 0;
+                for (int j = 0; j < kItems; ++j) dw[j] = a0 + j < a_end ? __ldcs(adj + a0 + j) : 0;
+#pragma unroll
+                for (int j = 0; j < kItems; ++j) {
+                    const int64_t a = a0 + j;
+                    su[j] = -1;
+                    if (a >= a_end) continue;
+                    while ((int64_t)woff[lo + 1] <= a) ++lo;
+                    const int64_t lw = (int64_t)dw[j] - v0;
+                    if (lw <= lo) continue;                  // each edge once, from its smaller end
+                    su[j] = lo;
+                    if (lw >= cnt) xmask |= 1u << j;         // to a later range: the global pass
+                }
+            }
+            // reserve list slots: one atomic per warp and round with such arcs
+            const int xc = __popc(xmask);
+            int xpre = xc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, xpre, o);
+                if (lane >= o) xpre += y;
+            }
+            long long xb = 0;
+            const int xtot = __shfl_sync(0xffffffffu, xpre, 31);
+            if (lane == 31 && xtot) xb = (long long)atomicAdd((unsigned long long *)nxl, (unsigned long long)xtot);
+            xb = __shfl_sync(0xffffffffu, xb, 31) + (xpre - xc);
+            if (a0 >= a_end) continue;
 #pragma unroll
             for (int j = 0; j < kItems; ++j) {
-                const int64_t a = a0 + j;
-                if (a >= a_end) break;
-                while ((int64_t)woff[lo + 1] <= a) ++lo;
-                const int32_t w = dw[j];
-                const int64_t lw = (int64_t)w - v0;
-                if (lw <= lo) continue;                // each edge once, from its smaller end
-                if (lw >= cnt) {                       // to a later range: the global pass
-                    const int k = atomicAdd(&xcount, 1);
-                    if (k < kXBuf) {
-                        xbuf[k] = make_int2((int32_t)(v0 + lo), w);
-                    } else {
-                        const long long q = (long long)atomicAdd((unsigned long long *)nxl, 1ull);
-                        if (q < xl_cap) xl[q] = make_int2((int32_t)(v0 + lo), w);
-                    }
+                if (su[j] < 0) continue;
+                if ((xmask >> j) & 1u) {
+                    if (xb < xl_cap) xl[xb] = make_int2((int32_t)(v0 + su[j]), dw[j]);
+                    ++xb;
                     continue;
                 }
-                int32_t ru = sm_find(par, lo), rv = sm_find(par, (int32_t)lw);
+                const int32_t lw = (int32_t)(dw[j] - v0);
+                int32_t ru = sm_find(par, su[j]), rv = sm_find(par, lw);
                 for (int it = 0; it < kUniteCap && ru != rv; ++it) {
                     const int32_t h = ru > rv ? ru : rv, l = ru > rv ? rv : ru;
-                    const int32_t old = atomicCAS(par + h, h, l);
+                    const int32_t old = atomicCAS(par + h, (unsigned short)h, (unsigned short)l);
                     if (old == h) {
-                        te_u[v0 + h] = (int32_t)(v0 + lo);
-                        te_v[v0 + h] = w;
+                        te_u[v0 + h] = (int32_t)(v0 + su[j]);
+                        te_v[v0 + h] = dw[j];
                         break;
                     }
                     ru = sm_find(par, old);
@@ -255,17 +284,11 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
             }
         }
         __syncthreads();
-        const int staged = xcount < kXBuf ? xcount : kXBuf;
-        if (threadIdx.x == 0)
-            xbase = staged ? (long long)atomicAdd((unsigned long long *)nxl, (unsigned long long)staged) : 0;
         for (int i = threadIdx.x; i < cnt; i += kLocalThreads) {
             int32_t r = i;
             while (par[r] != r) r = par[r];
             uf[v0 + i] = (int32_t)(v0 + r);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < staged; i += kLocalThreads)
-            if (xbase + i < xl_cap) xl[xbase + i] = xbuf[i];
     }
     (void)err;
 }
@@ -316,10 +339,7 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restri
     }
 }
 
-size_t cc_local_smem(int V, bool off64)
-{
-    return (size_t)kXBuf * sizeof(int2) + (size_t)(V + 1) * (off64 ? 8 : 4) + 8 + (size_t)V * 4;
-}
+size_t cc_local_smem(int V, bool off64) { return (size_t)(V + 1) * (off64 ? 8 : 4) + 8 + (size_t)V * 2; }
 
 cudaError_t prepare_cc_local(int V)
 {
@@ -365,8 +385,10 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             L.mark("k_uf_compress");
             k_cc_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, n, big);
             L.mark("k_cc_pick_big");
+            k_mark_big<<<gv, kThreads, 0, L.s>>>(d.uf, n, big, d.bigb);
+            L.mark("k_mark_big");
             k_cc_hook_skip<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
-                                                          big, d.err, vec);
+                                                          d.bigb, d.err, vec);
             L.mark("k_cc_hook_skip");
         } else {
             k_cc_hook<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v, d.err,
@@ -490,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
 // Sampling variant of the cross-edge pass (the Afforest idea applied to G'):
 // first every vertex unites along its first `k` cross edges, then the component
 // holding most sampled positions is found, and the full pass skips every source
-// already in it. A skipped arc still reaches its other endpoint's side, so here
+// in it (membership fixed before the pass, see k_mark_big). A skipped arc still reaches its other endpoint's side, so here
 // cross edges are tested from both ends: towards a later vertex w as above, and
 // towards an earlier one iff first[u] > last[w] (u after T_w; a parent arc and a
 // back edge to an ancestor fail it).
@@ -537,11 +559,10 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross_skip(const OffT *__r
                                                                  const int2 *__restrict__ cr,
                                                                  const int32_t *__restrict__ lastp,
                                                                  const uint8_t *__restrict__ dirb, int32_t *uf,
-                                                                 const int32_t *big, int *err, bool vec)
+                                                                 const uint32_t *__restrict__ bigb, int *err, bool vec)
 {
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
-    const int32_t root = *big;
     const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
     for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
         arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
@@ -558,7 +579,7 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross_skip(const OffT *__r
             if (j < at.cnt && at.src[j] != cur) {
                 cur = at.src[j];
                 c = __ldg(cr + cur);
-                skip = uf_find(uf, c.y) == root;
+                skip = test_bit(bigb, c.y);
                 if (!skip) lastu = __ldg(lastp + c.x);
             }
             cs[j] = c;
@@ -626,20 +647,33 @@ __global__ void __launch_bounds__(kThreads) k_final_label(int64_t n, const int32
 }
 
 // Label of every vertex: the id of its component's top vertex (roots: their own).
+// A top vertex t (a label) heads nothing itself: its BCC is its class plus the
+// head p(t) (the tree edge above a top is a fence, so p(t) lies outside the
+// class; Algorithm 1's head loop stores p(v) for every v whose parent has
+// another label, and all of one label's writers agree, t among them). So the
+// labels are counted here and each adds one to the count of labels its head
+// heads (articulation points and root heads need it).
 __global__ void __launch_bounds__(kThreads) k_lab_out(int64_t n, const int32_t *__restrict__ fin,
                                                       const int32_t *__restrict__ ord, const int32_t *__restrict__ porig,
-                                                      const int32_t *__restrict__ minorig, int32_t *lab, int32_t *smin)
+                                                      const int32_t *__restrict__ minorig, int32_t *lab, int32_t *smin,
+                                                      int32_t *nh, fbcc_stats *stats, int *err)
 {
+    long long c = 0;
     for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads) {
-        const int32_t v = ord[p];
-        if (porig[p] < 0) {
+        const int32_t v = ord[p], x = porig[p];
+        if (x < 0) {
             lab[v] = v;
             continue;
         }
         const int32_t r = fin[p];
         lab[v] = ord[r];
-        if (r == p) smin[v] = minorig[r];
+        if (r == p) {
+            smin[v] = minorig[r];
+            if (in_range(x, n, err)) atomicAdd(nh + x, 1);
+            ++c;
+        }
     }
+    block_count((long long *)&stats->n_bcc, c);
 }
 
 template <typename OffT>
@@ -670,8 +704,10 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
         L.mark("k_pos_compress");
         k_pos_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, d.porig, n, big);
         L.mark("k_pos_pick_big");
+        k_mark_big<<<gv, kThreads, 0, L.s>>>(d.uf, n, big, d.bigb);
+        L.mark("k_mark_big");
         k_last_cc_cross_skip<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
-            off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, big, d.err, vec);
+            off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, d.bigb, d.err, vec);
         L.mark("k_last_cc_cross_skip");
     } else if (nnz > 0) {
         k_last_cc_cross<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
@@ -681,7 +717,8 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
     CK(cudaMemsetAsync(d.minorig, 0x7f, n * sizeof(int32_t), L.s));
     k_final_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.uf, d.ord, d.porig, d.fin, d.minorig);
     L.mark("k_final_label");
-    k_lab_out<<<gv, kThreads, 0, L.s>>>(n, d.fin, d.ord, d.porig, d.minorig, d.uf, d.smin);
+    CK(cudaMemsetAsync(d.nh, 0, n * sizeof(int32_t), L.s));
+    k_lab_out<<<gv, kThreads, 0, L.s>>>(n, d.fin, d.ord, d.porig, d.minorig, d.uf, d.smin, d.nh, d.stats, d.err);
     L.mark("k_lab_out");
 #undef CK
     return cudaGetLastError();

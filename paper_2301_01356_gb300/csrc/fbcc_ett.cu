@@ -366,18 +366,29 @@ __global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *_
                                                        int32_t *lastp, int32_t *ord, int32_t *porig, int32_t *w1,
                                                        int32_t *w2, long long *ticket, uint64_t *status, int *err)
 {
+    // the tile's records pass through shared memory: coalesced loads, then each
+    // thread takes its kItems consecutive records (slot e at e + e / 8 keeps the
+    // 8-byte reads of a warp free of bank conflicts)
+    __shared__ int2 srec[kTile + kTile / 8];
     const int64_t ntiles = (n2 + kTile - 1) / kTile;
     const int64_t n = n2 / 2;
     while (true) {
         int64_t t = scan_ticket(ticket);
         if (t >= ntiles) return;
         const int64_t p0 = t * kTile + (int64_t)threadIdx.x * kItems;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int e = k * kThreads + threadIdx.x;
+            const int64_t p = t * kTile + e;
+            srec[e + (e >> 3)] = p < n2 ? __ldcs(rec + p) : make_int2(-3, 0);
+        }
+        __syncthreads();
         long long v[kItems];
         int2 r[kItems];
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            const int64_t p = p0 + j;
-            r[j] = p < n2 ? rec[p] : make_int2(-3, 0);
+            const int e = threadIdx.x * kItems + j;
+            r[j] = srec[e + (e >> 3)];
             v[j] = r[j].x >= 0 || r[j].x == -2;
         }
         scan_tile_exclusive(v, t, status, err);

@@ -44,6 +44,8 @@ struct Dev {
     // First-CC
     int32_t *uf;              // union-find parent (First-CC, then Last-CC)
     int32_t *te_u, *te_v;     // tree edge recorded at the vertex it hooked (-1: none)
+    uint32_t *bigb;           // sampling variants: one bit per vertex (First-CC) or position
+                              // (Last-CC) in the sampled largest component, fixed for the full pass
     int2 *xl;                 // local-first First-CC: edges between vertex ranges {u, w}, u < w
     int64_t xl_cap;           // (aliases the rooting scratch, which is dead during First-CC)
     int32_t *tile_v;          // source vertex of the first arc of every arc tile (+1 sentinel)
@@ -86,7 +88,6 @@ struct Dev {
     int32_t *minorig;         // smallest vertex id of the component rooted at position r
     int32_t *smin;            // by label vertex: smallest vertex id of its label class
     // Last-CC and outputs
-    int32_t *head;            // head of label L at [L]
     int32_t *nh;              // number of labels a vertex heads
     unsigned long long *key;  // smallest arc id (src < dst) of label L at [L]
     uint8_t *scanv;           // vertex whose list must be scanned for keys

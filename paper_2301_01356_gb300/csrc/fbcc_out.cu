@@ -4,7 +4,9 @@
 // After Last-CC every non-root vertex v has a label l[v] (the top vertex of its
 // skeleton component). For each v with l[v] != l[p(v)], p(v) is the head of
 // label l[v]; every such writer of one label stores the same vertex (head lemma,
-// section 4.2). Label l's BCC is {v : l[v] = l} plus its head.
+// section 4.2), the top vertex l itself among them, so head(l) = p(l) is read
+// from the parent array rather than stored. Label l's BCC is {v : l[v] = l} plus
+// its head.
 //
 // Expansion to the per-edge canonical form:
 //  - articulation points: non-root heads, and roots that head two or more labels
@@ -29,39 +31,11 @@ namespace fbcc {
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
 
-__global__ void __launch_bounds__(kThreads) k_heads(int64_t n, const int2 *__restrict__ fp,
-                                                    const int32_t *__restrict__ lab, int32_t *head)
-{
-    GRID_STRIDE(v, n)
-    {
-        int32_t x = fp[v].y;
-        if (x < 0) continue;
-        int32_t l = lab[v];
-        if (lab[x] != l) head[l] = x;
-    }
-}
-
-// Labels: non-root v with lab[v] == v. Count them and how many each vertex heads.
-__global__ void __launch_bounds__(kThreads) k_label_count(int64_t n, const int2 *__restrict__ fp,
-                                                          const int32_t *__restrict__ lab,
-                                                          const int32_t *__restrict__ head, int32_t *nh,
-                                                          fbcc_stats *stats, int *err)
-{
-    long long c = 0;
-    GRID_STRIDE(v, n)
-    {
-        if (fp[v].y < 0 || lab[v] != v) continue;
-        if (in_range(head[v], n, err)) atomicAdd(nh + head[v], 1);
-        ++c;
-    }
-    block_count((long long *)&stats->n_bcc, c);
-}
-
 // Articulation points, component count, and the keys that need no list scan.
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__restrict__ off,
                                                       const int2 *__restrict__ fp, const int32_t *__restrict__ lab,
-                                                      const int32_t *__restrict__ head, const int32_t *__restrict__ nh,
+                                                      const int32_t *__restrict__ nh,
                                                       const int32_t *__restrict__ smin,
                                                       uint8_t *is_ap, unsigned long long *key, uint8_t *scanv,
                                                       fbcc_stats *stats, int *err)
@@ -69,14 +43,15 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
     long long nap = 0, ncc = 0;
     GRID_STRIDE(v, n)
     {
-        const bool root = fp[v].y < 0;
+        const int2 fv = fp[v];
+        const bool root = fv.y < 0;
         const int32_t h = nh[v];
         const uint8_t ap = root ? h >= 2 : h >= 1;
         is_ap[v] = ap;
         nap += ap;
         ncc += root;
         if (root || lab[v] != v) continue;
-        const int32_t hd = head[v];
+        const int32_t hd = fv.y;   // a label's head is its parent
         if (!in_range(hd, n, err)) continue;
         const int32_t sm = smin[v];
         const int32_t u0 = hd < sm ? hd : sm;
@@ -100,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
                                                        const uint8_t *__restrict__ scanv,
                                                        const uint8_t *__restrict__ dirb,
                                                        const int32_t *__restrict__ lab,
-                                                       const int32_t *__restrict__ head,
+                                                       const int2 *__restrict__ fp,
                                                        const int32_t *__restrict__ smin, unsigned long long *key,
                                                        bool vec)
 {
@@ -139,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
             const int32_t l = __ldg(lab + x);
             if (l == last_l) continue;  // a later arc of the same BCC cannot be smaller
             last_l = l;
-            const int32_t hd = __ldg(head + l), sm = __ldg(smin + l);
+            const int32_t hd = __ldg(&fp[l].y), sm = __ldg(smin + l);
             if ((hd < sm ? hd : sm) == u) atomicMin(key + l, (unsigned long long)(at.a0 + j));
         }
     }
@@ -164,12 +139,13 @@ __global__ void __launch_bounds__(kThreads) k_rank(int64_t n, const int2 *__rest
                                                    const unsigned long long *__restrict__ key,
                                                    const uint32_t *__restrict__ key_bits,
                                                    const int32_t *__restrict__ key_pre,
-                                                   const int32_t *__restrict__ head, int32_t *rank, int32_t *bcc_head,
+                                                   int32_t *rank, int32_t *bcc_head,
                                                    Batch B, int64_t nnz, int *err)
 {
     GRID_STRIDE(v, n)
     {
-        if (fp[v].y < 0 || lab[v] != v) continue;
+        const int32_t hd = fp[v].y;   // a label's head is its parent
+        if (hd < 0 || lab[v] != v) continue;
         const int64_t k = (int64_t)key[v];
         if (!in_range(k, nnz, err)) continue;
         int32_t r = key_pre[k >> 5] + __popc(key_bits[k >> 5] & ((1u << (k & 31)) - 1u));
@@ -178,10 +154,10 @@ __global__ void __launch_bounds__(kThreads) k_rank(int64_t n, const int2 *__rest
             const int64_t vb = B.vtx_base[g];
             r -= (int32_t)B.bcc_base[g];
             rank[v] = r;
-            if (in_range(r, B.vtx_base[g + 1] - vb, err)) bcc_head[vb + r] = head[v] - (int32_t)vb;
+            if (in_range(r, B.vtx_base[g + 1] - vb, err)) bcc_head[vb + r] = hd - (int32_t)vb;
         } else {
             rank[v] = r;
-            if (in_range(r, n, err)) bcc_head[r] = head[v];
+            if (in_range(r, n, err)) bcc_head[r] = hd;
         }
     }
 }
@@ -318,18 +294,13 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     const int gv = grid_for(L, ceil_div(n, kThreads));
     const int64_t ntiles = ceil_div(nnz, kWTile);
     const int64_t nwords = ceil_div(nnz, 32);
-    CK(cudaMemsetAsync(d.nh, 0, n * sizeof(int32_t), L.s));
     CK(cudaMemsetAsync(d.scanv, 0, n, L.s));
-    k_heads<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.head);
-    L.mark("k_heads");
-    k_label_count<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.head, d.nh, d.stats, d.err);
-    L.mark("k_label_count");
-    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.uf, d.head, d.nh, d.smin, is_ap, d.key, d.scanv, d.stats, d.err);
+    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.uf, d.nh, d.smin, is_ap, d.key, d.scanv, d.stats, d.err);
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
         k_key_scan<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.dirb,
-                                                                   d.uf, d.head, d.smin, d.key, vec);
+                                                                   d.uf, d.fp, d.smin, d.key, vec);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
         k_key_bits<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.key, d.key_bits, nnz, d.err);
@@ -340,7 +311,7 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
             k_bcc_base<<<grid_for(L, ceil_div(B.G + 1, kThreads)), kThreads, 0, L.s>>>(B, d.key_bits, d.key_pre);
             L.mark("k_bcc_base");
         }
-        k_rank<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.key, d.key_bits, d.key_pre, d.head, d.rank, bcc_head, B, nnz, d.err);
+        k_rank<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.key, d.key_bits, d.key_pre, d.rank, bcc_head, B, nnz, d.err);
         L.mark("k_rank");
         k_fo<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.rank, d.vbits, d.word, d.stats);
         L.mark("k_fo");
