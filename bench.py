@@ -156,7 +156,7 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_chase": 16 * A + 16 * nr,
         "k_jump": 24 * nr,
         "k_comp_size": 16 * n,
-        "k_place": 36 * A,
+        "k_place_records": 30 * A,
         "k_root_tags": 12 * n_cc,
         "k_preorder": 16 * n + 28 * n,
         "k_first_of": 12 * n,
@@ -173,15 +173,13 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_edge_out": B * (n + 1) + 4 * nnz + nnz // 8 + 4 * nnz // 2 + 4 * n + 4 * nnz + nnz,
         "k_cc_local": B * (n + 1) + 4 * nnz + 12 * n,
         "k_cc_hook_cross": B * (n + 1) + 4 * nnz + 8 * n,
-        "k_tour_records": 28 * A,
         "k_rulers2": 17 * nr,
         "k_chase2": 20 * nr,
         "k_expand2": 28 * nr,
         "k_ext_compact": n,
         "k_ext_jump": 12 * (n // 64),
         "k_plain_label": 20 * n,
-        "k_final_label": 20 * n,
-        "k_lab_out": 24 * n,
+        "k_final_label": 28 * n,
         "k_lcc_sample": B * (n + 1) + 16 * n + 24 * n,
         "k_pos_compress": 8 * n,
         "k_last_cc_cross_skip": B * (n + 1) + 4 * nnz + nnz // 8 + 16 * n,

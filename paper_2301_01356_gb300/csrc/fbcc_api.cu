@@ -98,7 +98,6 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.is_head = c.take<uint8_t>(2 * N);
     d.link = c.take<int2>(2 * N);
     d.relem = c.take<int32_t>(d.ruler_max);
-    d.oo = c.take<int2>(2 * N);
     for (int i = 0; i < 2; ++i) {
         d.rnext[i] = c.take<int32_t>(d.ruler_max);
         d.rval[i] = c.take<int32_t>(d.ruler_max);
@@ -112,7 +111,6 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.sd1 = c.take<int32_t>(d.ruler_max);
     d.csize = c.take<int32_t>(N + 1);
     d.vbase = c.take<int32_t>(N + 1);
-    d.pos = c.take<int32_t>(2 * N);
     d.rec = c.take<int2>(2 * N);
     const size_t rooting_end = c.used;
     {
@@ -134,8 +132,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.qlist = c.take<int32_t>(N);
     d.first4 = c.take<int32_t>(N);
     d.cr = c.take<int2>(N);
-    d.fin = c.take<int32_t>(N);
-    d.minorig = c.take<int32_t>(N);
+    d.lab = c.take<int32_t>(N);
     d.smin = c.take<int32_t>(N);
     d.nh = c.take<int32_t>(N);
     d.key = c.take<unsigned long long>(N);
@@ -641,7 +638,7 @@ extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *nam
         }
         return FBCC_OK;
     }
-    if (!strcmp(name, "label")) src = d.uf;
+    if (!strcmp(name, "label")) src = d.lab;
     else if (!strcmp(name, "w1")) src = d.w1;
     else if (!strcmp(name, "w2")) src = d.w2;
     else if (!strcmp(name, "low")) src = d.low;

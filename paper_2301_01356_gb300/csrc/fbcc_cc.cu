@@ -623,55 +623,47 @@ __global__ void __launch_bounds__(kThreads) k_pos_pick_big(int32_t *uf, const in
     }
 }
 
-// Final root of every position and the smallest vertex id of every component.
-// Lanes with the same root reduce first; a read of the current minimum (stale
-// values only cost an extra atomic) filters most of the remaining atomics.
+// Final labels. Every position's skeleton component root r (its top vertex has
+// position r), the label of its vertex (the top vertex's id; roots are their own
+// label), and the smallest vertex id of every class (lanes with the same root
+// reduce first, and a read of the current minimum, stale values only costing an
+// extra atomic, filters most of the remaining atomics).
+// A top vertex t heads nothing itself: its BCC is its class plus the head p(t)
+// (the tree edge above a top is a fence, so p(t) lies outside the class;
+// Algorithm 1's head loop stores p(v) for every v whose parent has another label,
+// and all of one label's writers agree, t among them). So the labels are counted
+// here and each adds one to the count of labels its head heads (articulation
+// points and root heads need it). The labels go to their own array: the
+// union-find over positions is still being read.
 __global__ void __launch_bounds__(kThreads) k_final_label(int64_t n, const int32_t *__restrict__ lp,
-                                                          const int32_t *uf, const int32_t *__restrict__ ord,
-                                                          const int32_t *__restrict__ porig, int32_t *fin,
-                                                          int32_t *minorig)
+                                                          const int32_t *__restrict__ uf,
+                                                          const int32_t *__restrict__ ord,
+                                                          const int32_t *__restrict__ porig, int32_t *lab,
+                                                          int32_t *smin, int32_t *nh, fbcc_stats *stats, int *err)
 {
+    long long c = 0;
     const int64_t n_pad = (n + 31) & ~31ll;
     for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * kThreads) {
-        int32_t r = -1, v = INT32_MAX;
+        int32_t r = -1, v = INT32_MAX, l = -1;
         if (p < n) {
-            r = uf_root(uf, plain_root(lp, p));
-            fin[p] = r;
-            if (porig[p] >= 0) v = ord[p];
-            else r = -1;
+            const int32_t u = ord[p], x = porig[p];
+            if (x < 0) {
+                lab[u] = u;
+            } else {
+                r = uf_root(uf, plain_root(lp, p));
+                l = ord[r];
+                lab[u] = l;
+                v = u;
+                if (r == p) {
+                    if (in_range(x, n, err)) atomicAdd(nh + x, 1);
+                    ++c;
+                }
+            }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, r);
         const int32_t m = (int32_t)__reduce_min_sync(peers, (unsigned)v);
-        if (r >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1 && m < minorig[r]) atomicMin(minorig + r, m);
-    }
-}
-
-// Label of every vertex: the id of its component's top vertex (roots: their own).
-// A top vertex t (a label) heads nothing itself: its BCC is its class plus the
-// head p(t) (the tree edge above a top is a fence, so p(t) lies outside the
-// class; Algorithm 1's head loop stores p(v) for every v whose parent has
-// another label, and all of one label's writers agree, t among them). So the
-// labels are counted here and each adds one to the count of labels its head
-// heads (articulation points and root heads need it).
-__global__ void __launch_bounds__(kThreads) k_lab_out(int64_t n, const int32_t *__restrict__ fin,
-                                                      const int32_t *__restrict__ ord, const int32_t *__restrict__ porig,
-                                                      const int32_t *__restrict__ minorig, int32_t *lab, int32_t *smin,
-                                                      int32_t *nh, fbcc_stats *stats, int *err)
-{
-    long long c = 0;
-    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads) {
-        const int32_t v = ord[p], x = porig[p];
-        if (x < 0) {
-            lab[v] = v;
-            continue;
-        }
-        const int32_t r = fin[p];
-        lab[v] = ord[r];
-        if (r == p) {
-            smin[v] = minorig[r];
-            if (in_range(x, n, err)) atomicAdd(nh + x, 1);
-            ++c;
-        }
+        if (r >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1 && in_range(l, n, err) && m < smin[l])
+            atomicMin(smin + l, m);
     }
     block_count((long long *)&stats->n_bcc, c);
 }
@@ -714,12 +706,10 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
             off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, d.err, vec);
         L.mark("k_last_cc_cross");
     }
-    CK(cudaMemsetAsync(d.minorig, 0x7f, n * sizeof(int32_t), L.s));
-    k_final_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.uf, d.ord, d.porig, d.fin, d.minorig);
-    L.mark("k_final_label");
+    CK(cudaMemsetAsync(d.smin, 0x7f, n * sizeof(int32_t), L.s));
     CK(cudaMemsetAsync(d.nh, 0, n * sizeof(int32_t), L.s));
-    k_lab_out<<<gv, kThreads, 0, L.s>>>(n, d.fin, d.ord, d.porig, d.minorig, d.uf, d.smin, d.nh, d.stats, d.err);
-    L.mark("k_lab_out");
+    k_final_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.uf, d.ord, d.porig, d.lab, d.smin, d.nh, d.stats, d.err);
+    L.mark("k_final_label");
 #undef CK
     return cudaGetLastError();
 }

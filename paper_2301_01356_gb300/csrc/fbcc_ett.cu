@@ -110,12 +110,15 @@ __global__ void __launch_bounds__(kThreads) k_succ_rulers(int64_t n, const int32
 
 // Each ruler walks its successors until the next ruler or the tour's end. A
 // thread advances kChains rulers' walks in lock step, so it keeps that many
-// independent loads in flight (the walk is bound by load latency).
+// independent loads in flight (the walk is bound by load latency). Every
+// non-ruler arc is visited by exactly one walk, which overwrites its link entry
+// (just read) with {owning ruler, -distance from it}: a ruler's entry keeps
+// {successor, ruler id >= 0}, so the sign of .y tells the two apart afterwards,
+// and the write lands in a line the walk has just loaded.
 template <int kChains>
 __global__ void __launch_bounds__(kThreads) k_chase(int64_t n,
                                                     const long long *__restrict__ nr_p, const int32_t *__restrict__ relem,
-                                                    const int2 *__restrict__ link, int2 *oo, int32_t *rnext,
-                                                    int32_t *rlen, int *err)
+                                                    int2 *link, int32_t *rnext, int32_t *rlen, int *err)
 {
     const int64_t A = 2 * n;
     const int64_t nr = *nr_p;
@@ -131,9 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_chase(int64_t n,
             nxr[k] = -1;
             t[k] = -1;
             if (r < nr) {
-                const int32_t s = relem[r];
-                oo[s] = make_int2((int32_t)r, 0);
-                t[k] = link[s].x;
+                t[k] = link[relem[r]].x;
                 if (t[k] >= 0) live |= 1u << k;
             }
         }
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_chase(int64_t n,
                     live &= ~(1u << k);
                     continue;
                 }
-                oo[t[k]] = make_int2((int32_t)(r0 + k * T), acc[k]++);
+                link[t[k]] = make_int2((int32_t)(r0 + k * T), -(acc[k]++));
                 t[k] = lk[k].x;
                 if (t[k] < 0) live &= ~(1u << k);
             }
@@ -300,37 +301,40 @@ __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t
     }
 }
 
-// Tour position of every tree arc: 2*base + L - (arcs from it to the tour's end).
-__global__ void __launch_bounds__(kThreads) k_place(int64_t n, const int32_t *__restrict__ te_u,
-                                                    const int32_t *__restrict__ te_v, const int32_t *__restrict__ uf,
-                                                    const int32_t *__restrict__ csize, const int32_t *__restrict__ vbase,
-                                                    const int2 *__restrict__ oo, const int32_t *__restrict__ sd,
-                                                    int32_t *pos, int *err)
+// Tour positions of both arcs of every forest edge, and their tour records. The
+// position of arc s is its tour's base (2 * vbase at the root r) plus the tour
+// length L = 2 (size(r) - 1) minus its distance to the tour's end, which is the
+// owning ruler's suffix length minus the arc's distance from that ruler. The
+// earlier of the two arcs is the down arc: it stores {child, parent}; the up
+// arc stores {-1, its distance back to the down arc}.
+__global__ void __launch_bounds__(kThreads) k_place_records(int64_t n, const int32_t *__restrict__ te_u,
+                                                            const int32_t *__restrict__ te_v,
+                                                            const int32_t *__restrict__ uf,
+                                                            const int32_t *__restrict__ csize,
+                                                            const int32_t *__restrict__ vbase,
+                                                            const int2 *__restrict__ link,
+                                                            const int32_t *__restrict__ sd, int2 *rec, int *err)
 {
-    GRID_STRIDE(s, 2 * n)
+    GRID_STRIDE(h, n)
     {
-        if (te_u[s >> 1] < 0) continue;
-        const int32_t r = uf[arc_dst(te_u, te_v, s)];
+        const int32_t u = te_u[h];
+        if (u < 0) continue;
+        const int32_t v = te_v[h];
+        const int32_t r = uf[u];
         const int32_t L = 2 * (csize[r] - 1);
-        const int2 o = oo[s];
-        const int32_t dist = sd[o.x] - o.y;
-        pos[s] = in_range(dist - 1, L, err) ? 2 * vbase[r] + L - dist : -1;
-    }
-}
-
-// Tour record at every arc's position: a down arc (it precedes its reverse)
-// stores {child, parent}; an up arc stores {-1, the child it leaves}.
-__global__ void __launch_bounds__(kThreads) k_tour_records(int64_t n, const int32_t *__restrict__ te_u,
-                                                           const int32_t *__restrict__ te_v,
-                                                           const int32_t *__restrict__ pos, int2 *rec)
-{
-    GRID_STRIDE(s, 2 * n)
-    {
-        if (te_u[s >> 1] < 0) continue;
-        const int32_t p = pos[s], q = pos[s ^ 1];
-        if (p < 0) continue;
-        // down arc x->y: {y, x}; up arc: {-1, distance back to its down arc}
-        rec[p] = p < q ? make_int2(arc_dst(te_u, te_v, s), arc_src(te_u, te_v, s)) : make_int2(-1, p - q);
+        const int32_t base = 2 * vbase[r] + L;
+        const int4 lk = *reinterpret_cast<const int4 *>(link + 2 * h);   // arcs 2h (u->v) and 2h+1 (v->u)
+        const int32_t d0 = lk.y >= 0 ? sd[lk.y] : sd[lk.x] + lk.y;
+        const int32_t d1 = lk.w >= 0 ? sd[lk.w] : sd[lk.z] + lk.w;
+        if (!in_range(d0 - 1, L, err) || !in_range(d1 - 1, L, err)) continue;
+        const int32_t p0 = base - d0, p1 = base - d1;
+        if (p0 < p1) {
+            rec[p0] = make_int2(v, u);
+            rec[p1] = make_int2(-1, p1 - p0);
+        } else {
+            rec[p1] = make_int2(u, v);
+            rec[p0] = make_int2(-1, p0 - p1);
+        }
     }
 }
 
@@ -432,11 +436,11 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     const int64_t rbound = n / 2 + ceil_div(2 * n, ruler_stride) + 1;
     const int gr = grid_for(L, ceil_div(rbound, kThreads));
     if (chase_chains >= 4)
-        k_chase<4><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
+        k_chase<4><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.rnx1, d.rlen, d.err);
     else if (chase_chains == 2)
-        k_chase<2><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
+        k_chase<2><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.rnx1, d.rlen, d.err);
     else
-        k_chase<1><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.oo, d.rnx1, d.rlen, d.err);
+        k_chase<1><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.rnx1, d.rlen, d.err);
     L.mark("k_chase");
     long long *nr2 = d.counters + 3;
     CK(cudaMemsetAsync(nr2, 0, sizeof(long long), L.s));
@@ -463,10 +467,8 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_comp_size");
     CK(cudaGetLastError());
     CK(launch_scan_i32(d, d.csize, d.vbase, n, L));
-    k_place<<<ga, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.csize, d.vbase, d.oo, sd, d.pos, d.err);
-    L.mark("k_place");
-    k_tour_records<<<ga, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.pos, d.rec);
-    L.mark("k_tour_records");
+    k_place_records<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.csize, d.vbase, d.link, sd, d.rec, d.err);
+    L.mark("k_place_records");
     k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.fp, d.lastp, d.ord, d.porig, d.w1,
                                           d.w2);
     L.mark("k_root_tags");

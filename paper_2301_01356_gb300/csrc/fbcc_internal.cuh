@@ -53,9 +53,9 @@ struct Dev {
     int32_t *lhead;           // first forest arc of every vertex's list (-1: none)
     int32_t *nxt;             // next arc in its source's list (2n ids; -1: last)
     uint8_t *is_head;         // first arc of a tour (2n)
-    int2 *link;               // {succ, ruler id or -1} per tree arc
+    int2 *link;               // {succ, ruler id or -1} per tree arc; after the walks a non-ruler
+                              // arc holds {owning ruler, -distance from it}
     int32_t *relem;           // arc of ruler r
-    int2 *oo;                 // {ruler owning the arc, the arc's distance from it}
     int32_t *rnext[2], *rval[2];  // ruler list: next ruler and suffix weight (double buffered)
     int32_t *rlen;            // ruler segment length
     int32_t *rnx1;            // next ruler in the tour (-1: last)
@@ -65,7 +65,6 @@ struct Dev {
     int32_t *sd1;             // suffix length (arcs to the tour's end) from every ruler
     int32_t *csize;           // component size at its root, 0 elsewhere
     int32_t *vbase;           // first preorder number of the component at its root
-    int32_t *pos;             // tour position of every tree arc
     int2 *rec;                // tour record at every position (down/up arc, padding)
     // Tagging (fp indexed by vertex; the rest by preorder number)
     int2 *fp;                 // {first, parent} by vertex (parent -1 at a root)
@@ -84,8 +83,7 @@ struct Dev {
     int32_t *qlist;           // compacted positions with ext set
     int2 *cr;                 // by vertex {first, plain-component root} (Last-CC arc passes)
     int32_t *lastp;           // last[] by preorder number (written by the preorder scan)
-    int32_t *fin;             // final skeleton-component root of every position
-    int32_t *minorig;         // smallest vertex id of the component rooted at position r
+    int32_t *lab;             // Last-CC label by vertex: its class's top vertex (a root: itself)
     int32_t *smin;            // by label vertex: smallest vertex id of its label class
     // Last-CC and outputs
     int32_t *nh;              // number of labels a vertex heads
@@ -228,16 +226,16 @@ __device__ __forceinline__ int64_t scan_ticket(long long *ticket)
     return t;
 }
 
-// In: v[] the thread's kItems values (items tile*kTile + threadIdx.x*kItems + j).
+// In: v[] the thread's N values (items tile*N*kThreads + threadIdx.x*N + j).
 // Out: v[] their global exclusive prefixes; returns the tile's inclusive total end.
-__device__ __forceinline__ long long scan_tile_exclusive(long long (&v)[kItems], int64_t tile,
-                                                         uint64_t *status, int *err)
+template <int N>
+__device__ __forceinline__ long long scan_tile_exclusive(long long (&v)[N], int64_t tile, uint64_t *status, int *err)
 {
     __shared__ long long warp_tot[kThreads / 32];
     __shared__ long long tile_excl;
     long long run = 0;
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
+    for (int j = 0; j < N; ++j) {
         long long x = v[j];
         v[j] = run;
         run += x;
@@ -302,7 +300,7 @@ __device__ __forceinline__ long long scan_tile_exclusive(long long (&v)[kItems],
     __syncthreads();
     long long base = tile_excl + texcl;
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) v[j] += base;
+    for (int j = 0; j < N; ++j) v[j] += base;
     return tile_excl + agg;
 }
 

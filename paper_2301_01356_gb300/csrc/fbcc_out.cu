@@ -295,15 +295,15 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     const int64_t ntiles = ceil_div(nnz, kWTile);
     const int64_t nwords = ceil_div(nnz, 32);
     CK(cudaMemsetAsync(d.scanv, 0, n, L.s));
-    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.uf, d.nh, d.smin, is_ap, d.key, d.scanv, d.stats, d.err);
+    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.lab, d.nh, d.smin, is_ap, d.key, d.scanv, d.stats, d.err);
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
         k_key_scan<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.dirb,
-                                                                   d.uf, d.fp, d.smin, d.key, vec);
+                                                                   d.lab, d.fp, d.smin, d.key, vec);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
-        k_key_bits<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.key, d.key_bits, nnz, d.err);
+        k_key_bits<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.lab, d.key, d.key_bits, nnz, d.err);
         L.mark("k_key_bits");
         CK(cudaGetLastError());
         CK(launch_scan_popc(d, d.key_bits, d.key_pre, nwords, L));
@@ -311,9 +311,9 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
             k_bcc_base<<<grid_for(L, ceil_div(B.G + 1, kThreads)), kThreads, 0, L.s>>>(B, d.key_bits, d.key_pre);
             L.mark("k_bcc_base");
         }
-        k_rank<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.key, d.key_bits, d.key_pre, d.rank, bcc_head, B, nnz, d.err);
+        k_rank<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.lab, d.key, d.key_bits, d.key_pre, d.rank, bcc_head, B, nnz, d.err);
         L.mark("k_rank");
-        k_fo<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.uf, d.rank, d.vbits, d.word, d.stats);
+        k_fo<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.lab, d.rank, d.vbits, d.word, d.stats);
         L.mark("k_fo");
         const bool vec_out = ((uintptr_t)edge_bcc & 15) == 0 && ((uintptr_t)is_bridge & 7) == 0;
         k_edge_out<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles,
