@@ -2,9 +2,11 @@
 
 For every size bucket of a sample batch, each candidate configuration (ruler
 stride of the list ranking; First-CC variant: plain hooking, local-first in
-shared memory, or sampled) is timed with CUDA events on the bucket's batched
-solve, and the fastest is written to ``tuning.json`` beside this module, which
-``batch.BatchRunner`` and ``bench.py`` read.
+shared memory, or sampled; Last-CC sampling) is timed with CUDA events on the
+bucket's batched solve (mean of a few runs), the three fastest are timed again
+over many more runs (a sampled variant can be slow now and then, and a short
+mean can miss it), and the fastest of those is written to ``tuning.json`` beside
+this module, which ``batch.BatchRunner`` and ``bench.py`` read.
 
     python -m paper_2301_01356_gb300.autotune [--graphs 512] [--out PATH]
 """
@@ -38,7 +40,11 @@ def _time(fn, reps: int) -> float:
     return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
 
-def tune_batch(batch, reps: int = 8, candidates=CANDIDATES, buckets=B.BUCKETS) -> list:
+def _finalists(times: dict, k: int = 3) -> list:
+    return sorted(times, key=times.get)[:k]
+
+
+def tune_batch(batch, reps: int = 8, candidates=CANDIDATES, buckets=B.BUCKETS, final_reps: int = 30) -> list:
     out = []
     sizes = batch.sizes()
     for lo, hi in buckets:
@@ -51,14 +57,19 @@ def tune_batch(batch, reps: int = 8, candidates=CANDIDATES, buckets=B.BUCKETS) -
         for cfg in candidates:
             fbcc.fbcc_workspace_configure(b.ws, **cfg)
             times[json.dumps(cfg, sort_keys=True)] = _time(runner.run, reps)
-        best = min(times, key=times.get)
+        final = {}
+        for key in _finalists(times):   # the closest few again, long enough to see rare slow runs
+            fbcc.fbcc_workspace_configure(b.ws, **json.loads(key))
+            final[key] = _time(runner.run, final_reps)
+        best = min(final, key=final.get)
+        times.update(final)
         out.append({"lo": lo, "hi": hi, "graphs": int(idx.size), "config": json.loads(best), "ms": times[best],
                     "candidates_ms": times})
         runner.close()
     return out
 
 
-def tune_graph(g, off64: bool, reps: int = 8, candidates=CANDIDATES) -> dict:
+def tune_graph(g, off64: bool, reps: int = 8, candidates=CANDIDATES, final_reps: int = 30) -> dict:
     import torch
     off = torch.from_numpy(g.offsets.astype(np.int64 if off64 else np.int32)).cuda()
     adj = torch.from_numpy(g.adj).cuda()
@@ -67,8 +78,13 @@ def tune_graph(g, off64: bool, reps: int = 8, candidates=CANDIDATES) -> dict:
     for cfg in candidates:
         s.configure(**cfg)
         times[json.dumps(cfg, sort_keys=True)] = _time(lambda: s.enqueue(off, adj), reps)
+    final = {}
+    for key in _finalists(times):
+        s.configure(**json.loads(key))
+        final[key] = _time(lambda: s.enqueue(off, adj), final_reps)
     s.close()
-    best = min(times, key=times.get)
+    best = min(final, key=final.get)
+    times.update(final)
     return {"config": json.loads(best), "ms": times[best], "candidates_ms": times}
 
 

@@ -308,21 +308,16 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
         for (int i = threadIdx.x; i < kRmqTile; i += kThreads)
             if (base + i >= n) sp[i] = (int32_t)(base + i);
         __syncthreads();
-        // pointer doubling inside the tile (at most 10 rounds for 1024 positions,
-        // fewer when the chains are short); pointers only move towards their root,
-        // so updating in place is safe
+        // pointer doubling inside the tile (10 rounds cover 1024 positions); pointers
+        // only move towards their root, so updating in place is safe
         for (int r = 0; r < 10; ++r) {
-            int moved = 0;
 #pragma unroll
             for (int k = 0; k < kPer; ++k) {
                 const int i = threadIdx.x + k * kThreads;
                 const int32_t q = sp[i];
-                if (q >= base) {
-                    const int32_t q2 = sp[q - base];
-                    if (q2 != q) { sp[i] = q2; moved = 1; }
-                }
+                if (q >= base) sp[i] = sp[q - base];
             }
-            if (!__syncthreads_or(moved)) break;
+            __syncthreads();
         }
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
