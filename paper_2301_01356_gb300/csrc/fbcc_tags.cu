@@ -163,22 +163,33 @@ __global__ void __launch_bounds__(kThreads) k_rmq_prefix(int64_t n, const int32_
     }
 }
 
-// Sparse-table level j over the tile extrema: level j covers 2^j tiles.
-__global__ void __launch_bounds__(kThreads) k_rmq_level(int64_t ntiles, int j, int64_t stride,
+// Sparse-table levels j0 .. j0+cnt-1 over the tile extrema (level j covers 2^j
+// tiles), all from level j0-1 in one launch: level j0+q is the extremum of
+// 2^(q+1) entries of level j0-1, h = 2^(j0-1) apart.
+constexpr int kLevelsPerLaunch = 3;
+
+__global__ void __launch_bounds__(kThreads) k_rmq_level(int64_t ntiles, int j0, int cnt, int64_t stride,
                                                         int32_t *tmin, int32_t *tmax)
 {
-    const int32_t *pm = tmin + (int64_t)(j - 1) * stride, *pM = tmax + (int64_t)(j - 1) * stride;
-    int32_t *qm = tmin + (int64_t)j * stride, *qM = tmax + (int64_t)j * stride;
-    const int64_t h = 1ll << (j - 1);
+    const int32_t *pm = tmin + (int64_t)(j0 - 1) * stride, *pM = tmax + (int64_t)(j0 - 1) * stride;
+    const int64_t h = 1ll << (j0 - 1);
     GRID_STRIDE(t, ntiles)
     {
         int32_t a = pm[t], b = pM[t];
-        if (t + h < ntiles) {
-            a = pm[t + h] < a ? pm[t + h] : a;
-            b = pM[t + h] > b ? pM[t + h] : b;
+        int k = 1;
+#pragma unroll
+        for (int q = 0; q < kLevelsPerLaunch; ++q) {
+            if (q >= cnt) break;
+            for (; k < (2 << q); ++k) {   // fold in the entries k*h, up to 2^(q+1) of them
+                const int64_t u = t + (int64_t)k * h;
+                if (u < ntiles) {
+                    a = pm[u] < a ? pm[u] : a;
+                    b = pM[u] > b ? pM[u] : b;
+                }
+            }
+            tmin[(int64_t)(j0 + q) * stride + t] = a;
+            tmax[(int64_t)(j0 + q) * stride + t] = b;
         }
-        qm[t] = a;
-        qM[t] = b;
     }
 }
 
@@ -243,22 +254,37 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
+            // this warp holds one chunk (lane = position in it): a sparse table of
+            // the chunk in registers answers ranges inside the chunk with two
+            // shuffles per level, the same work for every lane
             const int i = threadIdx.x + k * kThreads;
             const int64_t p = base + i;
-            if (p >= n) continue;
-            int32_t e = lastp[p];
-            if (e < p || e >= n) { atomicOr(err, kErrIndex); e = (int32_t)p; }
-            int32_t lo, hi;
+            const bool valid = p < n;
+            int32_t e = valid ? lastp[p] : (int32_t)p;
+            if (valid && (e < p || e >= n)) { atomicOr(err, kErrIndex); e = (int32_t)p; }
             const int ci = i / kChunk;
+            const int jl = (int)(e - base) - ci * kChunk;          // e's lane when inside the chunk
+            const bool in_chunk = jl < kChunk;
+            int32_t ra = s1[i], rb = s2[i], lo = INT32_MAX, hi = INT32_MIN;
+            const int len = in_chunk ? jl - lane + 1 : 1;
+            const int kl = 31 - __clz(len);                          // 0..5
+#pragma unroll
+            for (int lv = 0; lv < 5; ++lv) {
+                if (lv > 0) {   // ra/rb: extremum of the 2^lv positions from this lane on
+                    const int h = 1 << (lv - 1);
+                    const int32_t xa = __shfl_down_sync(0xffffffffu, ra, h), xb = __shfl_down_sync(0xffffffffu, rb, h);
+                    if (lane + h < kChunk) { ra = xa < ra ? xa : ra; rb = xb > rb ? xb : rb; }
+                }
+                int src = (in_chunk ? jl : lane) - (1 << lv) + 1;
+                src = src < 0 ? 0 : src;
+                const int32_t ya = __shfl_sync(0xffffffffu, ra, src), yb = __shfl_sync(0xffffffffu, rb, src);
+                if (lv == kl) { lo = ya < ra ? ya : ra; hi = yb > rb ? yb : rb; }
+            }
+            if (kl == 5) { lo = c1[ci]; hi = c2[ci]; }               // the whole chunk
+            if (!valid) continue;
             if (e < base + kRmqTile) {
                 const int je = (int)(e - base), ce = je / kChunk;
-                if (ci == ce) {
-                    lo = INT32_MAX; hi = INT32_MIN;
-                    for (int q = i; q <= je; ++q) {
-                        lo = s1[q] < lo ? s1[q] : lo;
-                        hi = s2[q] > hi ? s2[q] : hi;
-                    }
-                } else {
+                if (ci != ce) {
                     lo = suf1[i] < pre1[je] ? suf1[i] : pre1[je];
                     hi = suf2[i] > pre2[je] ? suf2[i] : pre2[je];
                     for (int c = ci + 1; c < ce; ++c) {
@@ -346,8 +372,11 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
     const int64_t rt = ceil_div(n, kRmqTile);
     k_rmq_prefix<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax);
     L.mark("k_rmq_prefix");
-    for (int j = 1; (1ll << j) <= rt; ++j) {
-        k_rmq_level<<<grid_for(L, ceil_div(rt, kThreads)), kThreads, 0, L.s>>>(rt, j, d.rmq_tiles_max, d.tmin,
+    int top = 0;   // levels 1 .. top are needed: 2^top <= rt
+    while ((2ll << top) <= rt) ++top;
+    for (int j = 1; j <= top; j += kLevelsPerLaunch) {
+        const int cnt = top - j + 1 < kLevelsPerLaunch ? top - j + 1 : kLevelsPerLaunch;
+        k_rmq_level<<<grid_for(L, ceil_div(rt, kThreads)), kThreads, 0, L.s>>>(rt, j, cnt, d.rmq_tiles_max, d.tmin,
                                                                                  d.tmax);
         L.mark("k_rmq_level");
     }
