@@ -201,46 +201,63 @@ __device__ __forceinline__ int32_t sm_find(uint16_t *par, int32_t v)
 
 template <typename OffT>
 __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restrict__ off,
-                                                            const int32_t *__restrict__ adj, int64_t n, int V,
-                                                            int32_t *uf, int32_t *te_u, int32_t *te_v, int2 *xl,
-                                                            int64_t xl_cap, long long *nxl, int *err)
+                                                            const int32_t *__restrict__ adj, int64_t n, int64_t nnz,
+                                                            int V, int32_t *uf, int32_t *te_u, int32_t *te_v,
+                                                            int2 *xl, int64_t xl_cap, long long *nxl, int *err,
+                                                            bool vec)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    OffT *woff = reinterpret_cast<OffT *>(smem);                                   // V+1 offsets
-    uint16_t *par = reinterpret_cast<uint16_t *>(smem + (size_t)(V + 1) * sizeof(OffT) + 8);
+    uint32_t *woff = reinterpret_cast<uint32_t *>(smem);                   // V+1 offsets, relative to the range
+    uint16_t *par = reinterpret_cast<uint16_t *>(smem + (size_t)(V + 1) * 4 + 12);
     const int lane = threadIdx.x & 31;
     const int64_t nranges = (n + V - 1) / V;
     for (int64_t g = blockIdx.x; g < nranges; g += gridDim.x) {
         const int64_t v0 = g * V;
         const int cnt = (int)((n - v0) < V ? (n - v0) : V);
+        const int64_t a_beg = off[v0], a_end = off[v0 + cnt];
+        if (a_end - a_beg > (int64_t)0x7fffffff) {   // relative offsets are 32-bit
+            if (threadIdx.x == 0) atomicOr(err, kErrIndex);
+            continue;
+        }
         __syncthreads();
         for (int i = threadIdx.x; i <= cnt; i += kLocalThreads) {
-            woff[i] = off[v0 + i];
+            woff[i] = (uint32_t)(off[v0 + i] - a_beg);
             if (i < cnt) par[i] = (uint16_t)i;
         }
         __syncthreads();
-        const int64_t a_beg = woff[0], a_end = woff[cnt];
-        const int64_t rounds = (a_end - a_beg + (int64_t)kLocalThreads * kItems - 1) / ((int64_t)kLocalThreads * kItems);
-        // each thread takes runs of kItems consecutive arcs; every lane runs every
-        // round (warp-wide reservation of the list slots below)
+        // runs of kItems arcs aligned to kItems in the global arc order (two 16-byte
+        // loads each); the range's arcs are [a_beg, a_end), relative [0, span)
+        const int64_t a_al = a_beg & ~(int64_t)(kItems - 1);
+        const int span = (int)(a_end - a_beg);
+        const int64_t rounds = (a_end - a_al + (int64_t)kLocalThreads * kItems - 1) / ((int64_t)kLocalThreads * kItems);
+        // every lane runs every round (warp-wide reservation of the list slots below)
         for (int64_t rd = 0; rd < rounds; ++rd) {
-            const int64_t a0 = a_beg + (rd * kLocalThreads + threadIdx.x) * kItems;
+            const int64_t a0 = a_al + (rd * kLocalThreads + threadIdx.x) * kItems;
+            const int r0 = (int)(a0 - a_beg);          // relative; the first run may start below 0
             int32_t dw[kItems], su[kItems];
             uint32_t xmask = 0;   // arcs to a later range
-            if (a0 < a_end) {
-                int lo = 0, hi = cnt - 1;   // the vertex whose list holds a0
+            if (r0 < span) {
+                if (vec && a0 + kItems <= nnz) {
+                    const int4 x = __ldcs(reinterpret_cast<const int4 *>(adj + a0));
+                    const int4 y = __ldcs(reinterpret_cast<const int4 *>(adj + a0) + 1);
+                    dw[0] = x.x; dw[1] = x.y; dw[2] = x.z; dw[3] = x.w;
+                    dw[4] = y.x; dw[5] = y.y; dw[6] = y.z; dw[7] = y.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kItems; ++j) dw[j] = a0 + j < nnz ? __ldcs(adj + a0 + j) : 0;
+                }
+                const uint32_t rs = r0 > 0 ? (uint32_t)r0 : 0u;
+                int lo = 0, hi = cnt - 1;   // the vertex whose list holds the run's first arc
                 while (lo < hi) {
                     int mid = (lo + hi + 1) >> 1;
-                    if ((int64_t)woff[mid] <= a0) lo = mid; else hi = mid - 1;
+                    if (woff[mid] <= rs) lo = mid; else hi = mid - 1;
                 }
 #pragma unroll
-                for (int j = 0; j < kItems; ++j) dw[j] = a0 + j < a_end ? __ldcs(adj + a0 + j) : 0;
-#pragma unroll
                 for (int j = 0; j < kItems; ++j) {
-                    const int64_t a = a0 + j;
+                    const int r = r0 + j;
                     su[j] = -1;
-                    if (a >= a_end) continue;
-                    while ((int64_t)woff[lo + 1] <= a) ++lo;
+                    if (r < 0 || r >= span) continue;
+                    while (woff[lo + 1] <= (uint32_t)r) ++lo;
                     const int64_t lw = (int64_t)dw[j] - v0;
                     if (lw <= lo) continue;                  // each edge once, from its smaller end
                     su[j] = lo;
@@ -259,7 +276,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
             const int xtot = __shfl_sync(0xffffffffu, xpre, 31);
             if (lane == 31 && xtot) xb = (long long)atomicAdd((unsigned long long *)nxl, (unsigned long long)xtot);
             xb = __shfl_sync(0xffffffffu, xb, 31) + (xpre - xc);
-            if (a0 >= a_end) continue;
+            if (r0 >= span) continue;
 #pragma unroll
             for (int j = 0; j < kItems; ++j) {
                 if (su[j] < 0) continue;
@@ -339,7 +356,11 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restri
     }
 }
 
-size_t cc_local_smem(int V, bool off64) { return (size_t)(V + 1) * (off64 ? 8 : 4) + 8 + (size_t)V * 2; }
+size_t cc_local_smem(int V, bool off64)
+{
+    (void)off64;
+    return (size_t)(V + 1) * 4 + 12 + (size_t)V * 2;
+}
 
 cudaError_t prepare_cc_local(int V)
 {
@@ -368,7 +389,7 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             const cudaError_t e = cudaMemsetAsync(nxl, 0, sizeof(long long), L.s);
             if (e != cudaSuccess) return e;
             k_cc_local<OffT><<<gl, kLocalThreads, cc_local_smem(cc_local, sizeof(OffT) == 8), L.s>>>(
-                off, adj, n, cc_local, d.uf, d.te_u, d.te_v, d.xl, d.xl_cap, nxl, d.err);
+                off, adj, n, nnz, cc_local, d.uf, d.te_u, d.te_v, d.xl, d.xl_cap, nxl, d.err, vec);
             L.mark("k_cc_local");
             int levels = 0;   // ranges r < r' < nr differ first at bit <= floor(log2(nr - 1))
             while ((1ll << levels) < nr) ++levels;
