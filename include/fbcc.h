@@ -121,6 +121,21 @@ fbcc_status fbcc_solve_host(const void *csr_offsets, int offsets_64, const int32
                             fbcc_stats *stats, fbcc_workspace *ws, void *stream);
 
 /*
+ * fbcc_solve_host without waiting: the copies in, the solve and the copies out
+ * are all enqueued on `stream` and the call returns at once. Every host buffer
+ * must be page-locked (cudaHostAlloc / cudaHostRegister) and stay untouched until
+ * the stream has been synchronised; stats (page-locked too, or NULL) is valid
+ * then. bcc_head receives all n entries (those at n_bcc and beyond are left
+ * unspecified), since n_bcc is not known when the copy is enqueued. Solves on two
+ * workspaces and two streams overlap: one's copies run during the other's kernels.
+ * Calls on one workspace must not overlap (its staging buffers are reused).
+ */
+fbcc_status fbcc_solve_host_async(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
+                                  int64_t n, int64_t m,
+                                  int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
+                                  fbcc_stats *stats, fbcc_workspace *ws, void *stream);
+
+/*
  * Many independent graphs in one call (the graphs are solved together as one
  * disjoint union; every kernel launch covers all of them).
  *   vtx_base   device, n_graphs+1 int64: graph g owns global vertices

@@ -435,17 +435,21 @@ fbcc_status fbcc_solve(const void *csr_offsets, int offsets_64, const int32_t *c
                         (cudaStream_t)stream);
 }
 
-fbcc_status fbcc_solve_host(const void *csr_offsets, int offsets_64, const int32_t *csr_adj, int64_t n, int64_t m,
-                            int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
-                            fbcc_stats *stats, fbcc_workspace *ws, void *stream)
+}  // extern "C"
+
+namespace {
+
+// The host entry points: inputs copied into the workspace's staging buffers,
+// the solve, the outputs copied back; `wait` synchronises and trims bcc_head to
+// n_bcc entries.
+fbcc_status solve_host(const void *csr_offsets, int offsets_64, const int32_t *csr_adj, int64_t n, int64_t m,
+                       int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge, fbcc_stats *stats,
+                       fbcc_workspace *ws, cudaStream_t s, bool wait)
 {
     fbcc_status st = check_args(csr_offsets, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, ws);
     if (st != FBCC_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = ws->d.n_max, Z = ws->d.nnz_max;
     if (!ws->stage) {
-        Dev tmp;
-        (void)tmp;
         ws->stage_bytes = size_t(N + 1) * 8 + size_t(Z) * 4 + size_t(Z) * 4 + size_t(N) * 4 + size_t(N) + size_t(Z) + 5 * 256;
         API_CK(cudaMalloc(&ws->stage, ws->stage_bytes), "cudaMalloc(staging)");
     }
@@ -461,13 +465,17 @@ fbcc_status fbcc_solve_host(const void *csr_offsets, int offsets_64, const int32
     if (n > 0) API_CK(cudaMemcpyAsync(d_off, csr_offsets, ob, cudaMemcpyHostToDevice, s), "H2D offsets");
     if (nnz > 0) API_CK(cudaMemcpyAsync(d_adj, csr_adj, nnz * 4, cudaMemcpyHostToDevice, s), "H2D adj");
     fbcc_stats hs;
-    st = solve_device(d_off, offsets_64, d_adj, n, m, d_eb, d_bh, d_ap, d_br, &hs, ws, s);
+    st = solve_device(d_off, offsets_64, d_adj, n, m, d_eb, d_bh, d_ap, d_br, wait ? &hs : stats, ws, s);
     if (st != FBCC_OK) return st;
     if (nnz > 0) {
         API_CK(cudaMemcpyAsync(edge_bcc, d_eb, nnz * 4, cudaMemcpyDeviceToHost, s), "D2H edge_bcc");
         API_CK(cudaMemcpyAsync(is_bridge, d_br, nnz, cudaMemcpyDeviceToHost, s), "D2H is_bridge");
     }
     if (n > 0) API_CK(cudaMemcpyAsync(is_ap, d_ap, n, cudaMemcpyDeviceToHost, s), "D2H is_ap");
+    if (!wait) {
+        if (n > 0) API_CK(cudaMemcpyAsync(bcc_head, d_bh, n * 4, cudaMemcpyDeviceToHost, s), "D2H bcc_head");
+        return FBCC_OK;
+    }
     API_CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (hs.n_bcc > 0)
         API_CK(cudaMemcpy(bcc_head, d_bh, hs.n_bcc * 4, cudaMemcpyDeviceToHost), "D2H bcc_head");
@@ -475,7 +483,24 @@ fbcc_status fbcc_solve_host(const void *csr_offsets, int offsets_64, const int32
     return FBCC_OK;
 }
 
-}  // extern "C"
+}  // namespace
+
+extern "C" fbcc_status fbcc_solve_host(const void *csr_offsets, int offsets_64, const int32_t *csr_adj, int64_t n,
+                                       int64_t m, int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap,
+                                       uint8_t *is_bridge, fbcc_stats *stats, fbcc_workspace *ws, void *stream)
+{
+    return solve_host(csr_offsets, offsets_64, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, stats, ws,
+                      (cudaStream_t)stream, true);
+}
+
+extern "C" fbcc_status fbcc_solve_host_async(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
+                                             int64_t n, int64_t m, int32_t *edge_bcc, int32_t *bcc_head,
+                                             uint8_t *is_ap, uint8_t *is_bridge, fbcc_stats *stats,
+                                             fbcc_workspace *ws, void *stream)
+{
+    return solve_host(csr_offsets, offsets_64, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, stats, ws,
+                      (cudaStream_t)stream, false);
+}
 
 // ---------------------------------------------------------------------------
 // Validation (warp per vertex)

@@ -22,7 +22,7 @@ FBCC_OK, FBCC_E_INVALID, FBCC_E_NOT_SIMPLE, FBCC_E_OOM, FBCC_E_CUDA, FBCC_E_ITER
 # Every entry point include/fbcc.h declares (checked by the tests).
 EXPORTS = (
     "fbcc_workspace_bytes", "fbcc_workspace_create", "fbcc_workspace_destroy", "fbcc_workspace_configure",
-    "fbcc_solve", "fbcc_solve_host", "fbcc_solve_noalloc", "fbcc_solve_batch", "fbcc_batch_workspace_bytes", "fbcc_validate",
+    "fbcc_solve", "fbcc_solve_host", "fbcc_solve_host_async", "fbcc_solve_noalloc", "fbcc_solve_batch", "fbcc_batch_workspace_bytes", "fbcc_validate",
     "fbcc_profile_count", "fbcc_profile_get", "fbcc_debug_read", "fbcc_status_string", "fbcc_last_cuda_error",
 )
 
@@ -75,7 +75,7 @@ def load(path: str = LIB_PATH):
         lib.fbcc_workspace_destroy.restype = None
         lib.fbcc_workspace_configure.argtypes = [P, ctypes.POINTER(fbcc_config)]
         lib.fbcc_workspace_configure.restype = INT
-        for name in ("fbcc_solve", "fbcc_solve_host"):
+        for name in ("fbcc_solve", "fbcc_solve_host", "fbcc_solve_host_async"):
             f = getattr(lib, name)
             f.argtypes = [P, INT, P, I64, I64, P, P, P, P, S, P, P]
             f.restype = INT
@@ -174,6 +174,19 @@ def fbcc_solve_host(offsets: np.ndarray, adj: np.ndarray, edge_bcc: np.ndarray, 
                                   is_bridge.ctypes.data, ctypes.byref(stats), ws, _stream_handle(stream)),
            "fbcc_solve_host")
     return stats
+
+
+def fbcc_solve_host_async(offsets: np.ndarray, adj: np.ndarray, edge_bcc: np.ndarray, bcc_head: np.ndarray,
+                          is_ap: np.ndarray, is_bridge: np.ndarray, ws: int, stream, stats=None) -> None:
+    """Enqueue copies in, solve and copies out on `stream` and return at once. All
+    arrays (and `stats`, an fbcc_stats in page-locked memory, or None) must be
+    page-locked and left alone until the stream is synchronised."""
+    n = offsets.size - 1
+    m = int(offsets[-1]) // 2
+    _check(load().fbcc_solve_host_async(offsets.ctypes.data, int(offsets.dtype == np.int64), adj.ctypes.data, n, m,
+                                        edge_bcc.ctypes.data, bcc_head.ctypes.data, is_ap.ctypes.data,
+                                        is_bridge.ctypes.data, stats, ws, _stream_handle(stream)),
+           "fbcc_solve_host_async")
 
 
 def fbcc_profile(ws: int) -> list:

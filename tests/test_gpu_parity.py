@@ -146,6 +146,35 @@ def test_host_entry_point(torch_cuda, oracle):
     s.close()
 
 
+def test_host_async_two_workspaces(torch_cuda, oracle):
+    """fbcc_solve_host_async on two workspaces and two streams, several rounds,
+    equals the oracle (bcc_head is compared over its first n_bcc entries)."""
+    from paper_2301_01356_gb300 import fbcc
+    torch = torch_cuda
+    graphs = [gg.uniform(6000, 15000, 3), gg.grid(90, 80, p=0.6, seed=2)]
+    exps = [oracle.solve(g.offsets, g.adj) for g in graphs]
+    nmax = max(g.n for g in graphs)
+    zmax = max(g.nnz for g in graphs)
+    wss = [fbcc.fbcc_workspace_create(nmax, zmax) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    ins = [(pin(g.offsets), pin(g.adj)) for g in graphs]
+    outs = [[pin(np.full(g.nnz, -1, np.int32)), pin(np.full(g.n, -1, np.int32)), pin(np.zeros(g.n, np.uint8)),
+             pin(np.zeros(g.nnz, np.uint8))] for g in graphs]
+    for rnd in range(3):
+        for i in range(2):
+            fbcc.fbcc_solve_host_async(*ins[i], *outs[i], wss[i], streams[i])
+        for st in streams:
+            st.synchronize()
+        for i, (g, e) in enumerate(zip(graphs, exps)):
+            eb, bh, ap, br = outs[i]
+            nb = e["n_bcc"]
+            assert np.array_equal(eb, e["edge_bcc"]) and np.array_equal(ap, e["is_ap"])
+            assert np.array_equal(br, e["is_bridge"]) and np.array_equal(bh[:nb], e["bcc_head"])
+    for w in wss:
+        fbcc.fbcc_workspace_destroy(w)
+
+
 def test_validate(torch_cuda):
     from paper_2301_01356_gb300 import fbcc
     s = fbcc.Solver(100, 1000)
