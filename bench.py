@@ -177,7 +177,8 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_chase2": 20 * nr,
         "k_expand2": 28 * nr,
         "k_ext_compact": n,
-        "k_ext_jump": 12 * (n // 64),
+        "k_ext_halve": 12 * (n // 64),
+        "k_ext_finish": 12 * (n // 64),
         "k_plain_label": 20 * n,
         "k_final_label": 28 * n,
         "k_lcc_sample": B * (n + 1) + 16 * n + 24 * n,

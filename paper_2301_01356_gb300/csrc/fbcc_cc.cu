@@ -461,16 +461,27 @@ __global__ void __launch_bounds__(kThreads) k_ext_compact(int64_t n, const uint8
     }
 }
 
-// One pointer-doubling round over the cross-tile positions (in place).
-__global__ void __launch_bounds__(kThreads) k_ext_jump(const long long *__restrict__ nq_p,
-                                                       const int32_t *__restrict__ qlist, int32_t *lp)
+// Cross-tile positions resolved to their plain roots in two passes, the way the
+// union-find is flattened: first a walk with path halving from every listed
+// position (every store writes an ancestor, so the pointer forest stays valid and
+// the chains shrink for every later walker), then a read-only walk that stores
+// each listed position's root (a halving store from another thread can then no
+// longer overwrite a root with a non-root).
+__global__ void __launch_bounds__(kThreads) k_ext_halve(const long long *__restrict__ nq_p,
+                                                        const int32_t *__restrict__ qlist, int32_t *lp)
+{
+    const int64_t nq = *nq_p;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nq; i += (int64_t)gridDim.x * kThreads)
+        (void)uf_find(lp, qlist[i]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_ext_finish(const long long *__restrict__ nq_p,
+                                                         const int32_t *__restrict__ qlist, int32_t *lp)
 {
     const int64_t nq = *nq_p;
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nq; i += (int64_t)gridDim.x * kThreads) {
         const int32_t q = qlist[i];
-        const int32_t t = ld_cg(lp + q);
-        const int32_t u = ld_cg(lp + t);
-        if (u != t) lp[q] = u;
+        lp[q] = uf_root(lp, q);
     }
 }
 
@@ -701,11 +712,10 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
     CK(cudaMemsetAsync(nq, 0, sizeof(long long), L.s));
     k_ext_compact<<<gv, kThreads, 0, L.s>>>(n, d.ext, d.qlist, nq);
     L.mark("k_ext_compact");
-    const int rounds = jump_rounds(ceil_div(n, kRmqTile));
-    for (int i = 0; i < rounds; ++i) {
-        k_ext_jump<<<gv, kThreads, 0, L.s>>>(nq, d.qlist, d.lp);
-        L.mark("k_ext_jump");
-    }
+    k_ext_halve<<<gv, kThreads, 0, L.s>>>(nq, d.qlist, d.lp);
+    L.mark("k_ext_halve");
+    k_ext_finish<<<gv, kThreads, 0, L.s>>>(nq, d.qlist, d.lp);
+    L.mark("k_ext_finish");
     k_plain_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.ord, d.cr, d.uf);
     L.mark("k_plain_label");
     if (nnz > 0 && lcc_sample > 0) {
