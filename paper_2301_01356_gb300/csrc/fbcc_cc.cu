@@ -176,14 +176,12 @@ __global__ void __launch_bounds__(kThreads) k_cc_pick_big(int32_t *uf, int64_t n
 // their geometry, such as grids or meshes, keep most edges inside a range); the
 // range's sets then enter the global union-find flattened.
 //
-// Edges between ranges (u < w) are gathered into a list on the way and hooked
-// level by level: an edge between ranges r and r' belongs to level
-// floor(log2(r xor r')), the level at which a binary merge tree over the ranges
-// first puts r and r' together. Hooking every boundary at once would let a
-// component that crosses R ranges hang its ranges' roots in a chain of length R
-// (each root hooked under its lower neighbour's while that one is hooked in
-// turn); in level order the chains stay within the number of levels. When the
-// list outgrows its space the global pass falls back to one full arc scan.
+// Edges between ranges (u < w) are gathered into a list on the way, and one
+// launch hooks them all. (Hooking every boundary at once can hang a component
+// that crosses R ranges in a chain of up to R roots; the finds walk such chains
+// through L1 and halve them, and measured faster than hooking the boundaries in
+// the level order of a merge tree, one launch per level.) When the list outgrows
+// its space the global pass falls back to one full arc scan.
 constexpr int kLocalThreads = 512;
 
 // Local union-find in shared memory with 16-bit parents (range-local ids < 2^15).
@@ -310,23 +308,20 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
     (void)err;
 }
 
-// Global hooks of the gathered edges of one level; when the list did not fit,
-// the level-0 launch hooks every edge between ranges from a full arc scan and
-// the other levels do nothing.
+// Global hooks of the gathered edges; when the list did not fit, every edge
+// between ranges is hooked from a full arc scan instead.
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restrict__ off,
                                                             const int32_t *__restrict__ adj, int64_t nnz,
                                                             const int32_t *__restrict__ tile_v, int64_t ntiles, int V,
                                                             const int2 *__restrict__ xl, int64_t xl_cap,
-                                                            const long long *__restrict__ nxl, int level, int32_t *uf,
+                                                            const long long *__restrict__ nxl, int32_t *uf,
                                                             int32_t *te_u, int32_t *te_v, int *err, bool vec)
 {
     const long long nx = *nxl;
     if (nx <= xl_cap) {
         for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nx; i += (int64_t)gridDim.x * kThreads) {
             const int2 e = xl[i];
-            const uint32_t x = (uint32_t)(e.x / V) ^ (uint32_t)(e.y / V);
-            if (x == 0 || 31 - __clz(x) != level) continue;
             const int32_t r = uf_unite(uf, e.x, e.y, err);
             if (r >= 0) {
                 te_u[r] = e.x;
@@ -335,7 +330,6 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restri
         }
         return;
     }
-    if (level != 0) return;
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
     const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -391,13 +385,9 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             k_cc_local<OffT><<<gl, kLocalThreads, cc_local_smem(cc_local, sizeof(OffT) == 8), L.s>>>(
                 off, adj, n, nnz, cc_local, d.uf, d.te_u, d.te_v, d.xl, d.xl_cap, nxl, d.err, vec);
             L.mark("k_cc_local");
-            int levels = 0;   // ranges r < r' < nr differ first at bit <= floor(log2(nr - 1))
-            while ((1ll << levels) < nr) ++levels;
-            for (int lv = 0; lv < levels; ++lv) {
-                k_cc_hook_cross<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, cc_local, d.xl,
-                                                               d.xl_cap, nxl, lv, d.uf, d.te_u, d.te_v, d.err, vec);
-                L.mark("k_cc_hook_cross");
-            }
+            k_cc_hook_cross<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, cc_local, d.xl,
+                                                           d.xl_cap, nxl, d.uf, d.te_u, d.te_v, d.err, vec);
+            L.mark("k_cc_hook_cross");
         } else if (cc_sample > 0) {
             int32_t *big = reinterpret_cast<int32_t *>(d.counters + 8);
             k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, d.err);
