@@ -150,7 +150,6 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_cc_init": B * (n + 1) + 8 * n,
         "k_cc_hook": B * (n + 1) + 4 * nnz + 2 * nnz + 8 * (n - n_cc),
         "k_uf_compress": 8 * n,
-        "k_scan_i32": 8 * n,
         "k_link": 12 * n + 4 * A,
         "k_succ_rulers": 16 * n + 13 * A + 4 * nr,
         "k_chase": 16 * A + 16 * nr,

@@ -280,24 +280,51 @@ __global__ void __launch_bounds__(kThreads) k_jump(const long long *__restrict__
     }
 }
 
-// Component size at its root: 1 for an isolated root, else tour length / 2 + 1.
+// Component size at its root (1 for an isolated root, else tour length / 2 + 1)
+// and the component's first preorder number. The components may take the
+// preorder range in any order (only the order inside a component matters), so
+// each CTA reserves one block of the range with one atomic and hands it out to its
+// roots by a block scan: no separate scan pass over all vertices.
 __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t *__restrict__ uf,
                                                         const int32_t *__restrict__ lhead,
                                                         const int2 *__restrict__ link, const int32_t *__restrict__ sd,
-                                                        const long long *nr_p, int32_t *csize, int *err)
+                                                        const long long *nr_p, int32_t *csize, int32_t *vbase,
+                                                        long long *next_base, int *err)
 {
+    __shared__ int32_t warp_tot[kThreads / 32];
+    __shared__ long long block_base;
     const int64_t nr = *nr_p;
-    GRID_STRIDE(v, n)
-    {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n_pad = (n + kThreads - 1) / kThreads * kThreads;   // whole CTAs take part
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
         int32_t c = 0;
-        if (uf[v] == v) {
+        if (v < n && uf[v] == v) {
             c = 1;
             if (lhead[v] >= 0) {
                 const int32_t id = link[lhead[v]].y;
                 if (in_range(id, nr, err)) c = sd[id] / 2 + 1;
             }
         }
-        csize[v] = c;
+        int32_t inc = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) warp_tot[wid] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int w = 0; w < kThreads / 32; ++w) t += warp_tot[w];
+            block_base = t ? (long long)atomicAdd((unsigned long long *)next_base, (unsigned long long)t) : 0;
+        }
+        __syncthreads();
+        long long b = block_base + inc - c;
+        for (int w = 0; w < wid; ++w) b += warp_tot[w];
+        __syncthreads();   // warp_tot / block_base are rewritten next iteration
+        if (v < n) {
+            csize[v] = c;
+            if (c) vbase[v] = (int32_t)b;
+        }
     }
 }
 
@@ -463,10 +490,11 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     k_expand2<<<gr, kThreads, 0, L.s>>>(nr, d.l2, d.rlen, d.owner2, d.offs2, d.rval[cur], d.sd1);
     L.mark("k_expand2");
     const int32_t *sd = d.sd1;
-    k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.lhead, d.link, sd, nr, d.csize, d.err);
+    long long *next_base = d.counters + 6;
+    CK(cudaMemsetAsync(next_base, 0, sizeof(long long), L.s));
+    k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.lhead, d.link, sd, nr, d.csize, d.vbase, next_base, d.err);
     L.mark("k_comp_size");
     CK(cudaGetLastError());
-    CK(launch_scan_i32(d, d.csize, d.vbase, n, L));
     k_place_records<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.csize, d.vbase, d.link, sd, d.rec, d.err);
     L.mark("k_place_records");
     k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.fp, d.lastp, d.ord, d.porig, d.w1,

@@ -510,7 +510,6 @@ cudaError_t launch_validate(const Dev &d, const OffT *off, const int32_t *adj, i
 
 // Generic exclusive scan over int32 counts: out[i] = sum of in[0..i), out[len] = total
 // (out has len+1 entries; in may alias out when in_place).
-cudaError_t launch_scan_i32(const Dev &d, const int32_t *in, int32_t *out, int64_t len, const Launch &L);
 // out[i] = set bits in words[0..i), i in [0, len].
 cudaError_t launch_scan_popc(const Dev &d, const uint32_t *words, int32_t *out, int64_t len, const Launch &L);
 
