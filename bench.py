@@ -154,9 +154,8 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_succ_rulers": 16 * n + 13 * A + 4 * nr,
         "k_chase": 16 * A + 16 * nr,
         "k_jump": 24 * nr,
-        "k_comp_size": 16 * n,
         "k_place_records": 30 * A,
-        "k_root_tags": 12 * n_cc,
+        "k_comp_size": 16 * n + 40 * n_cc,
         "k_preorder": 16 * n + 28 * n,
         "k_first_of": 12 * n,
         "k_w12": B * (n + 1) + 4 * nnz + 4 * nnz + nnz // 8 + 8 * n,

@@ -284,12 +284,18 @@ __global__ void __launch_bounds__(kThreads) k_jump(const long long *__restrict__
 // and the component's first preorder number. The components may take the
 // preorder range in any order (only the order inside a component matters), so
 // each CTA reserves one block of the range with one atomic and hands it out to its
-// roots by a block scan: no separate scan pass over all vertices.
+// roots by a block scan: no separate scan pass over all vertices. The root also
+// writes its own tags (preorder number b, last b + size - 1, no parent) and the
+// two padding records that end its tour's slot in the record array (the arcs fill
+// the slot's first 2 (size - 1) positions): a counting one, so that the count
+// restarts right at the next component's base, and a neutral one.
 __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t *__restrict__ uf,
                                                         const int32_t *__restrict__ lhead,
                                                         const int2 *__restrict__ link, const int32_t *__restrict__ sd,
                                                         const long long *nr_p, int32_t *csize, int32_t *vbase,
-                                                        long long *next_base, int *err)
+                                                        long long *next_base, int2 *rec, int2 *fp, int32_t *lastp,
+                                                        int32_t *ord, int32_t *porig, int32_t *w1, int32_t *w2,
+                                                        int *err)
 {
     __shared__ int32_t warp_tot[kThreads / 32];
     __shared__ long long block_base;
@@ -323,7 +329,18 @@ __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t
         __syncthreads();   // warp_tot / block_base are rewritten next iteration
         if (v < n) {
             csize[v] = c;
-            if (c) vbase[v] = (int32_t)b;
+            if (c) {
+                const int32_t bb = (int32_t)b;
+                vbase[v] = bb;
+                rec[2 * b + 2 * c - 2] = make_int2(-2, 0);
+                rec[2 * b + 2 * c - 1] = make_int2(-3, 0);
+                fp[v] = make_int2(bb, -1);
+                lastp[bb] = bb + c - 1;
+                ord[bb] = (int32_t)v;
+                porig[bb] = -1;
+                w1[bb] = bb;
+                w2[bb] = bb;
+            }
         }
     }
 }
@@ -362,28 +379,6 @@ __global__ void __launch_bounds__(kThreads) k_place_records(int64_t n, const int
             rec[p1] = make_int2(u, v);
             rec[p0] = make_int2(-1, p0 - p1);
         }
-    }
-}
-
-// Per component root: padding slots and the root's own tags.
-__global__ void __launch_bounds__(kThreads) k_root_tags(int64_t n, const int32_t *__restrict__ uf,
-                                                        const int32_t *__restrict__ csize,
-                                                        const int32_t *__restrict__ vbase, int2 *rec, int2 *fp,
-                                                        int32_t *lastp, int32_t *ord, int32_t *porig, int32_t *w1,
-                                                        int32_t *w2)
-{
-    GRID_STRIDE(r, n)
-    {
-        if (uf[r] != r) continue;
-        int32_t b = vbase[r], sz = csize[r];
-        rec[2 * b + 2 * sz - 2] = make_int2(-2, 0);   // counts: the prefix restarts at the next base
-        rec[2 * b + 2 * sz - 1] = make_int2(-3, 0);
-        fp[r] = make_int2(b, -1);
-        lastp[b] = b + sz - 1;
-        ord[b] = (int32_t)r;
-        porig[b] = -1;
-        w1[b] = b;
-        w2[b] = b;
     }
 }
 
@@ -492,14 +487,12 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     const int32_t *sd = d.sd1;
     long long *next_base = d.counters + 6;
     CK(cudaMemsetAsync(next_base, 0, sizeof(long long), L.s));
-    k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.lhead, d.link, sd, nr, d.csize, d.vbase, next_base, d.err);
+    k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.lhead, d.link, sd, nr, d.csize, d.vbase, next_base, d.rec,
+                                          d.fp, d.lastp, d.ord, d.porig, d.w1, d.w2, d.err);
     L.mark("k_comp_size");
     CK(cudaGetLastError());
     k_place_records<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.csize, d.vbase, d.link, sd, d.rec, d.err);
     L.mark("k_place_records");
-    k_root_tags<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.csize, d.vbase, d.rec, d.fp, d.lastp, d.ord, d.porig, d.w1,
-                                          d.w2);
-    L.mark("k_root_tags");
     CK(cudaGetLastError());
     const int64_t ntiles = ceil_div(2 * n, kTile);
     CK(cudaMemsetAsync(d.counters, 0, sizeof(long long), L.s));
