@@ -32,6 +32,10 @@ namespace fbcc {
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
 
 // Articulation points, component count, and the keys that need no list scan.
+// Each thread takes kVPer vertices per step and issues each round of their loads
+// together (the pass is bound by dependent-load latency, not bandwidth).
+constexpr int kVPer = 4;
+
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__restrict__ off,
                                                       const int2 *__restrict__ fp, const int32_t *__restrict__ lab,
@@ -41,26 +45,57 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
                                                       fbcc_stats *stats, int *err)
 {
     long long nap = 0, ncc = 0;
-    GRID_STRIDE(v, n)
-    {
-        const int2 fv = fp[v];
-        const bool root = fv.y < 0;
-        const int32_t h = nh[v];
-        const uint8_t ap = root ? h >= 2 : h >= 1;
-        is_ap[v] = ap;
-        nap += ap;
-        ncc += root;
-        if (root || lab[v] != v) continue;
-        const int32_t hd = fv.y;   // a label's head is its parent
-        if (!in_range(hd, n, err)) continue;
-        const int32_t sm = smin[v];
-        const int32_t u0 = hd < sm ? hd : sm;
-        const int32_t in_bccs = (fp[u0].y >= 0) + nh[u0];
-        if (in_bccs == 1) {
-            key[v] = (unsigned long long)off[u0];
-        } else {
-            key[v] = ~0ull;
-            scanv[u0] = 1;
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
+        int2 f[kVPer];
+        int32_t h[kVPer], l[kVPer];
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k * T;
+            f[k] = make_int2(0, -1);
+            h[k] = 0;
+            l[k] = -1;
+            if (v < n) { f[k] = fp[v]; h[k] = nh[v]; l[k] = lab[v]; }
+        }
+        uint32_t lbl = 0;
+        int32_t sm[kVPer];
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k * T;
+            sm[k] = 0;
+            if (v >= n) continue;
+            const bool root = f[k].y < 0;
+            const uint8_t ap = root ? h[k] >= 2 : h[k] >= 1;
+            is_ap[v] = ap;
+            nap += ap;
+            ncc += root;
+            // a label's head is its parent
+            if (!root && l[k] == v && in_range(f[k].y, n, err)) {
+                lbl |= 1u << k;
+                sm[k] = smin[v];
+            }
+        }
+        int32_t u0[kVPer], hu[kVPer];
+        bool pu[kVPer];
+        OffT ou[kVPer];
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            if (!((lbl >> k) & 1u)) continue;
+            u0[k] = f[k].y < sm[k] ? f[k].y : sm[k];
+            pu[k] = fp[u0[k]].y >= 0;
+            hu[k] = nh[u0[k]];
+            ou[k] = off[u0[k]];
+        }
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            if (!((lbl >> k) & 1u)) continue;
+            const int64_t v = v0 + k * T;
+            if ((int)pu[k] + hu[k] == 1) {   // u0 lies in this BCC only: its first arc is the key
+                key[v] = (unsigned long long)ou[k];
+            } else {
+                key[v] = ~0ull;
+                scanv[u0[k]] = 1;
+            }
         }
     }
     block_count((long long *)&stats->n_ap, nap);
