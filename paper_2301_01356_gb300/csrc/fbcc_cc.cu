@@ -486,9 +486,31 @@ __device__ __forceinline__ int32_t plain_root(const int32_t *lp, int64_t p)
 __global__ void __launch_bounds__(kThreads) k_plain_label(int64_t n, const int32_t *__restrict__ lp,
                                                           const int32_t *__restrict__ ord, int2 *cr, int32_t *uf)
 {
-    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads) {
-        cr[ord[p]] = make_int2((int32_t)p, plain_root(lp, p));
-        uf[p] = (int32_t)p;
+    // kPer positions per thread and step, each round of their loads issued together
+    constexpr int kPer = 4;
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    for (int64_t p0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; p0 < n; p0 += T * kPer) {
+        int32_t o[kPer], t[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t p = p0 + k * T;
+            if (p >= n) continue;
+            o[k] = ord[p];
+            t[k] = lp[p];
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t p = p0 + k * T;
+            if (p >= n) continue;
+            if (t[k] < (p & ~(int64_t)(kRmqTile - 1))) t[k] = lp[t[k]];   // plain_root
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t p = p0 + k * T;
+            if (p >= n) continue;
+            cr[o[k]] = make_int2((int32_t)p, t[k]);
+            uf[p] = (int32_t)p;
+        }
     }
 }
 

@@ -214,16 +214,30 @@ __global__ void __launch_bounds__(kThreads) k_fo(int64_t n, const int2 *__restri
                                                  const uint8_t *__restrict__ vbits, int32_t *word, fbcc_stats *stats)
 {
     long long nb = 0;
-    GRID_STRIDE(v, n)
-    {
-        int32_t w = 0;
-        const int2 f = fp[v];
-        if (f.y >= 0) {
-            const uint32_t br = vbits[v] & 1u;
-            w = (int32_t)((uint32_t)rank[lab[v]] | (br << 31));
-            nb += br;
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
+        int32_t y[kVPer], l[kVPer];
+        uint32_t br[kVPer];
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k * T;
+            y[k] = -1;
+            if (v >= n) continue;
+            y[k] = fp[v].y;
+            l[k] = lab[v];
+            br[k] = vbits[v] & 1u;
         }
-        word[v] = w;
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k * T;
+            if (v >= n) continue;
+            int32_t w = 0;
+            if (y[k] >= 0) {
+                w = (int32_t)((uint32_t)rank[l[k]] | (br[k] << 31));
+                nb += br[k];
+            }
+            word[v] = w;
+        }
     }
     block_count((long long *)&stats->n_bridge, nb);
 }
