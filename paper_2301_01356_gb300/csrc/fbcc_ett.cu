@@ -46,12 +46,30 @@ __device__ __forceinline__ int32_t arc_dst(const int32_t *te_u, const int32_t *t
 __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__restrict__ te_u,
                                                    const int32_t *__restrict__ te_v, int32_t *lhead, int32_t *nxt)
 {
-    GRID_STRIDE(h, n)
-    {
-        const int32_t u = te_u[h];
-        if (u < 0) continue;
-        nxt[2 * h] = atomicExch(lhead + u, (int32_t)(2 * h));
-        nxt[2 * h + 1] = atomicExch(lhead + te_v[h], (int32_t)(2 * h + 1));
+    // four edges per thread and step: their eight exchanges in flight together
+    constexpr int kPer = 4;
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    for (int64_t h0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; h0 < n; h0 += T * kPer) {
+        int32_t u[kPer], v[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t h = h0 + k * T;
+            u[k] = h < n ? te_u[h] : -1;
+            v[k] = u[k] >= 0 ? te_v[h] : -1;
+        }
+        int2 o[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (u[k] < 0) continue;
+            const int64_t h = h0 + k * T;
+            o[k].x = atomicExch(lhead + u[k], (int32_t)(2 * h));
+            o[k].y = atomicExch(lhead + v[k], (int32_t)(2 * h + 1));
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (u[k] < 0) continue;
+            *reinterpret_cast<int2 *>(nxt + 2 * (h0 + k * T)) = o[k];
+        }
     }
 }
 
