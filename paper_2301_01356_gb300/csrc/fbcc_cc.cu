@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
         if (!bits) continue;
         int32_t d[kItems];
         arc_tile_targets(adj, at.a0, at.cnt, vec, d);
-        int32_t cur = -1, lastu = 0;
+        int32_t cur = -1, lastu = 0, ru = -1;
         int2 cs = make_int2(0, 0);
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
@@ -546,9 +546,15 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
                 cur = at.src[j];
                 cs = __ldg(cr + cur);
                 lastu = __ldg(lastp + cs.x);
+                ru = -1;
             }
             const int2 cd = __ldg(cr + d[j]);
-            if (cd.y != cs.y && cd.x > lastu) uf_unite(uf, cs.y, cd.y, err);
+            if (cd.y == cs.y || cd.x <= lastu) continue;
+            if (ru < 0) ru = uf_find(uf, cs.y);
+            const int32_t rv = uf_find(uf, cd.y);
+            if (rv == ru) continue;
+            uf_unite(uf, ru, rv, err);
+            ru = -1;
         }
     }
 }

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, co
 
 // edge_bcc / is_bridge for every arc.
 template <typename OffT>
-__global__ void __launch_bounds__(kThreads) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
+__global__ void __launch_bounds__(kThreads, 8) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                        int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
                                                        const int32_t *__restrict__ word,
                                                        const uint8_t *__restrict__ dirb, int32_t *edge_bcc,
