@@ -417,11 +417,13 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
 // edges, by preorder number.
 //  1. plain components: the low/high kernel left lp[p] = parent position for a
 //     plain edge, flattened inside each 1024-position tile; positions referenced
-//     from another tile (ext) are compacted and resolved by pointer doubling;
+//     from another tile (ext) are compacted and resolved by a halving walk and a
+//     read-only flatten;
 //  2. cross edges: union-find over the plain components' roots (hook the larger
-//     position under the smaller); tree arcs are skipped by their tree bit, and a
-//     non-tree arc u->w with first[w] > first[u] is a back edge iff first[w] <=
-//     last[u] (u an ancestor of w; Algorithm 1, Back), a cross edge otherwise;
+//     position under the smaller); an arc u->w with first[w] > first[u] (its
+//     direction bit) that is not a tree arc to a child is a back edge iff
+//     first[w] <= last[u] (u an ancestor of w; Algorithm 1, Back), a cross edge
+//     otherwise, and a tree arc to a child always passes as a back edge there;
 //     arcs with first[w] < first[u] are left to the reverse arc;
 //  3. every position's final root, the smallest vertex id of each component and
 //     the label of every vertex: the id of its component's top vertex.

@@ -11,17 +11,20 @@
 //     cyclically (the paper's linking of u_i->v to v->u_{i+1}); each circuit is cut
 //     before the root's first arc, which becomes the tour's head;
 //  3. list ranking: rulers (every tour head plus one arc in `stride`) each walk
-//     their successors up to the next ruler, recording owner and offset; the
-//     short ruler lists are ranked by pointer jumping; every arc's tour position
-//     follows from its ruler's suffix length (the paper samples sqrt(n) nodes and
-//     chases pointers between them; the GPU takes many more rulers so that every
-//     thread has a short walk);
-//  4. preorder: an arc is a down arc iff it precedes its twin in the tour; a prefix
-//     count of down arcs over tour positions numbers the vertices in preorder: the
-//     down arc into v gives first[v], the up arc leaving v gives last[v].
+//     their successors up to the next ruler, recording owner and offset in the
+//     link entries they pass; the ruler lists are sampled again and the top
+//     level is ranked by pointer jumping; every arc's tour position follows from
+//     its ruler's suffix length (the paper samples sqrt(n) nodes and chases
+//     pointers between them; the GPU takes many more rulers so that every thread
+//     has a short walk);
+//  4. preorder: an arc is a down arc iff it precedes its reverse in the tour; a
+//     prefix count of down arcs over tour positions numbers the vertices in
+//     preorder: the down arc into v gives first[v], the up arc leaving v gives
+//     last[v].
 // Tours are laid out at positions [2*base, 2*base + 2*size) of their component
-// (base = preorder number of the root); the last two slots are padding, one of
-// which counts 1 so that the prefix count restarts at each component's base.
+// (base = preorder number of the root; components take their ranges in any
+// order); the last two slots are padding, one of which counts 1 so that the
+// prefix count restarts at each component's base.
 #include "fbcc_internal.cuh"
 
 namespace fbcc {
