@@ -71,3 +71,16 @@ def test_reference_arm_line():
 def test_rejects_short_warmup():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", "1"], capture_output=True)
     assert r.returncode != 0
+
+
+def test_cpu_baseline_sample_is_bounded():
+    """The oracle baseline runs on the full graph where that takes seconds, and on
+    the same recipe at a smaller scale for the R-MAT rows (minutes at full size)."""
+    import bench
+    from paper_2301_01356_gb300 import graphgen as gg
+    g = gg.workload_uniform_64k()
+    same, desc = bench.cpu_sample("uniform64k", g)
+    assert same is g and "full" in desc
+    small, desc = bench.cpu_sample("rmat24", None)
+    assert small.n == 1 << bench.CPU_SAMPLE_SCALE and small.m > 0
+    assert f"scale {bench.CPU_SAMPLE_SCALE}" in desc
