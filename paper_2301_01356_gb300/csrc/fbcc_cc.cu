@@ -431,14 +431,24 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
 __global__ void __launch_bounds__(kThreads) k_ext_compact(int64_t n, const uint8_t *__restrict__ ext, int32_t *qlist,
                                                           long long *nq)
 {
+    // kTile positions per CTA step (kItems per thread, striped), one atomic per step
     __shared__ int32_t warp_cnt[kThreads / 32];
     __shared__ long long block_base;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t n_pad = (n + kThreads - 1) / kThreads * kThreads;
-    for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * kThreads) {
-        const bool on = p < n && ext[p];
-        const unsigned mask = __ballot_sync(0xffffffffu, on);
-        if (lane == 0) warp_cnt[wid] = __popc(mask);
+    for (int64_t p0 = blockIdx.x * (int64_t)kTile; p0 < n; p0 += (int64_t)gridDim.x * kTile) {
+        uint32_t on = 0;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int64_t p = p0 + k * kThreads + threadIdx.x;
+            if (p < n && ext[p]) on |= 1u << k;
+        }
+        const int mine = __popc(on);
+        int inc = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) warp_cnt[wid] = inc;
         __syncthreads();
         if (threadIdx.x == 0) {
             int32_t t = 0;
@@ -446,10 +456,12 @@ __global__ void __launch_bounds__(kThreads) k_ext_compact(int64_t n, const uint8
             block_base = t ? (long long)atomicAdd((unsigned long long *)nq, (unsigned long long)t) : 0;
         }
         __syncthreads();
-        int32_t before = 0;
-        for (int w = 0; w < wid; ++w) before += warp_cnt[w];
-        if (on) qlist[block_base + before + __popc(mask & ((1u << lane) - 1u))] = (int32_t)p;
+        long long q = block_base + inc - mine;
+        for (int w = 0; w < wid; ++w) q += warp_cnt[w];
         __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kItems; ++k)
+            if ((on >> k) & 1u) qlist[q++] = (int32_t)(p0 + k * kThreads + threadIdx.x);
     }
 }
 
@@ -730,7 +742,7 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
     const int gv = grid_for(L, ceil_div(n, kThreads));
     long long *nq = d.counters + 2;
     CK(cudaMemsetAsync(nq, 0, sizeof(long long), L.s));
-    k_ext_compact<<<gv, kThreads, 0, L.s>>>(n, d.ext, d.qlist, nq);
+    k_ext_compact<<<grid_for(L, ceil_div(n, kTile)), kThreads, 0, L.s>>>(n, d.ext, d.qlist, nq);
     L.mark("k_ext_compact");
     k_ext_halve<<<gv, kThreads, 0, L.s>>>(nq, d.qlist, d.lp);
     L.mark("k_ext_halve");
