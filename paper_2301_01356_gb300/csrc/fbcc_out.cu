@@ -160,10 +160,22 @@ __global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const int2 *__
                                                        const unsigned long long *__restrict__ key, uint32_t *key_bits,
                                                        int64_t nnz, int *err)
 {
-    GRID_STRIDE(v, n)
-    {
-        if (fp[v].y < 0 || lab[v] != v) continue;
-        if (in_range((int64_t)key[v], nnz, err)) set_bit(key_bits, (int64_t)key[v]);
+    // kVPer vertices per thread and step, each round of their loads issued together
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
+        uint32_t lbl = 0;
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k * T;
+            if (v < n && fp[v].y >= 0 && lab[v] == v) lbl |= 1u << k;
+        }
+        unsigned long long ks[kVPer];
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k)
+            if ((lbl >> k) & 1u) ks[k] = key[v0 + k * T];
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k)
+            if (((lbl >> k) & 1u) && in_range((int64_t)ks[k], nnz, err)) set_bit(key_bits, (int64_t)ks[k]);
     }
 }
 
