@@ -74,7 +74,9 @@ typedef struct {
     int32_t profile;       /* 1 = record a CUDA event after every kernel (no graph); see fbcc_profile_get */
     int32_t chase_chains;  /* list ranking: walks a thread advances together (1, 2 or 4) */
     int32_t cc_local;      /* First-CC: unite inside ranges of this many consecutive vertex ids in
-                              shared memory first (power of 2, 1024..16384; 0 = off) */
+                              shared memory first (power of 2, 1024..16384; 0 = off); a range
+                              whose lists hold 2^31 arcs or more makes the solve report
+                              FBCC_E_INVALID in device_status */
     int32_t lcc_sample;    /* Last-CC: cross edges per vertex united before the full pass (0 = off) */
 } fbcc_config;
 
