@@ -286,6 +286,12 @@ def tuned_config(args) -> dict:
 # oracle run on the full scale-24 graph takes minutes).
 CPU_SAMPLE_SCALE = 19
 
+# Solves in flight in the pipelined end-to-end measurement (one workspace and one
+# stream each). With two, a workspace's next input copy waits for its own output
+# copy and the kernels idle meanwhile; three keep them busy (grid4096: 5.66 ms per
+# step with two, 4.47 ms with three; rmat24: 24.8 and 18.3 ms).
+E2E_STREAMS = 3
+
 
 def cpu_sample(workload: str, g):
     if workload in ("rmat22", "rmat24"):
@@ -402,31 +408,36 @@ def run_gpu(args, world, rank, local):
     e2e_sync_max = max_over_ranks(sum(e2e_ts), world)
     d2h_sync = h_eb.nbytes + h_br.nbytes + h_ap.nbytes + 4 * hs.n_bcc + ctypes.sizeof(fbcc.fbcc_stats)
 
-    # the same, pipelined: two workspaces on two streams, each step copying its
-    # inputs in and its outputs out, so one step's copies run during the other's
-    # kernels (fbcc_solve_host_async)
-    ws2 = fbcc.fbcc_workspace_create(n, nnz)
-    fbcc.fbcc_workspace_configure(ws2, **cfg)
+    # the same, pipelined: E2E_STREAMS workspaces on as many streams, each step
+    # copying its inputs in and its outputs out, so one step's copies run during
+    # the others' kernels and the kernels of different steps fill each other's
+    # gaps (fbcc_solve_host_async)
+    extra = [fbcc.fbcc_workspace_create(n, nnz) for _ in range(E2E_STREAMS - 1)]
+    for w in extra:
+        fbcc.fbcc_workspace_configure(w, **cfg)
     outs = [(h_eb, h_bh, h_ap, h_br)] + [tuple(torch.empty(k, dtype=dt).pin_memory().numpy()
                                                for k, dt in ((nnz, torch.int32), (n, torch.int32),
-                                                             (n, torch.uint8), (nnz, torch.uint8)))]
-    wss = [solver.ws, ws2]
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    for i in range(4):
-        fbcc.fbcc_solve_host_async(h_off, h_adj, *outs[i % 2], wss[i % 2], streams[i % 2])
+                                                             (n, torch.uint8), (nnz, torch.uint8)))
+                                         for _ in extra]
+    wss = [solver.ws] + extra
+    streams = [torch.cuda.Stream() for _ in wss]
+    S = len(wss)
+    for i in range(2 * S):
+        fbcc.fbcc_solve_host_async(h_off, h_adj, *outs[i % S], wss[i % S], streams[i % S])
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for i in range(args.steps):
         # a workspace's previous step is done with its buffers before it is reused:
         # its stream orders them
-        fbcc.fbcc_solve_host_async(h_off, h_adj, *outs[i % 2], wss[i % 2], streams[i % 2])
+        fbcc.fbcc_solve_host_async(h_off, h_adj, *outs[i % S], wss[i % S], streams[i % S])
     for q in streams:
         q.synchronize()
     e2e_max = max_over_ranks(time.perf_counter() - t0, world)
-    same = all(np.array_equal(outs[0][j], outs[1][j]) for j in (0, 2, 3)) and \
-        np.array_equal(outs[0][1][:hs.n_bcc], outs[1][1][:hs.n_bcc])
-    fbcc.fbcc_workspace_destroy(ws2)
+    same = all(all(np.array_equal(outs[0][j], o[j]) for j in (0, 2, 3)) and
+               np.array_equal(outs[0][1][:hs.n_bcc], o[1][:hs.n_bcc]) for o in outs[1:])
+    for w in extra:
+        fbcc.fbcc_workspace_destroy(w)
     if not same:
         raise SystemExit("pipelined host solves disagree")
     h2d = h_off.nbytes + h_adj.nbytes
@@ -460,8 +471,8 @@ def run_gpu(args, world, rank, local):
                    "p50_ms": p50, "p99_ms": p99},
         "e2e": {"value": whole_job_rate(m, args.steps, world, e2e_max), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max * 1e3 / args.steps,
-                "api": "fbcc_solve_host_async, pinned host buffers, two workspaces on two streams (a step's "
-                       "copies overlap the other workspace's kernels)",
+                "api": f"fbcc_solve_host_async, pinned host buffers, {E2E_STREAMS} workspaces on as many "
+                       "streams (a step's copies overlap the other workspaces' kernels)",
                 "sync": {"value": whole_job_rate(m, args.steps, world, e2e_sync_max), "unit": UNIT,
                          "ms_per_step": e2e_sync_max * 1e3 / args.steps, "d2h_bytes_per_step": d2h_sync,
                          "api": "fbcc_solve_host, one call at a time"}},
@@ -501,6 +512,18 @@ def run_single(args, rank, local):
     if rank == 0:
         print(json.dumps({"workload": args.workload, "n": g.n, "m": g.m, "tuning": tuned_config(args),
                           "launches": len(rows), "kernels": [name for name, _ in rows]}), flush=True)
+
+
+def bucket_summary(runner) -> list:
+    """Per size bucket: the vertex range of its graphs, their count, the number of
+    chunks it was split into and its tuned configuration."""
+    out = []
+    for i in sorted({b.bucket for b in runner.buckets}):
+        bs = [b for b in runner.buckets if b.bucket == i]
+        sz = np.concatenate([b.sub.sizes() for b in bs])
+        out.append({"n_range": [int(sz.min()), int(sz.max())], "graphs": int(sz.size), "chunks": len(bs),
+                    "config": bs[0].cfg})
+    return out
 
 
 def run_batch(args, world, rank, local):
@@ -543,13 +566,19 @@ def run_batch(args, world, rank, local):
     B.per_graph_loop(bt, graphs=range(min(64, bt.G)))
     loop_s = B.per_graph_loop(bt)
 
-    # per-kernel times on the largest bucket (profiled solve) for the roofline
+    # one profiled solve of every chunk: its launch count, and the per-kernel times
+    # of the largest chunk for the roofline
     big = max(runner.buckets, key=lambda b: b.sub.n_total)
-    fbcc.fbcc_workspace_configure(big.ws, profile=1, **big.cfg)
-    big.launch()
-    rows = fbcc.fbcc_profile(big.ws)
-    torch.cuda.synchronize()
-    fbcc.fbcc_workspace_configure(big.ws, **big.cfg)
+    launches = 0
+    for b in runner.buckets:
+        fbcc.fbcc_workspace_configure(b.ws, profile=1, **b.cfg)
+        b.launch()
+        r = fbcc.fbcc_profile(b.ws)
+        torch.cuda.synchronize()
+        fbcc.fbcc_workspace_configure(b.ws, **b.cfg)
+        launches += len(r)
+        if b is big:
+            rows = r
     prof = {}
     for name, ms in rows:
         t, c = prof.get(name, (0.0, 0))
@@ -563,7 +592,7 @@ def run_batch(args, world, rank, local):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
                 "algorithmic_bytes_per_launch": ab, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "ms_per_launch": dom_ms, "bucket_vertices": big.sub.n_total}
+                "ms_per_launch": dom_ms, "chunk_vertices": big.sub.n_total}
 
     # end to end: packed inputs from pinned host memory, outputs back to pinned host memory
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -576,8 +605,8 @@ def run_batch(args, world, rank, local):
     for _ in range(max(2, args.steps // 4)):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        # each bucket copies in, solves and copies out on its own stream, so one
-        # bucket's copies overlap the others' kernels
+        # each chunk copies in, solves and copies out on its own stream, so one
+        # chunk's copies overlap the others' kernels
         cur = torch.cuda.current_stream()
         for b, (lo, la), (eb, br, ap, sb) in zip(runner.buckets, h_in, h_out):
             b.stream.wait_stream(cur)
@@ -628,16 +657,15 @@ def run_batch(args, world, rank, local):
                                "thinned grid (p 0.55-0.75) / cycle chain families round-robin, seed 4",
                    "graphs": bt.G, "n_total": bt.n_total, "m_total": m_total, "parallelism": f"replicas{world}",
                    "l2": "inputs (packed CSR, %.1f GB) larger than L2" % ((bt.n_total + bt.nnz_total) * 4 / 1e9),
-                   "buckets": [{"n_range": [int(b.sub.sizes().min()), int(b.sub.sizes().max())],
-                                "graphs": b.sub.G, "config": b.cfg} for b in runner.buckets],
+                   "buckets": bucket_summary(runner),
                    "p50_ms": ms_sorted[len(ms_sorted) // 2], "p99_ms": ms_sorted[-1], "generate_s": round(gen_s, 1)},
         "graphs_per_s": whole_job_rate(bt.G, args.steps, world, max_s),
         "per_graph_loop": {"graphs_per_s": bt.G / loop_s, "value": m_total / loop_s, "unit": UNIT,
                            "seconds": loop_s, "api": "fbcc_solve per graph, direct launches"},
         "e2e": {"value": m_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_s * 1e3, "api": "per bucket on its own stream: pinned host copies in, "
-                                                   "fbcc_solve_batch, copies out (buckets overlap)"},
-        "gpu_launches": len(rows) * len(runner.buckets) * args.steps,
+                "ms_per_step": e2e_s * 1e3, "api": "per chunk on its own stream: pinned host copies in, "
+                                                   "fbcc_solve_batch, copies out (chunks overlap)"},
+        "gpu_launches": launches * args.steps,
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "parity_vs_oracle": parity,
     }
     if rank == 0:

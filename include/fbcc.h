@@ -128,8 +128,10 @@ fbcc_status fbcc_solve_host(const void *csr_offsets, int offsets_64, const int32
  * must be page-locked (cudaHostAlloc / cudaHostRegister) and stay untouched until
  * the stream has been synchronised; stats (page-locked too, or NULL) is valid
  * then. bcc_head receives all n entries (those at n_bcc and beyond are left
- * unspecified), since n_bcc is not known when the copy is enqueued. Solves on two
- * workspaces and two streams overlap: one's copies run during the other's kernels.
+ * unspecified), since n_bcc is not known when the copy is enqueued. Solves on
+ * several workspaces, each with its own stream, overlap: one's copies run during
+ * the others' kernels. Three in flight keep the GPU busy; with two, a workspace's
+ * next input copy waits for its own output copy and the kernels idle meanwhile.
  * Calls on one workspace must not overlap (its staging buffers are reused).
  */
 fbcc_status fbcc_solve_host_async(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,

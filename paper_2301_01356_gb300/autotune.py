@@ -52,14 +52,17 @@ def tune_batch(batch, reps: int = 8, candidates=CANDIDATES, buckets=B.BUCKETS, f
         if idx.size == 0:
             continue
         runner = B.BatchRunner(batch.subset(idx), buckets=((lo, hi),), tuning={})
-        b = runner.buckets[0]
+
+        def configure(cfg):
+            for b in runner.buckets:      # every chunk of the bucket
+                fbcc.fbcc_workspace_configure(b.ws, **cfg)
         times = {}
         for cfg in candidates:
-            fbcc.fbcc_workspace_configure(b.ws, **cfg)
+            configure(cfg)
             times[json.dumps(cfg, sort_keys=True)] = _time(runner.run, reps)
         final = {}
         for key in _finalists(times):   # the closest few again, long enough to see rare slow runs
-            fbcc.fbcc_workspace_configure(b.ws, **json.loads(key))
+            configure(json.loads(key))
             final[key] = _time(runner.run, final_reps)
         best = min(final, key=final.get)
         times.update(final)

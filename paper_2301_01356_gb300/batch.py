@@ -6,6 +6,12 @@ bucket is re-packed contiguously, uploaded once, and solved by one
 Each bucket has its own workspace, its tuned configuration (ruler stride,
 First-CC variant: see ``autotune``), its own stream and its own captured CUDA
 graph, so the buckets' solves overlap on the device.
+
+A bucket larger than ``MAX_CHUNK_ARCS`` arcs is split into chunks of consecutive
+graphs, each solved like a bucket of its own (same configuration). A chunk's
+copies in and out then overlap the other chunks' kernels, where one large bucket
+would copy all of its input before its first kernel and all of its output after
+its last.
 """
 from __future__ import annotations
 
@@ -20,6 +26,22 @@ from . import fbcc
 BUCKETS = ((0, 10_000), (10_000, 100_000), (100_000, 1 << 62))
 TUNING_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 STATS_WORDS = 5      # one fbcc_stats is 40 bytes
+MAX_CHUNK_ARCS = 1 << 28
+
+
+def chunks(idx: np.ndarray, arcs: np.ndarray, cap: int) -> list:
+    """Split the graph ids ``idx`` (in order) into runs whose arc counts add up to at
+    most ``cap``; a graph with more than ``cap`` arcs forms a run of its own."""
+    out, start, tot = [], 0, 0
+    for k, g in enumerate(idx):
+        a = int(arcs[g])
+        if k > start and tot + a > cap:
+            out.append(idx[start:k])
+            start, tot = k, 0
+        tot += a
+    if len(idx) > start:
+        out.append(idx[start:])
+    return out
 
 
 def load_tuning(path: str = TUNING_PATH) -> dict:
@@ -70,19 +92,24 @@ class _Bucket:
 class BatchRunner:
     """All graphs of a batch, solved bucket by bucket (buckets overlap on streams)."""
 
-    def __init__(self, batch, buckets=BUCKETS, tuning: dict | None = None, device="cuda", configs=None):
+    def __init__(self, batch, buckets=BUCKETS, tuning: dict | None = None, device="cuda", configs=None,
+                 max_chunk_arcs: int = MAX_CHUNK_ARCS):
         import torch
         self.torch = torch
         self.batch = batch
         sizes = batch.sizes()
+        arcs = np.diff(batch.arc_base)
         tuning = load_tuning() if tuning is None else tuning
-        self.buckets = []
+        self.buckets = []          # one entry per chunk; .bucket is its size bucket
         for i, (lo, hi) in enumerate(buckets):
             idx = np.nonzero((sizes >= lo) & (sizes < hi))[0]
             if idx.size == 0:
                 continue
             cfg = configs[i] if configs is not None else bucket_config(tuning, lo, hi)
-            self.buckets.append(_Bucket(torch, batch.subset(idx), idx, cfg, device))
+            for part in chunks(idx, arcs, max_chunk_arcs):
+                b = _Bucket(torch, batch.subset(part), part, cfg, device)
+                b.bucket = i
+                self.buckets.append(b)
         self.where = {}
         for bi, b in enumerate(self.buckets):
             for j, g in enumerate(b.idx):

@@ -84,3 +84,19 @@ def test_cpu_baseline_sample_is_bounded():
     small, desc = bench.cpu_sample("rmat24", None)
     assert small.n == 1 << bench.CPU_SAMPLE_SCALE and small.m > 0
     assert f"scale {bench.CPU_SAMPLE_SCALE}" in desc
+
+
+def test_batch_chunks():
+    """Splitting a bucket into chunks keeps every graph once, in order, and each
+    chunk within the arc cap unless it is a single graph above the cap."""
+    import numpy as np
+    from paper_2301_01356_gb300.batch import chunks
+    arcs = np.array([5, 3, 9, 2, 2, 12, 1, 4, 4], np.int64)
+    idx = np.array([0, 2, 3, 4, 5, 6, 8])
+    parts = chunks(idx, arcs, 10)
+    assert np.array_equal(np.concatenate(parts), idx)
+    for p in parts:
+        assert arcs[p].sum() <= 10 or p.size == 1
+    assert [list(p) for p in parts] == [[0], [2], [3, 4], [5], [6, 8]]
+    assert chunks(np.array([], np.int64), arcs, 10) == []
+    assert [list(p) for p in chunks(idx, arcs, 1 << 40)] == [list(idx)]

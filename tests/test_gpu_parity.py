@@ -146,23 +146,24 @@ def test_host_entry_point(torch_cuda, oracle):
     s.close()
 
 
-def test_host_async_two_workspaces(torch_cuda, oracle):
-    """fbcc_solve_host_async on two workspaces and two streams, several rounds,
-    equals the oracle (bcc_head is compared over its first n_bcc entries)."""
+def test_host_async_three_workspaces(torch_cuda, oracle):
+    """fbcc_solve_host_async on three workspaces and three streams (the pipelined
+    end-to-end form of the benchmark), several rounds, equals the oracle (bcc_head
+    is compared over its first n_bcc entries)."""
     from paper_2301_01356_gb300 import fbcc
     torch = torch_cuda
-    graphs = [gg.uniform(6000, 15000, 3), gg.grid(90, 80, p=0.6, seed=2)]
+    graphs = [gg.uniform(6000, 15000, 3), gg.grid(90, 80, p=0.6, seed=2), gg.grid(60, 70, p=0.7, seed=5)]
     exps = [oracle.solve(g.offsets, g.adj) for g in graphs]
     nmax = max(g.n for g in graphs)
     zmax = max(g.nnz for g in graphs)
-    wss = [fbcc.fbcc_workspace_create(nmax, zmax) for _ in range(2)]
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    wss = [fbcc.fbcc_workspace_create(nmax, zmax) for _ in graphs]
+    streams = [torch.cuda.Stream() for _ in graphs]
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     ins = [(pin(g.offsets), pin(g.adj)) for g in graphs]
     outs = [[pin(np.full(g.nnz, -1, np.int32)), pin(np.full(g.n, -1, np.int32)), pin(np.zeros(g.n, np.uint8)),
              pin(np.zeros(g.nnz, np.uint8))] for g in graphs]
     for rnd in range(3):
-        for i in range(2):
+        for i in range(len(graphs)):
             fbcc.fbcc_solve_host_async(*ins[i], *outs[i], wss[i], streams[i])
         for st in streams:
             st.synchronize()
@@ -315,13 +316,18 @@ def test_rmat24_full_size_properties(torch_cuda):
         assert np.any(eb[g.offsets[h]:g.offsets[h + 1]] == k), "head lies in its BCC"
 
 
-def test_bucketed_batch_runner(torch_cuda, oracle):
+@pytest.mark.parametrize("max_chunk_arcs", [1 << 28, 150_000])
+def test_bucketed_batch_runner(torch_cuda, oracle, max_chunk_arcs):
     """The config-4 recipe at small scale: every graph's result in the bucketed
-    batch equals the oracle's and its result when solved alone."""
+    batch equals the oracle's and its result when solved alone; also with the
+    buckets split into chunks (several solves per bucket)."""
     from paper_2301_01356_gb300 import batch as B, fbcc
     bt = gg.batch(96, 7, 200, 30000, families=("uniform", "grid", "chain", "knn"))
     runner = B.BatchRunner(bt, buckets=((0, 2000), (2000, 10000), (10000, 1 << 40)), tuning={},
-                           configs=[{}, {"cc_local": 4096}, {"ruler_stride": 32, "cc_sample": 2}])
+                           configs=[{}, {"cc_local": 4096}, {"ruler_stride": 32, "cc_sample": 2}],
+                           max_chunk_arcs=max_chunk_arcs)
+    if max_chunk_arcs < (1 << 28):
+        assert len(runner.buckets) > 3, "the small cap splits the buckets"
     runner.run()
     torch_cuda.cuda.synchronize()
     alone = fbcc.Solver(int(bt.sizes().max()), int(np.diff(bt.arc_base).max()))
