@@ -26,7 +26,7 @@ from . import fbcc
 BUCKETS = ((0, 10_000), (10_000, 100_000), (100_000, 1 << 62))
 TUNING_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 STATS_WORDS = 5      # one fbcc_stats is 40 bytes
-MAX_CHUNK_ARCS = 1 << 28
+MAX_CHUNK_ARCS = 1 << 26
 
 
 def chunks(idx: np.ndarray, arcs: np.ndarray, cap: int) -> list:

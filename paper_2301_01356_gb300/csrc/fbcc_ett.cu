@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kThreads) k_place_records(int64_t n, const int
 // of T_v spans positions p..q, two per vertex, so size(v) = (q - p + 1) / 2 and
 // the up arc also knows first[v] = S(q) - (q - p - 1) / 2: it stores last by
 // preorder number. Only fp is written by vertex id.
-__global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *__restrict__ rec, int2 *fp,
+__global__ void __launch_bounds__(kThreads, 5) k_preorder(int64_t n2, const int2 *__restrict__ rec, int2 *fp,
                                                        int32_t *lastp, int32_t *ord, int32_t *porig, int32_t *w1,
                                                        int32_t *w2, long long *ticket, uint64_t *status, int *err)
 {
@@ -417,6 +417,8 @@ __global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *_
     // thread takes its kItems consecutive records (slot e at e + e / 8 keeps the
     // 8-byte reads of a warp free of bank conflicts)
     __shared__ int2 srec[kTile + kTile / 8];
+    __shared__ long long s_base;
+    static_assert(2 * kTile * sizeof(int32_t) <= sizeof(srec), "staging fits in the record buffer");
     const int64_t ntiles = (n2 + kTile - 1) / kTile;
     const int64_t n = n2 / 2;
     while (true) {
@@ -439,21 +441,42 @@ __global__ void __launch_bounds__(kThreads) k_preorder(int64_t n2, const int2 *_
             v[j] = r[j].x >= 0 || r[j].x == -2;
         }
         scan_tile_exclusive(v, t, status, err);
+        // The tile's counting positions take consecutive preorder numbers from
+        // the tile's base on, so the arrays indexed by preorder number are staged
+        // in shared memory (srec is free again: the scan synchronised the CTA)
+        // and written out coalesced; slot i holds preorder number base + i + 1.
+        int32_t *s_ord = reinterpret_cast<int32_t *>(srec), *s_porig = s_ord + kTile;
+        if (threadIdx.x == 0) s_base = v[0];
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) s_ord[k * kThreads + threadIdx.x] = -1;
+        __syncthreads();
+        const long long base = s_base;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             if (r[j].x >= 0) {
                 const int32_t vtx = r[j].x, x = r[j].y, fv = (int32_t)v[j] + 1;
                 if (!in_range(fv, n, err) || !in_range(vtx, n, err)) continue;
                 fp[vtx] = make_int2(fv, x);
-                ord[fv] = vtx;
-                porig[fv] = x;
-                w1[fv] = fv;
-                w2[fv] = fv;
+                s_ord[v[j] - base] = vtx;
+                s_porig[v[j] - base] = x;
             } else if (r[j].x == -1) {
                 const int32_t e = (int32_t)v[j], fv = e - (r[j].y - 1) / 2;
                 if (in_range(fv, n, err) && fv <= e) lastp[fv] = e;
             }
         }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int i = k * kThreads + threadIdx.x;
+            const int32_t o = s_ord[i];
+            if (o < 0) continue;
+            const int32_t fv = (int32_t)(base + i + 1);
+            ord[fv] = o;
+            porig[fv] = s_porig[i];
+            w1[fv] = fv;
+            w2[fv] = fv;
+        }
+        __syncthreads();   // the next tile's records overwrite the staging
     }
 }
 

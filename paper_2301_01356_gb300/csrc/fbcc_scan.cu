@@ -12,14 +12,31 @@ __global__ void __launch_bounds__(kThreads) k_scan_popc(const uint32_t *words, i
     while (true) {
         int64_t t = scan_ticket(ticket);
         if (t >= ntiles) return;
+        static_assert(kItems == 8, "two 16-byte loads and stores per thread");
         long long v[kItems];
         const int64_t i0 = t * kTile + (int64_t)threadIdx.x * kItems;
+        // whole groups of eight move as 16-byte vectors (the workspace's pieces are
+        // 256-byte aligned and i0 is a multiple of 8)
+        const bool whole = i0 + kItems <= len;
+        if (whole) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(words + i0);
+            const uint4 b = *reinterpret_cast<const uint4 *>(words + i0 + 4);
+            v[0] = __popc(a.x); v[1] = __popc(a.y); v[2] = __popc(a.z); v[3] = __popc(a.w);
+            v[4] = __popc(b.x); v[5] = __popc(b.y); v[6] = __popc(b.z); v[7] = __popc(b.w);
+        } else {
 #pragma unroll
-        for (int j = 0; j < kItems; ++j) v[j] = (i0 + j < len) ? __popc(words[i0 + j]) : 0;
+            for (int j = 0; j < kItems; ++j) v[j] = (i0 + j < len) ? __popc(words[i0 + j]) : 0;
+        }
         scan_tile_exclusive(v, t, status, err);
+        if (whole) {
+            *reinterpret_cast<int4 *>(out + i0) = make_int4((int32_t)v[0], (int32_t)v[1], (int32_t)v[2], (int32_t)v[3]);
+            *reinterpret_cast<int4 *>(out + i0 + 4) =
+                make_int4((int32_t)v[4], (int32_t)v[5], (int32_t)v[6], (int32_t)v[7]);
+        } else {
 #pragma unroll
-        for (int j = 0; j < kItems; ++j)
-            if (i0 + j <= len) out[i0 + j] = (int32_t)v[j];
+            for (int j = 0; j < kItems; ++j)
+                if (i0 + j <= len) out[i0 + j] = (int32_t)v[j];
+        }
     }
 }
 

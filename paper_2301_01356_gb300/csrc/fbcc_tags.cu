@@ -112,12 +112,25 @@ __global__ void __launch_bounds__(kThreads) k_rmq_prefix(int64_t n, const int32_
     const int64_t ntiles = (n + kRmqTile - 1) / kRmqTile;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t p0 = t * kRmqTile + (int64_t)threadIdx.x * kPer;
+        static_assert(kPer == 4, "one 16-byte load per array and thread");
+        const bool whole = p0 + kPer <= n;   // the arrays' pieces are 256-byte aligned
+        int32_t x4[kPer], y4[kPer];
+        if (whole) {
+            const int4 xv = *reinterpret_cast<const int4 *>(w1 + p0), yv = *reinterpret_cast<const int4 *>(w2 + p0);
+            x4[0] = xv.x; x4[1] = xv.y; x4[2] = xv.z; x4[3] = xv.w;
+            y4[0] = yv.x; y4[1] = yv.y; y4[2] = yv.z; y4[3] = yv.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                x4[j] = p0 + j < n ? w1[p0 + j] : INT32_MAX;
+                y4[j] = p0 + j < n ? w2[p0 + j] : INT32_MIN;
+            }
+        }
         int32_t a[kPer], b[kPer];
         int32_t rmn = INT32_MAX, rmx = INT32_MIN;
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            int64_t p = p0 + j;
-            int32_t x = p < n ? w1[p] : INT32_MAX, y = p < n ? w2[p] : INT32_MIN;
+            const int32_t x = x4[j], y = y4[j];
             rmn = x < rmn ? x : rmn;
             rmx = y > rmx ? y : rmx;
             a[j] = rmn;
@@ -150,10 +163,19 @@ __global__ void __launch_bounds__(kThreads) k_rmq_prefix(int64_t n, const int32_
         }
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            int64_t p = p0 + j;
-            if (p < n) {
-                pmin[p] = a[j] < emn ? a[j] : emn;
-                pmax[p] = b[j] > emx ? b[j] : emx;
+            a[j] = a[j] < emn ? a[j] : emn;
+            b[j] = b[j] > emx ? b[j] : emx;
+        }
+        if (whole) {
+            *reinterpret_cast<int4 *>(pmin + p0) = make_int4(a[0], a[1], a[2], a[3]);
+            *reinterpret_cast<int4 *>(pmax + p0) = make_int4(b[0], b[1], b[2], b[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                if (p0 + j < n) {
+                    pmin[p0 + j] = a[j];
+                    pmax[p0 + j] = b[j];
+                }
             }
         }
         if (threadIdx.x == 0) {
