@@ -151,11 +151,11 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_cc_hook": B * (n + 1) + 4 * nnz + 2 * nnz + 8 * (n - n_cc),
         "k_uf_compress": 8 * n,
         "k_link": 12 * n + 4 * A,
-        "k_succ_rulers": 16 * n + 13 * A + 4 * nr,
+        "k_succ_rulers": 32 * n + 4 * A + 5 * nr,
         "k_chase": 16 * A + 16 * nr,
         "k_jump": 24 * nr,
         "k_place_records": 30 * A,
-        "k_comp_size": 16 * n + 40 * n_cc,
+        "k_comp_size": 4 * n + 68 * n_cc,
         "k_preorder": 16 * n + 28 * n,
         "k_first_of": 12 * n,
         "k_w12": B * (n + 1) + 4 * nnz + 4 * nnz + nnz // 8 + 8 * n,

@@ -95,7 +95,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     const size_t xl_from = c.used;
     d.lhead = c.take<int32_t>(N);
     d.nxt = c.take<int32_t>(2 * N);
-    d.is_head = c.take<uint8_t>(2 * N);
+    d.rhead = c.take<uint8_t>(d.ruler_max);
     d.link = c.take<int2>(2 * N);
     d.relem = c.take<int32_t>(d.ruler_max);
     for (int i = 0; i < 2; ++i) {

@@ -80,52 +80,96 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
 // succ(a) for a = x->y is the arc after a^1 in y's list, cyclically; when y is a
 // component root the wrap-around ends the tour instead, and the first arc of the
 // root's list heads it. Rulers: tour heads plus every arc id divisible by the
-// stride. link[a] = {succ, ruler id or -1}; relem[id] = a. Ids come from one
-// atomic per CTA and iteration.
+// stride. link[a] = {succ, ruler id or -1} ({-1, -1} for the unused ids of
+// vertices that hooked nothing); relem[id] = a; rhead[id] = 1 if the ruler heads
+// its tour. A thread takes four consecutive forest edges (eight arcs, loaded and
+// stored as 16-byte vectors); ids come from one atomic per CTA and step of kTile
+// arcs.
 __global__ void __launch_bounds__(kThreads) k_succ_rulers(int64_t n, const int32_t *__restrict__ te_u,
                                                           const int32_t *__restrict__ te_v,
                                                           const int32_t *__restrict__ uf,
                                                           const int32_t *__restrict__ lhead,
                                                           const int32_t *__restrict__ nxt, int stride, int2 *link,
-                                                          uint8_t *is_head, int32_t *relem, long long *nr)
+                                                          uint8_t *rhead, int32_t *relem, long long *nr)
 {
+    constexpr int kE = kItems / 2;   // forest edges per thread and step
+    static_assert(kE == 4, "one 16-byte load of te_u and te_v per thread");
     __shared__ int32_t warp_cnt[kThreads / 32];
     __shared__ long long block_base;
-    const int64_t A = 2 * n;
-    const int64_t A_pad = (A + kThreads - 1) / kThreads * kThreads;  // whole CTAs take part
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < A_pad; a += (int64_t)gridDim.x * kThreads) {
-        const bool in = a < A && te_u[a >> 1] >= 0;
-        int32_t sc = -1;
-        bool head = false;
-        if (in) {
-            const int32_t x = arc_src(te_u, te_v, a), y = arc_dst(te_u, te_v, a);
-            const int32_t nx = nxt[a ^ 1];
-            sc = nx >= 0 ? nx : (uf[y] == y ? -1 : lhead[y]);
-            head = uf[x] == x && lhead[x] == a;
+    const int64_t ntiles = (n + kThreads * kE - 1) / (kThreads * kE);
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {   // whole CTAs take part
+        const int64_t h0 = (t * kThreads + threadIdx.x) * kE;
+        // the workspace's pieces are 256-byte aligned and h0 is a multiple of 4
+        const bool whole = h0 + kE <= n;
+        int32_t eu[kE], ev[kE], nx[2 * kE];
+        if (whole) {
+            const int4 a = *reinterpret_cast<const int4 *>(te_u + h0), b = *reinterpret_cast<const int4 *>(te_v + h0);
+            const int4 c = *reinterpret_cast<const int4 *>(nxt + 2 * h0);
+            const int4 d = *reinterpret_cast<const int4 *>(nxt + 2 * h0 + 4);
+            eu[0] = a.x; eu[1] = a.y; eu[2] = a.z; eu[3] = a.w;
+            ev[0] = b.x; ev[1] = b.y; ev[2] = b.z; ev[3] = b.w;
+            nx[0] = c.x; nx[1] = c.y; nx[2] = c.z; nx[3] = c.w; nx[4] = d.x; nx[5] = d.y; nx[6] = d.z; nx[7] = d.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kE; ++k) {
+                const bool in = h0 + k < n;
+                eu[k] = in ? te_u[h0 + k] : -1;
+                ev[k] = in ? te_v[h0 + k] : -1;
+                nx[2 * k] = in ? nxt[2 * (h0 + k)] : -1;
+                nx[2 * k + 1] = in ? nxt[2 * (h0 + k) + 1] : -1;
+            }
         }
-        const bool ruler = in && (head || (a & (stride - 1)) == 0);
-        const unsigned mask = __ballot_sync(0xffffffffu, ruler);
-        if (lane == 0) warp_cnt[wid] = __popc(mask);
+        int32_t sc[2 * kE];
+        unsigned head = 0, ruler = 0;
+#pragma unroll
+        for (int j = 0; j < 2 * kE; ++j) {
+            const int k = j >> 1;
+            const int64_t a = 2 * h0 + j;
+            sc[j] = -1;
+            if (eu[k] < 0) continue;
+            const int32_t x = (j & 1) ? ev[k] : eu[k], y = (j & 1) ? eu[k] : ev[k];
+            const int32_t nxr = nx[j ^ 1];   // nxt of the reverse arc
+            sc[j] = nxr >= 0 ? nxr : (uf[y] == y ? -1 : lhead[y]);
+            if (uf[x] == x && lhead[x] == a) head |= 1u << j;
+            if (((head >> j) & 1u) || (a & (stride - 1)) == 0) ruler |= 1u << j;
+        }
+        const int cnt = __popc(ruler);
+        int inc = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) warp_cnt[wid] = inc;
         __syncthreads();
         if (threadIdx.x == 0) {
-            int32_t t = 0;
-            for (int w = 0; w < kThreads / 32; ++w) t += warp_cnt[w];
-            block_base = t ? (long long)atomicAdd((unsigned long long *)nr, (unsigned long long)t) : 0;
+            int32_t tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) tot += warp_cnt[w];
+            block_base = tot ? (long long)atomicAdd((unsigned long long *)nr, (unsigned long long)tot) : 0;
         }
         __syncthreads();
-        int32_t before = 0;
-        for (int w = 0; w < wid; ++w) before += warp_cnt[w];
-        const long long base = block_base + before;
-        __syncthreads();  // warp_cnt / block_base are rewritten next iteration
-        if (!in) continue;
-        int32_t id = -1;
-        if (ruler) {
-            id = (int32_t)(base + __popc(mask & ((1u << lane) - 1u)));
-            relem[id] = (int32_t)a;
+        long long id = block_base + inc - cnt;
+        for (int w = 0; w < wid; ++w) id += warp_cnt[w];
+        __syncthreads();  // warp_cnt / block_base are rewritten next step
+        int32_t rid[2 * kE];
+#pragma unroll
+        for (int j = 0; j < 2 * kE; ++j) {
+            rid[j] = -1;
+            if ((ruler >> j) & 1u) {
+                rid[j] = (int32_t)id++;
+                relem[rid[j]] = (int32_t)(2 * h0 + j);
+                rhead[rid[j]] = (head >> j) & 1u;
+            }
         }
-        link[a] = make_int2(sc, id);
-        is_head[a] = head;
+        if (whole) {
+            int4 *o = reinterpret_cast<int4 *>(link + 2 * h0);
+#pragma unroll
+            for (int q = 0; q < kE; ++q) o[q] = make_int4(sc[2 * q], rid[2 * q], sc[2 * q + 1], rid[2 * q + 1]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2 * kE; ++j)
+                if (h0 + (j >> 1) < n) link[2 * h0 + j] = make_int2(sc[j], rid[j]);
+        }
     }
 }
 
@@ -197,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_chase(int64_t n,
 // heads and every stride2-th ruler become level-2 rulers.
 __global__ void __launch_bounds__(kThreads) k_rulers2(const long long *__restrict__ nr_p, int stride2,
                                                       const int32_t *__restrict__ relem,
-                                                      const uint8_t *__restrict__ is_head,
+                                                      const uint8_t *__restrict__ rhead,
                                                       const int32_t *__restrict__ rnext1, int2 *l2, int32_t *relem2,
                                                       long long *nr2)
 {
@@ -211,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_rulers2(const long long *__restric
         bool single = false, ruler = false;
         int32_t nx = -1;
         if (in) {
-            const bool head = is_head[relem[r]];
+            const bool head = rhead[r];
             nx = rnext1[r];
             single = head && nx < 0;
             ruler = !single && (head || (r & (stride2 - 1)) == 0);
@@ -304,12 +348,14 @@ __global__ void __launch_bounds__(kThreads) k_jump(const long long *__restrict__
 // Component size at its root (1 for an isolated root, else tour length / 2 + 1)
 // and the component's first preorder number. The components may take the
 // preorder range in any order (only the order inside a component matters), so
-// each CTA reserves one block of the range with one atomic and hands it out to its
-// roots by a block scan: no separate scan pass over all vertices. The root also
-// writes its own tags (preorder number b, last b + size - 1, no parent) and the
-// two padding records that end its tour's slot in the record array (the arcs fill
-// the slot's first 2 (size - 1) positions): a counting one, so that the count
-// restarts right at the next component's base, and a neutral one.
+// each CTA reserves one block of the range with one atomic per step of kTile
+// vertices (kItems consecutive ones per thread, loaded as 16-byte vectors) and
+// hands it out to its roots by a block scan: no separate scan pass over all
+// vertices. Only roots are written. The root also writes its own tags (preorder
+// number b, last b + size - 1, no parent) and the two padding records that end
+// its tour's slot in the record array (the arcs fill the slot's first
+// 2 (size - 1) positions): a counting one, so that the count restarts right at
+// the next component's base, and a neutral one.
 __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t *__restrict__ uf,
                                                         const int32_t *__restrict__ lhead,
                                                         const int2 *__restrict__ link, const int32_t *__restrict__ sd,
@@ -318,51 +364,83 @@ __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t
                                                         int32_t *ord, int32_t *porig, int32_t *w1, int32_t *w2,
                                                         int *err)
 {
-    __shared__ int32_t warp_tot[kThreads / 32];
+    static_assert(kItems == 8, "two 16-byte loads per thread");
+    __shared__ long long warp_tot[kThreads / 32];
     __shared__ long long block_base;
+    __shared__ int32_t s_c[kTile + kTile / 32], s_b[kTile + kTile / 32];   // padded against bank conflicts
     const int64_t nr = *nr_p;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t n_pad = (n + kThreads - 1) / kThreads * kThreads;   // whole CTAs take part
-    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
-        int32_t c = 0;
-        if (v < n && uf[v] == v) {
-            c = 1;
-            if (lhead[v] >= 0) {
-                const int32_t id = link[lhead[v]].y;
-                if (in_range(id, nr, err)) c = sd[id] / 2 + 1;
-            }
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {     // whole CTAs take part
+        const int64_t v0 = t * kTile + (int64_t)threadIdx.x * kItems;
+        int32_t p[kItems];
+        if (v0 + kItems <= n) {   // uf is a 256-byte aligned workspace piece
+            const int4 a = *reinterpret_cast<const int4 *>(uf + v0), b = *reinterpret_cast<const int4 *>(uf + v0 + 4);
+            p[0] = a.x; p[1] = a.y; p[2] = a.z; p[3] = a.w; p[4] = b.x; p[5] = b.y; p[6] = b.z; p[7] = b.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) p[j] = v0 + j < n ? uf[v0 + j] : -1;
         }
-        int32_t inc = c;
+        int32_t c[kItems];
+        long long run = 0;
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int64_t v = v0 + j;
+            c[j] = 0;
+            if (p[j] == v) {
+                c[j] = 1;
+                const int32_t h = lhead[v];
+                if (h >= 0) {
+                    const int32_t id = link[h].y;
+                    if (in_range(id, nr, err)) c[j] = sd[id] / 2 + 1;
+                }
+            }
+            run += c[j];
+        }
+        long long inc = run;
         for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            const long long y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) warp_tot[wid] = inc;
         __syncthreads();
         if (threadIdx.x == 0) {
-            long long t = 0;
-            for (int w = 0; w < kThreads / 32; ++w) t += warp_tot[w];
-            block_base = t ? (long long)atomicAdd((unsigned long long *)next_base, (unsigned long long)t) : 0;
+            long long tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) tot += warp_tot[w];
+            block_base = tot ? (long long)atomicAdd((unsigned long long *)next_base, (unsigned long long)tot) : 0;
         }
         __syncthreads();
-        long long b = block_base + inc - c;
+        long long b = block_base + inc - run;
         for (int w = 0; w < wid; ++w) b += warp_tot[w];
-        __syncthreads();   // warp_tot / block_base are rewritten next iteration
-        if (v < n) {
-            csize[v] = c;
-            if (c) {
-                const int32_t bb = (int32_t)b;
-                vbase[v] = bb;
-                rec[2 * b + 2 * c - 2] = make_int2(-2, 0);
-                rec[2 * b + 2 * c - 1] = make_int2(-3, 0);
-                fp[v] = make_int2(bb, -1);
-                lastp[bb] = bb + c - 1;
-                ord[bb] = (int32_t)v;
-                porig[bb] = -1;
-                w1[bb] = bb;
-                w2[bb] = bb;
-            }
+        // the roots' writes go out in vertex order across the lanes (slot e holds
+        // vertex t * kTile + e), so that neighbouring lanes write neighbouring words
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int e = threadIdx.x * kItems + j;
+            s_c[e + (e >> 5)] = c[j];
+            s_b[e + (e >> 5)] = (int32_t)b;
+            b += c[j];
         }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int e = k * kThreads + threadIdx.x;
+            const int32_t cc = s_c[e + (e >> 5)];
+            if (!cc) continue;
+            const int64_t v = t * kTile + e;
+            const int32_t bb = s_b[e + (e >> 5)];
+            csize[v] = cc;
+            vbase[v] = bb;
+            rec[2 * (int64_t)bb + 2 * cc - 2] = make_int2(-2, 0);
+            rec[2 * (int64_t)bb + 2 * cc - 1] = make_int2(-3, 0);
+            fp[v] = make_int2(bb, -1);
+            lastp[bb] = bb + cc - 1;
+            ord[bb] = (int32_t)v;
+            porig[bb] = -1;
+            w1[bb] = bb;
+            w2[bb] = bb;
+        }
+        __syncthreads();   // warp_tot, block_base and the staging are rewritten next step
     }
 }
 
@@ -494,7 +572,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_link");
     long long *nr = d.counters + 1;
     CK(cudaMemsetAsync(nr, 0, sizeof(long long), L.s));
-    k_succ_rulers<<<ga, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.lhead, d.nxt, ruler_stride, d.link, d.is_head,
+    k_succ_rulers<<<grid_for(L, ceil_div(n, kTile / 2)), kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.lhead, d.nxt, ruler_stride, d.link, d.rhead,
                                             d.relem, nr);
     L.mark("k_succ_rulers");
     // upper bound on the number of rulers: a head per tour (a tour spans at least
@@ -510,7 +588,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_chase");
     long long *nr2 = d.counters + 3;
     CK(cudaMemsetAsync(nr2, 0, sizeof(long long), L.s));
-    k_rulers2<<<gr, kThreads, 0, L.s>>>(nr, kStride2, d.relem, d.is_head, d.rnx1, d.l2, d.relem2, nr2);
+    k_rulers2<<<gr, kThreads, 0, L.s>>>(nr, kStride2, d.relem, d.rhead, d.rnx1, d.l2, d.relem2, nr2);
     L.mark("k_rulers2");
     // level-2 rulers: heads of lists with several rulers (each holds a stride
     // sample, so at most 2n / stride of them) plus one in kStride2 rulers
@@ -531,7 +609,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     const int32_t *sd = d.sd1;
     long long *next_base = d.counters + 6;
     CK(cudaMemsetAsync(next_base, 0, sizeof(long long), L.s));
-    k_comp_size<<<gv, kThreads, 0, L.s>>>(n, d.uf, d.lhead, d.link, sd, nr, d.csize, d.vbase, next_base, d.rec,
+    k_comp_size<<<grid_for(L, ceil_div(n, kTile)), kThreads, 0, L.s>>>(n, d.uf, d.lhead, d.link, sd, nr, d.csize, d.vbase, next_base, d.rec,
                                           d.fp, d.lastp, d.ord, d.porig, d.w1, d.w2, d.err);
     L.mark("k_comp_size");
     CK(cudaGetLastError());

@@ -52,7 +52,7 @@ struct Dev {
     // Rooting
     int32_t *lhead;           // first forest arc of every vertex's list (-1: none)
     int32_t *nxt;             // next arc in its source's list (2n ids; -1: last)
-    uint8_t *is_head;         // first arc of a tour (2n)
+    uint8_t *rhead;           // by ruler id: 1 if the ruler heads its tour
     int2 *link;               // {succ, ruler id or -1} per tree arc; after the walks a non-ruler
                               // arc holds {owning ruler, -distance from it}
     int32_t *relem;           // arc of ruler r
@@ -63,7 +63,7 @@ struct Dev {
     int32_t *relem2;          // level-1 ruler of level-2 ruler R
     int32_t *owner2, *offs2;  // level-2 owner of every ruler and its weighted offset
     int32_t *sd1;             // suffix length (arcs to the tour's end) from every ruler
-    int32_t *csize;           // component size at its root, 0 elsewhere
+    int32_t *csize;           // component size at its root (other entries unspecified)
     int32_t *vbase;           // first preorder number of the component at its root
     int2 *rec;                // tour record at every position (down/up arc, padding)
     // Tagging (fp indexed by vertex; the rest by preorder number)
