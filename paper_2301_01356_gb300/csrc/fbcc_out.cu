@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, co
 
 // edge_bcc / is_bridge for every arc.
 template <typename OffT>
-__global__ void __launch_bounds__(kThreads, 8) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
+__global__ void __launch_bounds__(kThreads, 6) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                        int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
                                                        const int32_t *__restrict__ word,
                                                        const uint8_t *__restrict__ dirb, int32_t *edge_bcc,
@@ -313,18 +313,22 @@ __global__ void __launch_bounds__(kThreads, 8) k_edge_out(const OffT *__restrict
         const uint32_t bits = __ldg(dirb + (at.a0 >> 3));
         int32_t lab8[kItems];
         uint8_t br8[kItems];
-        int32_t cur = -1, ws = 0;
+        // x = the endpoint with the larger preorder number (the direction bit):
+        // every arc's word gather is issued before any is used (a lane's sources
+        // are few and neighbouring, so their repeated loads hit L1)
+        int32_t wx[kItems];
+#pragma unroll
+        for (int j = 0; j < kItems; ++j)
+            wx[j] = j < at.cnt ? __ldg(word + ((bits >> j) & 1u ? d[j] : at.src[j])) : 0;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             lab8[j] = 0;
             br8[j] = 0;
             if (j >= at.cnt) continue;
-            if (at.src[j] != cur) { cur = at.src[j]; ws = __ldg(word + cur); }
-            // x = the endpoint with the larger preorder number (the direction bit).
             // If x's parent edge is a bridge, x's label class is {x} and that bridge
             // is the only edge of its BCC, so every arc labelled through x is the
             // bridge itself.
-            const int32_t w = (bits >> j) & 1u ? __ldg(word + d[j]) : ws;
+            const int32_t w = wx[j];
             lab8[j] = w & 0x7fffffff;
             br8[j] = (uint8_t)((uint32_t)w >> 31);
         }
@@ -337,9 +341,12 @@ __global__ void __launch_bounds__(kThreads, 8) k_edge_out(const OffT *__restrict
             b.y = br8[4] | (br8[5] << 8) | (br8[6] << 16) | ((uint32_t)br8[7] << 24);
             __stcs(reinterpret_cast<uint2 *>(is_bridge + at.a0), b);
         } else {
-            for (int j = 0; j < at.cnt; ++j) {
-                edge_bcc[at.a0 + j] = lab8[j];
-                is_bridge[at.a0 + j] = br8[j];
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) {
+                if (j < at.cnt) {
+                    edge_bcc[at.a0 + j] = lab8[j];
+                    is_bridge[at.a0 + j] = br8[j];
+                }
             }
         }
     }

@@ -51,7 +51,11 @@ __global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, 
         arc_tile_sources(off, nnz, tile_v, t, win, at);
         // A lane whose arcs all leave one source keeps that run for a warp-wide
         // reduction: the lanes of a long list then add one atomic per warp.
-        const bool single = at.cnt > 0 && at.src[0] == at.src[at.cnt - 1];
+        int32_t src_last = at.src[0];   // (static indices keep at.src in registers)
+#pragma unroll
+        for (int j = 1; j < kItems; ++j)
+            if (j < at.cnt) src_last = at.src[j];
+        const bool single = at.cnt > 0 && at.src[0] == src_last;
         int32_t cur = -1, mn = INT32_MAX, mx = INT32_MIN;
         int2 fc = make_int2(0, -1);
         uint32_t bits = 0;
@@ -59,15 +63,13 @@ __global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, 
             int32_t d[kItems];
             arc_tile_targets(adj, at.a0, at.cnt, vec, d);
 #pragma unroll
-            for (int j = 0; j <= kItems; ++j) {
-                bool live = j < at.cnt;
-                if (!live || at.src[j] != cur) {
-                    if (!live && single) break;   // flushed below, with the warp
+            for (int j = 0; j < kItems; ++j) {
+                if (j >= at.cnt) break;
+                if (at.src[j] != cur) {   // a new source: the previous run adds its atomics
                     if (cur >= 0 && mn != INT32_MAX && in_range(fc.x, n, err)) {
                         if (mn < fc.x) atomicMin(w1 + fc.x, mn);
                         if (mx > fc.x) atomicMax(w2 + fc.x, mx);
                     }
-                    if (!live) break;
                     cur = at.src[j];
                     fc = __ldg(fp + cur);
                     mn = INT32_MAX;
@@ -78,6 +80,12 @@ __global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, 
                 if (fw > fc.x) bits |= 1u << j;
                 mn = fw < mn ? fw : mn;
                 mx = fw > mx ? fw : mx;
+            }
+            // the last run adds its atomics here, unless the lane has a single
+            // source (flushed below, with the warp)
+            if (!single && cur >= 0 && mn != INT32_MAX && in_range(fc.x, n, err)) {
+                if (mn < fc.x) atomicMin(w1 + fc.x, mn);
+                if (mx > fc.x) atomicMax(w2 + fc.x, mx);
             }
             dirb[at.a0 >> 3] = (uint8_t)bits;   // a0 is a multiple of kItems = 8
         }
