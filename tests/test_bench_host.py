@@ -100,3 +100,93 @@ def test_batch_chunks():
     assert [list(p) for p in parts] == [[0], [2], [3, 4], [5], [6, 8]]
     assert chunks(np.array([], np.int64), arcs, 10) == []
     assert [list(p) for p in chunks(idx, arcs, 1 << 40)] == [list(idx)]
+
+
+def test_clock_sampler_parses_reasons():
+    """The clocks object reports the median SM clock under load, the maximum, and
+    every throttle reason seen active in any sample."""
+    import bench
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.file.write("0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "0, 1800, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+                 "0, 1900, 2070, 1200.0, 0x0, Active, Not Active, Not Active, Not Active\n"
+                 "garbage line\n")
+    s.proc = Done()
+    c = s.stop()
+    assert c["sm_mhz"] == 1900.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_traffic_is_dropped_when_the_source_changes(tmp_path, monkeypatch):
+    """The committed DRAM traffic counts only for the exact source file it was
+    captured from (a hash of the file sits beside the figure)."""
+    import hashlib
+    import bench
+    src = tmp_path / "paper_2301_01356_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "k.cu").write_text("kernel source\n")
+    sha = hashlib.sha1(b"kernel source\n").hexdigest()[:12]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        f"kernel=k_x workload=w bytes_per_launch=123456 file=k.cu sha={sha} source=test\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic("k_x", "w") == 123456
+    assert bench.load_traffic("k_x", "other") is None
+    (src / "k.cu").write_text("kernel source, edited\n")
+    assert bench.load_traffic("k_x", "w") is None
+
+
+def test_committed_traffic_matches_the_current_source():
+    """profiles/traffic.txt carries a figure for the bench's dominant kernel; it is
+    reported while it still matches the committed source (skipped, with the reason,
+    after a kernel change that awaits a new capture)."""
+    import bench
+    lines = [ln for ln in open(os.path.join(ROOT, "profiles", "traffic.txt")) if ln.strip()]
+    assert lines
+    kv = dict(x.split("=", 1) for x in lines[0].split() if "=" in x)
+    assert {"kernel", "workload", "bytes_per_launch", "file", "sha"} <= set(kv)
+    got = bench.load_traffic(kv["kernel"], kv["workload"])
+    if got is None:
+        pytest.skip(f"traffic.txt predates the current {kv['file']}: the kernel needs a new capture")
+    assert got == int(float(kv["bytes_per_launch"]))
+
+
+def test_tuned_config_and_overrides():
+    """The tuned configuration of a workload comes from tuning.json; knobs given on
+    the command line override it; --config default ignores the tuning."""
+    import argparse
+    import bench
+    from paper_2301_01356_gb300 import batch as B
+    tuned = B.load_tuning()["graphs"]["grid4096"]["config"]
+    none = dict(ruler_stride=None, cc_sample=None, chase_chains=None, cc_local=None, lcc_sample=None)
+    a = argparse.Namespace(config="tuned", workload="grid4096", **none)
+    cfg = bench.tuned_config(a)
+    assert all(cfg[k] == v for k, v in tuned.items())
+    a = argparse.Namespace(config="tuned", workload="grid4096", **dict(none, ruler_stride=8))
+    assert bench.tuned_config(a)["ruler_stride"] == 8
+    a = argparse.Namespace(config="default", workload="grid4096", **none)
+    assert bench.tuned_config(a) == dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0, lcc_sample=0)
+
+
+def test_bucket_summary_groups_chunks():
+    """The batch line reports one entry per size bucket, with its chunk count."""
+    import types
+    import numpy as np
+    import bench
+
+    def chunk(bucket, sizes, cfg):
+        sub = types.SimpleNamespace(sizes=lambda s=np.array(sizes): s)
+        return types.SimpleNamespace(bucket=bucket, sub=sub, cfg=cfg)
+    runner = types.SimpleNamespace(buckets=[chunk(0, [1000, 5000], {"a": 1}), chunk(2, [200000], {"b": 2}),
+                                            chunk(2, [900000, 150000], {"b": 2})])
+    out = bench.bucket_summary(runner)
+    assert out == [{"n_range": [1000, 5000], "graphs": 2, "chunks": 1, "config": {"a": 1}},
+                   {"n_range": [150000, 900000], "graphs": 3, "chunks": 2, "config": {"b": 2}}]
