@@ -21,6 +21,7 @@ import ctypes
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -192,9 +193,24 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
     return table.get(kernel)
 
 
+def kernel_source_hash(path: str, kernel: str) -> str | None:
+    """Hash of one kernel's definition (its template line, signature and body) in a
+    CUDA source file, so that edits elsewhere in the file leave it unchanged."""
+    try:
+        src = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"^(template <[^\n]*>\n)?__global__[^\n]*\b" + re.escape(kernel) + r"\(", src, re.M)
+    end = src.find("\n}\n", m.start()) if m else -1
+    if end < 0:
+        return None
+    return hashlib.sha1(src[m.start():end + 3].encode()).hexdigest()[:12]
+
+
 def load_traffic(kernel: str, workload: str):
     """dram bytes per launch from the committed ncu summary, or None when absent
-    or when the kernel's source changed since the capture."""
+    or when the kernel's definition changed since the capture (with func=, the
+    hash covers that kernel's source text; without, the whole file)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -202,7 +218,11 @@ def load_traffic(kernel: str, workload: str):
         kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
         if kv.get("kernel") == kernel and kv.get("workload") == workload:
             src = os.path.join(ROOT, "paper_2301_01356_gb300", "csrc", kv.get("file", ""))
-            if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] != kv.get("sha"):
+            if "func" in kv:
+                now = kernel_source_hash(src, kv["func"])
+            else:
+                now = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] if os.path.exists(src) else None
+            if now is None or now != kv.get("sha"):
                 return None
             return int(float(kv["bytes_per_launch"]))
     return None

@@ -502,7 +502,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_preorder(int64_t n2, const int2
     while (true) {
         int64_t t = scan_ticket(ticket);
         if (t >= ntiles) return;
-        const int64_t p0 = t * kTile + (int64_t)threadIdx.x * kItems;
 #pragma unroll
         for (int k = 0; k < kItems; ++k) {
             const int e = k * kThreads + threadIdx.x;

@@ -125,6 +125,28 @@ def test_clock_sampler_parses_reasons():
     assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
 
 
+def test_traffic_is_tied_to_the_kernel_definition(tmp_path, monkeypatch):
+    """With func=, the figure stays valid while only other code in the file changes,
+    and is dropped once the captured kernel's own text changes."""
+    import bench
+    src = tmp_path / "paper_2301_01356_gb300" / "csrc"
+    src.mkdir(parents=True)
+    body = ("template <int K>\n__global__ void __launch_bounds__(256) k_x(int *a)\n{\n    a[0] = K;\n}\n"
+            "\n__global__ void k_y(int *a)\n{\n    a[1] = 2;\n}\n")
+    (src / "k.cu").write_text(body)
+    sha = bench.kernel_source_hash(str(src / "k.cu"), "k_x")
+    assert sha and sha != bench.kernel_source_hash(str(src / "k.cu"), "k_y")
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        f"kernel=k_x workload=w bytes_per_launch=77 file=k.cu func=k_x sha={sha} source=test\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic("k_x", "w") == 77
+    (src / "k.cu").write_text(body.replace("a[1] = 2", "a[1] = 3") + "// a comment\n")
+    assert bench.load_traffic("k_x", "w") == 77
+    (src / "k.cu").write_text(body.replace("a[0] = K", "a[0] = K + 1"))
+    assert bench.load_traffic("k_x", "w") is None
+
+
 def test_traffic_is_dropped_when_the_source_changes(tmp_path, monkeypatch):
     """The committed DRAM traffic counts only for the exact source file it was
     captured from (a hash of the file sits beside the figure)."""
