@@ -463,10 +463,10 @@ def run_gpu(args, world, rank, local):
     h2d = h_off.nbytes + h_adj.nbytes
     d2h = h_eb.nbytes + h_br.nbytes + h_ap.nbytes + h_bh.nbytes
 
-    # parity of the benchmarked configuration and the CPU baseline (rank 0 only)
+    # parity of the benchmarked configuration and the CPU baseline (one rank, N = 1 only)
     cpu = None
     parity = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         sample, sdesc = cpu_sample(args.workload, g)
         exp, cpu_s = cpu_baseline(sample)
         if sample is g:
@@ -645,8 +645,8 @@ def run_batch(args, world, rank, local):
     h2d = sum(lo.numel() * 4 + la.numel() * 4 for lo, la in h_in)
     d2h = sum(eb.numel() * 4 + br.numel() + ap.numel() + sb.numel() * 8 for eb, br, ap, sb in h_out)
 
-    parity = cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    parity = cpu = None   # oracle parity and the CPU baseline: one rank, N = 1 only
+    if world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(0)
         sample = rng.choice(bt.G, size=min(48, bt.G), replace=False)
         ok = True
