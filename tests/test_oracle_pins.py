@@ -233,3 +233,55 @@ def test_rejects_bad_input(oracle):
     bad = adj.copy(); bad[0] = 9                         # id out of range
     assert oracle.check_csr(off, bad) == 1
     assert oracle.check_csr(off, adj) == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_against_networkx(oracle, seed):
+    """An independent library (networkx: biconnected_component_edges,
+    articulation_points, bridges) on medium graphs of every family. The oracle's
+    per-edge labels must induce the same partition of the edges, its canonical
+    numbering must follow smallest edge id, and each block's head must be the
+    block's vertex nearest to its component's smallest vertex (BFS depth), which
+    is unique for a block."""
+    nx = pytest.importorskip("networkx")
+    g = [gg.uniform(1500, 2600, seed), gg.grid(40, 45, p=0.62, seed=seed),
+         gg.cycle_chain(1800, 10, 3, 120, seed), gg.knn3(1500, 3, seed),
+         gg.disjoint_union(gg.uniform(300, 500, seed), gg.grid(20, 20, p=0.7, seed=seed), gg.from_edges(4, [], [])),
+         gg.uniform(800, 4000, seed)][seed]
+    r = oracle.solve(g.offsets, g.adj)
+    src = _arc_src(g)
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    G.add_edges_from((int(s), int(d)) for s, d in zip(src, g.adj) if s < d)
+    eid = {}
+    for i, (s, d) in enumerate((int(s), int(d)) for s, d in zip(src, g.adj) if s < d):
+        eid[(s, d)] = i
+    # partition of the edges, named by smallest edge id, ranked
+    blocks = [sorted(eid[(min(a, b), max(a, b))] for a, b in comp) for comp in nx.biconnected_component_edges(G)]
+    blocks.sort(key=lambda b: b[0])
+    lab = {}
+    for k, b in enumerate(blocks):
+        for e in b:
+            lab[e] = k
+    ids = _edge_ids(g)
+    assert r["n_bcc"] == len(blocks)
+    assert all(int(r["edge_bcc"][a]) == lab[int(ids[a])] for a in range(g.nnz))
+    # articulation points and bridges
+    ap = np.zeros(g.n, np.uint8)
+    ap[list(nx.articulation_points(G))] = 1
+    assert np.array_equal(r["is_ap"], ap)
+    br = {eid[(min(a, b), max(a, b))] for a, b in nx.bridges(G)}
+    assert all(bool(r["is_bridge"][a]) == (int(ids[a]) in br) for a in range(g.nnz))
+    assert r["n_cc"] == nx.number_connected_components(G)
+    # heads: the block's vertex nearest to the component's smallest vertex
+    depth = {}
+    for comp in nx.connected_components(G):
+        depth.update(nx.single_source_shortest_path_length(G, min(comp)))
+    for k, b in enumerate(blocks):
+        verts = set()
+        for e in b:
+            a = int(np.nonzero(ids == e)[0][0])
+            verts.update((int(src[a]), int(g.adj[a])))
+        dmin = min(depth[v] for v in verts)
+        near = [v for v in verts if depth[v] == dmin]
+        assert len(near) == 1 and int(r["bcc_head"][k]) == near[0], k
