@@ -1,6 +1,5 @@
 """The C-ABI library loads on a machine without a GPU and exports every entry
 point include/fbcc.h declares (no compute call is made here)."""
-import ctypes
 import os
 import re
 
