@@ -7,9 +7,12 @@ undirected edges per second. Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl fbcc|reference]
 
-Workloads: grid4096 (default; the large-diameter road-like graph: 4096x4096
-open grid, edges kept with p = 0.62, plus 0.1 % short-range extra edges),
-uniform64k, rmat24. `--impl reference` times the CPU Hopcroft-Tarjan oracle (the
+Workloads: rmat24 (default; the low-diameter power-law graph, R-MAT scale 24,
+edge factor 16, the largest single graph), grid4096 (the large-diameter road-like
+graph: 4096x4096 open grid, edges kept with p = 0.62, plus 0.1 % short-range
+extra edges), uniform64k (the small launch-bound graph), batch (4,096 graphs per
+step through the bucketed batched form), serve (the continuous-batching server
+on a Poisson stream). `--impl reference` times the CPU Hopcroft-Tarjan oracle (the
 only reference that exists for this method) on the same metric and workload.
 The GPU path is replicated per rank (the problem does not shard): N ranks each
 solve their own copy and the value is the whole job's edges per second.
@@ -140,56 +143,65 @@ class ClockSampler:
 # roofline: algorithmic bytes per launch of each kernel
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, stride: int) -> int | None:
-    """Bytes the method must move in one launch of `kernel`: every array the kernel
-    needs counted once, gathers at element size (derivations in the design doc)."""
-    A = 2 * (n - n_cc)                 # tree arcs
-    nr = n_cc + A // stride            # rulers (upper estimate)
-    B = off_bytes
+# Algorithm 1's steps as the profiled kernels run them: a phase starts at its first
+# kernel and lasts until the next phase starts.
+PHASES = ("first_cc", "rooting", "tagging", "last_cc", "outputs")
+PHASE_START = {"k_link": "rooting", "k_first_of": "tagging", "k_ext_compact": "last_cc", "k_ap_keys": "outputs"}
+
+
+def phase_bytes(n: int, nnz: int, n_cc: int, off_bytes: int) -> dict:
+    """Algorithmic bytes the method must move per phase of one solve: each array a
+    phase needs counted once, gathers at element size, the offsets (B bytes each)
+    and the adjacency (4 bytes per arc) once per arc pass. A = 2 (n - #CC) tree arcs.
+      First-CC   B n + 4 nnz + 16 n     (adjacency, parent read/write, forest record)
+      Rooting    48 A + 16 n            (per tree arc: build 16, link 8, rank 8, scan and
+                                         scatter 16; first, last, parent, size)
+      Tagging    B n + 4 nnz + 40 n     (w1/w2 write, RMQ build read, query reads and writes)
+      Last-CC    B n + 4 nnz + 28 n     (five tags, union-find)
+      Outputs    B n + 9 nnz + 12 n     (adjacency, edge_bcc and is_bridge written, per vertex)"""
+    A, B = 2 * (n - n_cc), off_bytes
+    return {"first_cc": B * n + 4 * nnz + 16 * n, "rooting": 48 * A + 16 * n,
+            "tagging": B * n + 4 * nnz + 40 * n, "last_cc": B * n + 4 * nnz + 28 * n,
+            "outputs": B * n + 9 * nnz + 12 * n}
+
+
+def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, stride: int = 0) -> int | None:
+    """The share of its phase's algorithmic bytes (phase_bytes) that one launch of
+    `kernel` moves: the arc pass of a phase takes the offsets, the adjacency and the
+    per-arc outputs, the other kernels the per-vertex and per-tree-arc terms they
+    read or write; kernels that only reshape data the method does not ask for take
+    none. `stride` is unused (kept for callers)."""
+    A, B = 2 * (n - n_cc), off_bytes
+    arc_cc = B * n + 4 * nnz + 8 * n            # a First-CC arc pass: adjacency plus the forest record
     table = {
-        "k_cc_init": B * (n + 1) + 8 * n,
-        "k_cc_hook": B * (n + 1) + 4 * nnz + 2 * nnz + 8 * (n - n_cc),
-        "k_uf_compress": 8 * n,
-        "k_link": 12 * n + 4 * A,
-        "k_succ_rulers": 32 * n + 4 * A + 5 * nr,
-        "k_chase": 16 * A + 16 * nr,
-        "k_jump": 24 * nr,
-        "k_place_records": 30 * A,
-        "k_comp_size": 4 * n + 68 * n_cc,
-        "k_preorder": 16 * n + 28 * n,
-        "k_first_of": 12 * n,
-        "k_w12": B * (n + 1) + 4 * nnz + 4 * nnz + nnz // 8 + 8 * n,
-        "k_rmq_prefix": 16 * n,
-        "k_iota": 4 * n,
-        "k_rmq_query": 41 * n,
-        "k_last_cc_cross": B * (n + 1) + nnz // 8 + (4 * nnz + 8 * nnz) // 2 + 12 * n,
-        "k_ap_keys": 17 * n,
-        "k_key_bits": 20 * n,
-        "k_scan_popc": nnz // 4,
-        "k_rank": 20 * n,
-        "k_fo": 21 * n,
-        "k_edge_out": B * (n + 1) + 4 * nnz + nnz // 8 + 4 * nnz // 2 + 4 * n + 4 * nnz + nnz,
-        "k_cc_local": B * (n + 1) + 4 * nnz + 12 * n,
-        "k_cc_hook_cross": B * (n + 1) + 4 * nnz + 8 * n,
-        "k_rulers2": 17 * nr,
-        "k_chase2": 20 * nr,
-        "k_expand2": 28 * nr,
-        "k_ext_compact": n,
-        "k_ext_halve": 12 * (n // 64),
-        "k_ext_finish": 12 * (n // 64),
-        "k_plain_label": 20 * n,
-        "k_final_label": 28 * n,
-        "k_lcc_sample": B * (n + 1) + 16 * n + 24 * n,
-        "k_pos_compress": 8 * n,
-        "k_last_cc_cross_skip": B * (n + 1) + 4 * nnz + nnz // 8 + 16 * n,
-        # sampled variants (two sampled neighbours per vertex) and the key scan
-        # (offsets and selection flags; the scanned lists are few)
-        "k_cc_sample": B * (n + 1) + 8 * n + 8 * n,
-        "k_mark_big": 4 * n + n // 8,
-        "k_cc_hook_skip": B * (n + 1) + 4 * nnz + 8 * n,
-        "k_key_scan": B * (n + 1) + n,
+        # First-CC
+        "k_cc_init": 4 * n, "k_uf_compress": 4 * n,
+        "k_cc_hook": arc_cc, "k_cc_local": arc_cc, "k_cc_hook_skip": arc_cc, "k_cc_hook_cross": 0,
+        "k_cc_sample": 0, "k_mark_big": 0, "k_cc_pick_big": 0,
+        # Rooting
+        "k_link": 8 * A, "k_succ_rulers": 16 * A, "k_chase": 8 * A, "k_lvl_rulers": 0, "k_lvl_chase": 0,
+        "k_top": 0, "k_lvl_expand": 0, "k_comp_size": 0, "k_place_records": 8 * A, "k_preorder": 8 * A + 16 * n,
+        # Tagging
+        "k_first_of": 0, "k_w12": B * n + 4 * nnz + 8 * n, "k_rmq_prefix": 8 * n, "k_rmq_level": 0,
+        "k_rmq_query": 24 * n,
+        # Last-CC
+        "k_ext_compact": 0, "k_ext_halve": 0, "k_ext_finish": 0, "k_plain_label": 0,
+        "k_last_cc_cross": B * n + 4 * nnz + 20 * n, "k_last_cc_cross_skip": B * n + 4 * nnz + 20 * n,
+        "k_lcc_sample": 0, "k_pos_compress": 0, "k_pos_pick_big": 0, "k_final_label": 8 * n,
+        # Outputs
+        "k_ap_keys": 12 * n, "k_key_adj": 0, "k_key_scan": 0, "k_key_bits": 0, "k_scan_popc": 0, "k_rank": 0, "k_fo": 0,
+        "k_edge_out": B * n + 9 * nnz, "k_bcc_base": 0, "k_batch_stats": 0, "k_finish": 0,
     }
     return table.get(kernel)
+
+
+def phases_of(rows) -> list:
+    """The phase of every row of a profiled solve's [(kernel, ms)] launch list."""
+    cur, out = PHASES[0], []
+    for name, _ in rows:
+        cur = PHASE_START.get(name, cur)
+        out.append(cur)
+    return out
 
 
 def kernel_source_hash(path: str, kernel: str) -> str | None:
@@ -331,6 +343,30 @@ def cpu_baseline(g, runs: int = 3):
     return res, statistics.median(ts)
 
 
+def roofline_line(kernels: dict, phase_ms: dict, n: int, nnz: int, n_cc: int, off_bytes: int,
+                  ms_per_step: float, workload: str) -> dict:
+    """The dominant kernel against the measured copy bandwidth (its algorithmic bytes
+    per launch over its CUDA-event launch time), the whole solve (the phases' bytes
+    over the timed step) and every phase (its bytes over its kernels' event times)."""
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    peak, peak_kind = measured_peak_gbs()
+    ab = algorithmic_bytes(dom, n, nnz, n_cc, off_bytes)
+    achieved = ab / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9 if ab else None
+    pb = phase_bytes(n, nnz, n_cc, off_bytes)
+    solve_b = sum(pb.values())
+    phases = {}
+    for ph in PHASES:
+        ms = phase_ms.get(ph, 0.0)
+        gbs = pb[ph] / (ms / 1e3) / 1e9 if ms > 0 else None
+        phases[ph] = {"ms": round(ms, 4), "bytes": pb[ph], "gbs": gbs, "frac": gbs / peak if gbs else None}
+    solve_gbs = solve_b / (ms_per_step / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": load_traffic(dom, workload),
+            "algorithmic_bytes_per_launch": ab, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "ms_per_launch": kernels[dom]["ms_per_launch"],
+            "solve_bytes": solve_b, "solve_gbs": solve_gbs, "solve_frac": solve_gbs / peak, "phases": phases}
+
+
 def run_gpu(args, world, rank, local):
     import torch
     from paper_2301_01356_gb300 import fbcc
@@ -387,27 +423,23 @@ def run_gpu(args, world, rank, local):
     # per-kernel times (profiled solves: an event after every kernel)
     solver.configure(profile=1, **cfg)
     prof = {}
+    phase_ms = dict.fromkeys(PHASES, 0.0)
     launches_per_step = 0
     for _ in range(args.profile_steps):
         flush.zero_()
         solver.enqueue(off, adj)
         rows = fbcc.fbcc_profile(solver.ws)
         launches_per_step = len(rows)
-        for name, ms in rows:
+        for (name, ms), ph in zip(rows, phases_of(rows)):
             tot, cnt = prof.get(name, (0.0, 0))
             prof[name] = (tot + ms, cnt + 1)
+            phase_ms[ph] += ms / args.profile_steps
     torch.cuda.synchronize()
     solver.configure(**cfg)
     kernels = {k: {"ms_per_step": t / args.profile_steps, "launches_per_step": c // args.profile_steps,
                    "ms_per_launch": t / c} for k, (t, c) in prof.items()}
-    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
-    peak, peak_kind = measured_peak_gbs()
-    ab = algorithmic_bytes(dom, n, nnz, st["n_cc"], off_np.itemsize, cfg["ruler_stride"])
-    achieved = ab / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9 if ab else None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": load_traffic(dom, args.workload),
-                "algorithmic_bytes_per_launch": ab, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "ms_per_launch": kernels[dom]["ms_per_launch"]}
+    roofline = roofline_line(kernels, phase_ms, n, nnz, st["n_cc"], off_np.itemsize, max_s * 1e3 / args.steps,
+                             args.workload)
 
     # end to end through the public host API: pinned host in, pinned host out
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
@@ -602,16 +634,16 @@ def run_batch(args, world, rank, local):
     for name, ms in rows:
         t, c = prof.get(name, (0.0, 0))
         prof[name] = (t + ms, c + 1)
-    dom = max(prof, key=lambda k: prof[k][0])
+    phase_ms = dict.fromkeys(PHASES, 0.0)
+    for (name, ms), ph in zip(rows, phases_of(rows)):
+        phase_ms[ph] += ms
     n_cc_big = int(runner.stats()[big.idx, 3].sum())
-    ab = algorithmic_bytes(dom, big.sub.n_total, big.sub.nnz_total, n_cc_big, 8, big.cfg.get("ruler_stride", 16))
-    dom_ms = prof[dom][0] / prof[dom][1]
-    peak, peak_kind = measured_peak_gbs()
-    achieved = ab / (dom_ms / 1e3) / 1e9 if ab else None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
-                "algorithmic_bytes_per_launch": ab, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "ms_per_launch": dom_ms, "chunk_vertices": big.sub.n_total}
+    kernels = {k: {"ms_per_step": t, "ms_per_launch": t / c} for k, (t, c) in prof.items()}
+    roofline = roofline_line(kernels, phase_ms, big.sub.n_total, big.sub.nnz_total, n_cc_big, 8,
+                             sum(phase_ms.values()), "batch")
+    roofline["traffic"] = None
+    roofline["chunk_vertices"] = big.sub.n_total
+    roofline["solve_basis"] = "the largest chunk's profiled solve (its kernels' event times)"
 
     # end to end: packed inputs from pinned host memory, outputs back to pinned host memory
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -619,7 +651,8 @@ def run_batch(args, world, rank, local):
     h_out = [(torch.empty(b.edge_bcc.shape, dtype=torch.int32).pin_memory(),
               torch.empty(b.is_bridge.shape, dtype=torch.uint8).pin_memory(),
               torch.empty(b.is_ap.shape, dtype=torch.uint8).pin_memory(),
-              torch.empty(b.stats.shape, dtype=torch.int64).pin_memory()) for b in runner.buckets]
+              torch.empty(b.stats.shape, dtype=torch.int64).pin_memory(),
+              torch.empty(b.bcc_head.shape, dtype=torch.int32).pin_memory()) for b in runner.buckets]
     e2e_ts = []
     for _ in range(max(2, args.steps // 4)):
         torch.cuda.synchronize()
@@ -627,7 +660,7 @@ def run_batch(args, world, rank, local):
         # each chunk copies in, solves and copies out on its own stream, so one
         # chunk's copies overlap the others' kernels
         cur = torch.cuda.current_stream()
-        for b, (lo, la), (eb, br, ap, sb) in zip(runner.buckets, h_in, h_out):
+        for b, (lo, la), (eb, br, ap, sb, bh) in zip(runner.buckets, h_in, h_out):
             b.stream.wait_stream(cur)
             with torch.cuda.stream(b.stream):
                 b.loff.copy_(lo, non_blocking=True)
@@ -638,11 +671,13 @@ def run_batch(args, world, rank, local):
                 br.copy_(b.is_bridge, non_blocking=True)
                 ap.copy_(b.is_ap, non_blocking=True)
                 sb.copy_(b.stats, non_blocking=True)
+                bh.copy_(b.bcc_head, non_blocking=True)   # all n entries: n_bcc is not known yet
         torch.cuda.synchronize()
         e2e_ts.append(time.perf_counter() - t1)
     e2e_s = statistics.median(e2e_ts)
     h2d = sum(lo.numel() * 4 + la.numel() * 4 for lo, la in h_in)
-    d2h = sum(eb.numel() * 4 + br.numel() + ap.numel() + sb.numel() * 8 for eb, br, ap, sb in h_out)
+    d2h = sum(eb.numel() * 4 + br.numel() + ap.numel() + sb.numel() * 8 + bh.numel() * 4
+              for eb, br, ap, sb, bh in h_out)
 
     parity = cpu = None   # oracle parity and the CPU baseline: one rank, N = 1 only
     if world == 1 and not args.no_cpu_baseline:
@@ -693,7 +728,9 @@ def run_batch(args, world, rank, local):
 
 
 def run_serve(args, world, rank, local):
-    """Config 5: Poisson arrivals, continuous batching, p50/p99 latency."""
+    """Config 5: Poisson arrivals, continuous batching, p50/p99 latency; then the
+    same kind of requests all at once (the server's saturation throughput) and one
+    at a time through the plain form (the per-request loop it must beat)."""
     import torch
     from paper_2301_01356_gb300 import fbcc, serving
 
@@ -702,27 +739,30 @@ def run_serve(args, world, rank, local):
     graphs = serving.make_pool(args.pool, 5, nmax_knn=args.knn_max)
     gen_s = time.perf_counter() - t0
     pool = serving.Pool(torch, graphs)
-    srv = serving.Server(pool, slots=args.slots, hbm_budget=150 << 30)
+    srv = serving.Server(pool, streams=args.streams, hbm_budget=150 << 30)
     arrivals = serving.poisson_arrivals(args.rate, args.serve_seconds, 5)
     ids = np.random.default_rng(5).integers(0, len(graphs), size=arrivals.size)
-    # warm-up: a short burst (first batches allocate the batch staging buffers)
-    wa = serving.poisson_arrivals(args.rate, 0.5, 6)
+    # warm-up: every pool graph once (their CSRs become resident) and a short burst
+    srv.run(np.zeros(len(graphs)), np.arange(len(graphs)))
+    wa = serving.poisson_arrivals(args.rate, 1.0, 6)
     srv.run(wa, np.random.default_rng(6).integers(0, len(graphs), size=wa.size))
     sampler = ClockSampler(local)
     sampler.start()
     rep = srv.run(arrivals, ids)
     clocks = sampler.stop()
+    # saturation: the first requests of the stream all at once
+    k = min(arrivals.size, args.saturation_requests)
+    sat = srv.run(np.zeros(k), ids[:k])
     srv.close()
+    loop = serving.per_request_loop(pool, ids[:min(k, args.loop_requests)])
     # each pool graph alone (plain form) vs in the mix: a verification run keeping outputs
     check = None
     if rank == 0:
-        vsrv = serving.Server(pool, slots=args.slots, keep_outputs=True)
+        vsrv = serving.Server(pool, streams=args.streams, keep_outputs=True)
         va = serving.poisson_arrivals(args.rate, min(1.0, args.serve_seconds), 7)
         vids = np.random.default_rng(7).integers(0, len(graphs), size=va.size)
         vsrv.run(va, vids)
-        n_max = int(pool.n.max())
-        z_max = int(pool.nnz.max())
-        alone = fbcc.Solver(n_max, z_max)
+        alone = fbcc.Solver(int(pool.n.max()), int(pool.nnz.max()))
         solo = {}
         ok = True
         for r, out in vsrv.outputs.items():
@@ -730,7 +770,7 @@ def run_serve(args, world, rank, local):
             if g not in solo:
                 x = graphs[g]
                 solo[g] = alone.solve(torch.from_numpy(x.offsets).cuda(), torch.from_numpy(x.adj).cuda())
-            ok &= all(np.array_equal(np.asarray(out[k]), np.asarray(solo[g][k])) for k in
+            ok &= all(np.array_equal(np.asarray(out[k2]), np.asarray(solo[g][k2])) for k2 in
                       ("edge_bcc", "bcc_head", "is_ap", "is_bridge", "n_bcc", "n_ap", "n_bridge", "n_cc"))
         alone.close()
         vsrv.close()
@@ -741,9 +781,17 @@ def run_serve(args, world, rank, local):
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"serve: Poisson {args.rate:g} req/s for {args.serve_seconds:g} s over a pool of "
                                f"{len(graphs)} graphs (config-4 families on [1e3, 1e6] and k-NN k=5 on "
-                               f"[1e4, {args.knn_max:.0e}]), continuous batching, {rep['slots']} slots, "
-                               "HBM budget 150 GB", "pool_generate_s": round(gen_s, 1)},
-        "serving": rep, "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "mix_vs_alone": check, "clocks": clocks,
+                               f"[1e4, {args.knn_max:.0e}]), continuous batching on {args.streams} streams, "
+                               "admission by HBM footprint within 150 GB, resident CSRs",
+                   "pool_generate_s": round(gen_s, 1)},
+        "serving": rep, "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"],
+        "saturation": {"requests": sat["requests"], "graphs_per_s": sat["completed_per_s"],
+                       "edges_per_s": sat["edges_per_s"], "mean_batch": sat["mean_batch"]},
+        "per_request_loop": {"requests": loop["requests"], "graphs_per_s": loop["graphs_per_s"],
+                             "edges_per_s": loop["edges_per_s"],
+                             "api": "fbcc_solve per request on its resident CSR, outputs to pinned host memory"},
+        "serving_vs_loop_graphs_per_s": sat["completed_per_s"] / loop["graphs_per_s"],
+        "mix_vs_alone": check, "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -754,14 +802,17 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="grid4096", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs in --workload batch")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle time budget of the batch baseline")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve: length of the arrival stream")
     ap.add_argument("--pool", type=int, default=128, help="serve: graphs in the request pool")
     ap.add_argument("--knn-max", type=float, default=1e7, help="serve: largest k-NN graph in the pool")
-    ap.add_argument("--slots", type=int, default=6, help="serve: batches in flight")
+    ap.add_argument("--streams", type=int, default=4, help="serve: batches in flight (one stream each)")
+    ap.add_argument("--saturation-requests", type=int, default=4000,
+                    help="serve: requests of the all-at-once saturation run")
+    ap.add_argument("--loop-requests", type=int, default=1000, help="serve: requests of the per-request loop")
     ap.add_argument("--impl", default="fbcc", choices=("fbcc", "reference"))
     ap.add_argument("--config", default="tuned", choices=("tuned", "default"),
                     help="start from the autotuner's table (paper_2301_01356_gb300/tuning.json) or the defaults")

@@ -80,14 +80,39 @@ typedef struct {
     int32_t lcc_sample;    /* Last-CC: cross edges per vertex united before the full pass (0 = off) */
 } fbcc_config;
 
-/* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds. */
+/* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds.
+ * The workspace is the algorithm's auxiliary space, which section 4.3 (cost
+ * bounds, the theorem's space part) bounds by O(n) beyond the input: every tag
+ * and union-find array is per vertex; the per-arc part is one direction bit and
+ * a 4-byte index per 256 arcs (about 132 bytes per vertex plus 0.14 per arc).
+ * Used for admission by HBM footprint. No device call; never fails. */
 size_t fbcc_workspace_bytes(int64_t n, int64_t nnz);
 
-/* Allocate a workspace for graphs with n <= n_max and 2m <= nnz_max.
- * Returns FBCC_OK and *ws, FBCC_E_INVALID for bad sizes, FBCC_E_OOM or FBCC_E_CUDA. */
+/* Allocate a workspace (one cudaMalloc of fbcc_workspace_bytes(n_max, nnz_max)
+ * bytes, plus a private capture stream) for graphs with n <= n_max and
+ * 2m <= nnz_max: the O(n) auxiliary space of section 4.3. The library owns it
+ * until fbcc_workspace_destroy. Returns FBCC_OK and *ws, FBCC_E_INVALID for bad
+ * sizes (n_max >= 2^30, nnz_max >= 2^40, negative, ws NULL), FBCC_E_OOM or
+ * FBCC_E_CUDA (*ws is then NULL). */
 fbcc_status fbcc_workspace_create(int64_t n_max, int64_t nnz_max, fbcc_workspace **ws);
 
-/* Release a workspace (synchronises the device first). NULL is ignored. */
+/* A workspace carved from device memory the caller owns (for callers that pool
+ * device memory themselves, e.g. a server admitting requests by HBM footprint):
+ * `mem` (256-byte aligned) holds at least fbcc_batch_workspace_bytes(n_max,
+ * nnz_max, max_graphs) bytes when max_graphs > 0 (fbcc_solve_batch of up to
+ * max_graphs graphs), else fbcc_workspace_bytes(n_max, nnz_max). The library
+ * allocates no device memory for it: fbcc_solve and fbcc_solve_batch run in
+ * `mem`; fbcc_solve_host / _async, which need staging of their own, return
+ * FBCC_E_INVALID on it, and fbcc_solve_batch returns FBCC_E_WORKSPACE for more
+ * than max_graphs graphs. The memory must outlive the workspace and every solve
+ * on it; fbcc_workspace_destroy releases only the library's host-side state and
+ * does not synchronise. Returns FBCC_E_INVALID (NULL, unaligned or bad sizes) or
+ * FBCC_E_WORKSPACE (bytes too small). Same O(n) auxiliary space as above. */
+fbcc_status fbcc_workspace_create_in(void *mem, size_t bytes, int64_t n_max, int64_t nnz_max, int32_t max_graphs,
+                                     fbcc_workspace **ws);
+
+/* Release a workspace (synchronises the device first, unless it lives in caller
+ * memory). NULL is ignored. */
 void fbcc_workspace_destroy(fbcc_workspace *ws);
 
 /* Set tuning knobs of a workspace (copied). NULL restores the defaults. */
@@ -140,8 +165,11 @@ fbcc_status fbcc_solve_host_async(const void *csr_offsets, int offsets_64, const
                                   fbcc_stats *stats, fbcc_workspace *ws, void *stream);
 
 /*
- * Many independent graphs in one call (the graphs are solved together as one
- * disjoint union; every kernel launch covers all of them).
+ * Many independent graphs in one call. Section 4.1 (First-CC) observes that the
+ * connected components of a graph are simply processed in parallel; a batch is
+ * solved as the disjoint union of its graphs, whose components are exactly the
+ * graphs' components, so every kernel launch covers all of them and each graph's
+ * outputs equal those of fbcc_solve on that graph alone (numbered per graph).
  *   vtx_base   device, n_graphs+1 int64: graph g owns global vertices
  *              [vtx_base[g], vtx_base[g+1]); vtx_base[0] = 0, vtx_base[G] = n_total
  *   arc_base   device, n_graphs+1 int64: graph g owns arcs [arc_base[g], arc_base[g+1])
@@ -174,7 +202,8 @@ fbcc_status fbcc_solve_batch(int32_t n_graphs, const int64_t *vtx_base, const in
  *   fbcc_stats (or NULL) filled by a device-to-device copy on `stream`.
  *   Set-up: the first call on each device looks up that device's copy of the
  *   array (cudaGetSymbolAddress) with the device current; make that first call
- *   before any stream capture.
+ *   before any stream capture. The address is cached with the id of the context
+ *   it came from: after a cudaDeviceReset the next call looks it up again.
  *   Sharing: all calls use the same array and every call re-initialises what it
  *   needs; calls that overlap on the GPU (other streams, other threads) race on
  *   it and must be serialised by the caller.
@@ -184,13 +213,53 @@ fbcc_status fbcc_solve_noalloc(const void *csr_offsets, int offsets_64, const in
                                int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
                                fbcc_stats *stats_dev, void *stream);
 
+/*
+ * Biconnectivity queries over the last solve on `ws` (section 3.4, the
+ * space-efficient BCC representation: a label per vertex plus one head per label;
+ * a label's BCC is its class plus its head, section 4.2). They read the
+ * workspace's labels, parents, label ranks and head counts, which stay valid
+ * until the next solve on the same workspace, and answer in the canonical BCC
+ * numbering of that solve's outputs (for a batch: the vertex ids are global,
+ * vtx_base[g] + local id, and the BCC indices are those of the vertex's graph).
+ * The first query after a solve also enqueues a per-head index of the labels
+ * (two O(n) passes). All arrays are device memory, owned by the caller; the calls
+ * are asynchronous on `stream` (order them after the solve, e.g. the same
+ * stream). Returns FBCC_E_INVALID when no solve has run on ws or for a NULL array
+ * with q > 0; vertex ids outside [0, n) are answered as having no BCC.
+ *
+ * fbcc_query_biconnected: bcc[i] = the BCC index that u[i] and v[i] share, or -1
+ *   when they share none (also for u[i] == v[i]); two BCCs share at most one
+ *   vertex, so the answer is unique.
+ */
+fbcc_status fbcc_query_biconnected(fbcc_workspace *ws, const int32_t *u, const int32_t *v, int64_t q,
+                                   int32_t *bcc, void *stream);
+
+/*
+ * fbcc_query_bcc_count: out_off[i] = the number of BCCs holding the vertices
+ *   v[0..i) (exclusive prefix, q+1 entries, int64), out_off[q] = the total; an
+ *   isolated vertex is in none, an articulation point in several. q <= 2 n_max
+ *   (else FBCC_E_WORKSPACE).
+ * fbcc_query_bccs_of: with out_off from fbcc_query_bcc_count on the same v, writes
+ *   the BCC indices of v[i] to out[out_off[i] .. out_off[i+1]) (out holds
+ *   out_off[q] entries): first the BCC of v[i]'s own label (when v[i] is not a
+ *   component root), then those of the labels v[i] heads, in no fixed order.
+ */
+fbcc_status fbcc_query_bcc_count(fbcc_workspace *ws, const int32_t *v, int64_t q, int64_t *out_off, void *stream);
+fbcc_status fbcc_query_bccs_of(fbcc_workspace *ws, const int32_t *v, int64_t q, const int64_t *out_off,
+                               int32_t *out, void *stream);
+
 /* Device bytes fbcc_solve_batch needs beyond the inputs and outputs (for admission). */
 size_t fbcc_batch_workspace_bytes(int64_t n_total, int64_t nnz_total, int32_t n_graphs);
 
 /*
  * Check the graph format on the device: ids in range, lists sorted strictly
  * ascending, no self-loops, every arc has its reverse, offsets monotone with
- * offsets[n] = 2m. Synchronous. Returns FBCC_OK, FBCC_E_INVALID or FBCC_E_NOT_SIMPLE.
+ * offsets[n] = 2m. Section 2 (preliminaries) states the problem on an undirected
+ * graph G = (V, E) with edges x--y and is silent on self-loops and parallel
+ * edges; this library reads the input as a simple graph (the solvers recognise
+ * the tree arc to a parent by its endpoint, which needs simplicity), and this call
+ * is the check of that reading. Synchronous on `stream`. Returns FBCC_OK,
+ * FBCC_E_INVALID (bad sizes, pointers, offsets or ids) or FBCC_E_NOT_SIMPLE.
  */
 fbcc_status fbcc_validate(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
                           int64_t n, int64_t m, fbcc_workspace *ws, void *stream);

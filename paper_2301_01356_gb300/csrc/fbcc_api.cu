@@ -52,6 +52,8 @@ struct Carver {
     }
 };
 
+size_t batch_stage_bytes(int64_t N, int64_t Z, int32_t G);
+
 int64_t st_levels_for(int64_t tiles)
 {
     int64_t l = 1;
@@ -98,17 +100,30 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.rhead = c.take<uint8_t>(d.ruler_max);
     d.link = c.take<int2>(2 * N);
     d.relem = c.take<int32_t>(d.ruler_max);
-    for (int i = 0; i < 2; ++i) {
-        d.rnext[i] = c.take<int32_t>(d.ruler_max);
-        d.rval[i] = c.take<int32_t>(d.ruler_max);
-    }
     d.rlen = c.take<int32_t>(d.ruler_max);
     d.rnx1 = c.take<int32_t>(d.ruler_max);
-    d.l2 = c.take<int2>(d.ruler_max);
-    d.relem2 = c.take<int32_t>(d.ruler_max);
-    d.owner2 = c.take<int32_t>(d.ruler_max);
-    d.offs2 = c.take<int32_t>(d.ruler_max);
     d.sd1 = c.take<int32_t>(d.ruler_max);
+    {
+        // level k holds the heads of the multi-node lists of level k-1 (at most the
+        // stride samples of level k-2) plus one node in kStride2 of level k-1
+        int64_t below = d.ruler_max, below2 = ceil_div(2 * N, kMinStride);
+        for (int k = 0; k < kRankLevels; ++k) {
+            RankLevel &v = d.lv[k];
+            v.cap = below2 + ceil_div(below, kStride2) + 2;
+            v.l = c.take<int2>(below);
+            v.relem = c.take<int32_t>(v.cap);
+            v.owner = c.take<int32_t>(below);
+            v.offs = c.take<int32_t>(below);
+            v.next = c.take<int32_t>(v.cap);
+            v.w = c.take<int32_t>(v.cap);
+            v.head = c.take<uint8_t>(v.cap);
+            v.sd = c.take<int32_t>(v.cap);
+            below2 = ceil_div(below, kStride2);
+            below = v.cap;
+        }
+        d.top_tmp_cap = below;
+        for (int i = 0; i < 4; ++i) d.top_tmp[i] = c.take<int32_t>(below);
+    }
     d.csize = c.take<int32_t>(N + 1);
     d.vbase = c.take<int32_t>(N + 1);
     d.rec = c.take<int2>(2 * N);
@@ -136,11 +151,17 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.smin = c.take<int32_t>(N);
     d.nh = c.take<int32_t>(N);
     d.key = c.take<unsigned long long>(N);
-    d.scanv = c.take<uint8_t>(N);
+    d.scanb = c.take<uint32_t>(ceil_div(N, 32) + 1);
+    d.klist_cap = N + ceil_div(Z, kKeyChunk) + 2;
+    d.klist = c.take<int2>(d.klist_cap);
+    d.kmin = c.take<int32_t>(N);
     d.key_bits = c.take<uint32_t>(words);
     d.key_pre = c.take<int32_t>(words + 1);
     d.rank = c.take<int32_t>(N);
     d.word = c.take<int32_t>(N);
+    d.hoff = c.take<int32_t>(N + 1);
+    d.hfill = c.take<int32_t>(N);
+    d.hlist = c.take<int32_t>(N);
     if (c.used < rooting_end) c.used = rooting_end;
     return c.used + 256;
 }
@@ -162,7 +183,10 @@ struct fbcc_workspace {
     // global offsets/adjacency and per-graph bases of fbcc_solve_batch (first use)
     void *bstage = nullptr;
     size_t bstage_bytes = 0;
+    bool caller_mem = false;   // slab and batch staging are the caller's memory (fbcc_workspace_create_in)
     Prof prof;             // per-kernel events of profiled solves
+    int64_t last_n = -1;   // vertices of the last solve (-1: none yet)
+    bool qindex = false;   // the query index of the last solve has been enqueued
 };
 
 static fbcc_config default_config()
@@ -210,11 +234,45 @@ fbcc_status fbcc_workspace_create(int64_t n_max, int64_t nnz_max, fbcc_workspace
         return cuda_fail(e, "cudaMalloc(workspace)");
     }
     carve(w->d, static_cast<char *>(w->slab), n_max, nnz_max);
-    e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
+    e = prepare_rooting();
     if (e != cudaSuccess) {
         cudaFree(w->slab);
         delete w;
-        return cuda_fail(e, "cudaStreamCreate");
+        return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    *ws = w;
+    return FBCC_OK;
+}
+
+fbcc_status fbcc_workspace_create_in(void *mem, size_t bytes, int64_t n_max, int64_t nnz_max, int32_t max_graphs,
+                                     fbcc_workspace **ws)
+{
+    if (!ws) return FBCC_E_INVALID;
+    *ws = nullptr;
+    if (!mem || ((uintptr_t)mem & 255) || n_max < 0 || nnz_max < 0 || n_max >= (1ll << 30) ||
+        nnz_max >= (1ll << 40) || max_graphs < 0)
+        return FBCC_E_INVALID;
+    Dev probe;
+    // carve() reports the slab's last byte plus 256: the staging starts 256-aligned
+    // below that, and the total never exceeds fbcc_batch_workspace_bytes
+    const size_t wb = carve(probe, nullptr, n_max, nnz_max) & ~size_t(255);
+    const size_t bb = max_graphs > 0 ? batch_stage_bytes(n_max, nnz_max, max_graphs) : 0;
+    if (bytes < wb + bb) return FBCC_E_WORKSPACE;
+    fbcc_workspace *w = new (std::nothrow) fbcc_workspace();
+    if (!w) return FBCC_E_OOM;
+    w->cfg = default_config();
+    w->caller_mem = true;
+    w->slab = mem;
+    w->bytes = wb;
+    carve(w->d, static_cast<char *>(mem), n_max, nnz_max);
+    if (bb) {
+        w->bstage = static_cast<char *>(mem) + wb;
+        w->bstage_bytes = bb;
+    }
+    const cudaError_t e = prepare_rooting();
+    if (e != cudaSuccess) {
+        delete w;
+        return cuda_fail(e, "cudaFuncSetAttribute");
     }
     *ws = w;
     return FBCC_OK;
@@ -223,14 +281,16 @@ fbcc_status fbcc_workspace_create(int64_t n_max, int64_t nnz_max, fbcc_workspace
 void fbcc_workspace_destroy(fbcc_workspace *ws)
 {
     if (!ws) return;
-    cudaDeviceSynchronize();
+    if (!ws->caller_mem) cudaDeviceSynchronize();
     if (ws->exec) cudaGraphExecDestroy(ws->exec);
     if (ws->cap) cudaStreamDestroy(ws->cap);
     if (ws->prof.ready)
         for (int i = 0; i <= kProfMax; ++i) cudaEventDestroy(ws->prof.ev[i]);
-    cudaFree(ws->slab);
-    cudaFree(ws->stage);
-    cudaFree(ws->bstage);
+    if (!ws->caller_mem) {
+        cudaFree(ws->slab);
+        cudaFree(ws->stage);
+        cudaFree(ws->bstage);
+    }
     delete ws;
 }
 
@@ -347,7 +407,7 @@ fbcc_status check_args(const void *off, const int32_t *adj, int64_t n, int64_t m
 {
     if (!ws || n < 0 || m < 0) return FBCC_E_INVALID;
     if (n >= (1ll << 30)) return FBCC_E_INVALID;
-    if (n > ws->d.n_max || 2 * m > ws->d.nnz_max) return FBCC_E_WORKSPACE;
+    if (n > ws->d.n_max || m > ws->d.nnz_max / 2) return FBCC_E_WORKSPACE;
     if (m > 0 && n < 2) return FBCC_E_INVALID;
     if (n > 0 && (!off || !is_ap || !bcc_head)) return FBCC_E_INVALID;
     if (m > 0 && (!adj || !edge_bcc || !is_bridge)) return FBCC_E_INVALID;
@@ -372,6 +432,8 @@ fbcc_status solve_device(const void *off, int offsets_64, const int32_t *adj, in
             ? enqueue_solve<int64_t>(ws, (const int64_t *)off, adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, q, B)
             : enqueue_solve<int32_t>(ws, (const int32_t *)off, adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, q, B);
     };
+    ws->last_n = n;
+    ws->qindex = false;
     if (ws->cfg.profile && !ws->prof.ready) {
         for (int i = 0; i <= kProfMax; ++i) API_CK(cudaEventCreate(&ws->prof.ev[i]), "cudaEventCreate");
         ws->prof.ready = true;
@@ -389,6 +451,7 @@ fbcc_status solve_device(const void *off, int offsets_64, const int32_t *adj, in
                 ws->exec = nullptr;
             }
             ws->have_key = false;
+            if (!ws->cap) API_CK(cudaStreamCreateWithFlags(&ws->cap, cudaStreamNonBlocking), "cudaStreamCreate");
             API_CK(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
             cudaError_t e = enqueue(ws->cap);
             cudaGraph_t g = nullptr;
@@ -448,6 +511,7 @@ fbcc_status solve_host(const void *csr_offsets, int offsets_64, const int32_t *c
 {
     fbcc_status st = check_args(csr_offsets, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, ws);
     if (st != FBCC_OK) return st;
+    if (ws->caller_mem) return FBCC_E_INVALID;   // its staging would be an allocation
     const int64_t N = ws->d.n_max, Z = ws->d.nnz_max;
     if (!ws->stage) {
         ws->stage_bytes = size_t(N + 1) * 8 + size_t(Z) * 4 + size_t(Z) * 4 + size_t(N) * 4 + size_t(N) + size_t(Z) + 5 * 256;
@@ -538,7 +602,7 @@ extern "C" fbcc_status fbcc_validate(const void *csr_offsets, int offsets_64, co
                                      int64_t m, fbcc_workspace *ws, void *stream)
 {
     if (!ws || n < 0 || m < 0 || (n > 0 && !csr_offsets) || (m > 0 && !csr_adj)) return FBCC_E_INVALID;
-    if (n > ws->d.n_max || 2 * m > ws->d.nnz_max) return FBCC_E_WORKSPACE;
+    if (n > ws->d.n_max || m > ws->d.nnz_max / 2) return FBCC_E_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     int64_t ends[2] = {0, 0};
     if (n == 0) return m == 0 ? FBCC_OK : FBCC_E_INVALID;
@@ -597,6 +661,7 @@ extern "C" fbcc_status fbcc_solve_batch(int32_t n_graphs, const int64_t *vtx_bas
     if (n > 0 && !local_off) return FBCC_E_INVALID;
     const size_t need = batch_stage_bytes(ws->d.n_max, ws->d.nnz_max, n_graphs);
     if (ws->bstage_bytes < need) {
+        if (ws->caller_mem) return FBCC_E_WORKSPACE;   // more graphs than the memory was carved for
         cudaStreamSynchronize((cudaStream_t)stream);
         cudaFree(ws->bstage);
         ws->bstage = nullptr;
@@ -679,6 +744,57 @@ extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *nam
 }
 
 // ---------------------------------------------------------------------------
+// Biconnectivity queries over the last solve (section 3.4's representation)
+// ---------------------------------------------------------------------------
+namespace {
+
+fbcc_status query_ready(fbcc_workspace *ws, cudaStream_t s)
+{
+    if (!ws || ws->last_n < 0) return FBCC_E_INVALID;
+    if (!ws->qindex) {
+        API_CK(launch_query_index(ws->d, ws->last_n, s), "query index");
+        ws->qindex = true;
+    }
+    return FBCC_OK;
+}
+
+}  // namespace
+
+extern "C" fbcc_status fbcc_query_biconnected(fbcc_workspace *ws, const int32_t *u, const int32_t *v, int64_t q,
+                                              int32_t *bcc, void *stream)
+{
+    if (q < 0 || (q > 0 && (!u || !v || !bcc))) return FBCC_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    fbcc_status st = query_ready(ws, s);
+    if (st != FBCC_OK) return st;
+    API_CK(launch_query_pairs(ws->d, ws->last_n, u, v, q, bcc, device_grid(ws->cfg), s), "k_qpairs");
+    return FBCC_OK;
+}
+
+extern "C" fbcc_status fbcc_query_bcc_count(fbcc_workspace *ws, const int32_t *v, int64_t q, int64_t *out_off,
+                                            void *stream)
+{
+    if (q < 0 || !out_off || (q > 0 && !v)) return FBCC_E_INVALID;
+    if (ws && q > 2 * ws->d.n_max) return FBCC_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    fbcc_status st = query_ready(ws, s);
+    if (st != FBCC_OK) return st;
+    API_CK(launch_query_count(ws->d, ws->last_n, v, q, out_off, device_grid(ws->cfg), s), "k_qcount_scan");
+    return FBCC_OK;
+}
+
+extern "C" fbcc_status fbcc_query_bccs_of(fbcc_workspace *ws, const int32_t *v, int64_t q, const int64_t *out_off,
+                                          int32_t *out, void *stream)
+{
+    if (q < 0 || (q > 0 && (!v || !out_off || !out))) return FBCC_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    fbcc_status st = query_ready(ws, s);
+    if (st != FBCC_OK) return st;
+    API_CK(launch_query_list(ws->d, ws->last_n, v, q, out_off, out, device_grid(ws->cfg), s), "k_qlist");
+    return FBCC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Solve with no allocation at all: the workspace lives in a fixed device array.
 //
 // For callers that must not allocate device memory themselves or through us:
@@ -697,8 +813,42 @@ constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+// The device address of g_noalloc_scratch differs per device and per context (a
+// cudaDeviceReset destroys the primary context, and the module is loaded again
+// into the next one), so it is cached per device together with the id of the
+// context it was looked up in, and looked up again when that id changes.
+struct NoAllocSlot {
+    unsigned long long ctx_id;
+    char *base;
+};
 std::mutex g_noalloc_mu;
-char *g_noalloc_base[kNoAllocMaxDevices];  // device address of g_noalloc_scratch, per device
+NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices];
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Id of the context current on this thread (0 when the driver cannot tell).
+unsigned long long current_ctx_id()
+{
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        looked = true;
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur && get_id && get_cur(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
 
 }  // namespace
 
@@ -707,22 +857,27 @@ extern "C" fbcc_status fbcc_solve_noalloc(const void *csr_offsets, int offsets_6
                                           uint8_t *is_ap, uint8_t *is_bridge, fbcc_stats *stats_dev, void *stream)
 {
     if (n < 0 || m < 0) return FBCC_E_INVALID;
-    if (n > kNoAllocMaxN || 2 * m > kNoAllocMaxNnz) return FBCC_E_WORKSPACE;
+    if (n > kNoAllocMaxN || m > kNoAllocMaxNnz / 2) return FBCC_E_WORKSPACE;
     int dev = 0;
     API_CK(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= kNoAllocMaxDevices) return FBCC_E_INVALID;
+    API_CK(cudaSetDevice(dev), "cudaSetDevice");   // makes the device's primary context current
     char *base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_base[dev]) {
+        const unsigned long long id = current_ctx_id();
+        NoAllocSlot &sl = g_noalloc_slot[dev];
+        if (!sl.base || id == 0 || sl.ctx_id != id) {
             // host code may not use g_noalloc_scratch as an address: ask the runtime
-            // for the device address of this device's copy (once per device)
+            // for the device address of this device's copy in the current context
             void *p = nullptr;
             API_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
-            g_noalloc_base[dev] = static_cast<char *>(p);
+            sl.base = static_cast<char *>(p);
+            sl.ctx_id = id;
         }
-        base = g_noalloc_base[dev];
+        base = sl.base;
     }
+    API_CK(prepare_rooting(), "cudaFuncSetAttribute");
     fbcc_workspace ws;  // host-side view only: no allocation, no stream, no graph
     ws.cfg = default_config();
     ws.cfg.use_graph = -1;

@@ -291,11 +291,13 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
                     if (old == h) {
                         te_u[v0 + h] = (int32_t)(v0 + su[j]);
                         te_v[v0 + h] = dw[j];
+                        ru = rv;   // joined
                         break;
                     }
                     ru = sm_find(par, old);
                     rv = sm_find(par, l);
                 }
+                if (ru != rv) atomicOr(err, kErrUnite);   // the cap ended the retries: the union is lost
             }
         }
         __syncthreads();
@@ -305,7 +307,6 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
             uf[v0 + i] = (int32_t)(v0 + r);
         }
     }
-    (void)err;
 }
 
 // Global hooks of the gathered edges; when the list did not fit, every edge

@@ -236,29 +236,30 @@ __global__ void __launch_bounds__(kThreads) k_chase(int64_t n,
     }
 }
 
-// Level 2 of the ranking: the ruler lists themselves are sampled again. A ruler
-// list of one ruler (a short tour) is finished already (marked -2); the others'
-// heads and every stride2-th ruler become level-2 rulers.
-__global__ void __launch_bounds__(kThreads) k_rulers2(const long long *__restrict__ nr_p, int stride2,
-                                                      const int32_t *__restrict__ relem,
-                                                      const uint8_t *__restrict__ rhead,
-                                                      const int32_t *__restrict__ rnext1, int2 *l2, int32_t *relem2,
-                                                      long long *nr2)
+// One more level of the ranking: the lists of the level below (next_lo, with
+// head flags head_lo) are sampled again. A list of one node (a short tour) is
+// finished already (marked -2); the others' heads and every stride-th node become
+// nodes of this level, which inherit the head flag.
+__global__ void __launch_bounds__(kThreads) k_lvl_rulers(const long long *__restrict__ cnt_lo_p, int stride,
+                                                         const int32_t *__restrict__ next_lo,
+                                                         const uint8_t *__restrict__ head_lo, int2 *l,
+                                                         int32_t *relem, uint8_t *head_up, long long *cnt_up,
+                                                         int64_t cap_up, int *err)
 {
     __shared__ int32_t warp_cnt[kThreads / 32];
     __shared__ long long block_base;
-    const int64_t nr = *nr_p;
+    const int64_t nr = *cnt_lo_p;
     const int64_t pad = (nr + kThreads - 1) / kThreads * kThreads;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t r = blockIdx.x * (int64_t)kThreads + threadIdx.x; r < pad; r += (int64_t)gridDim.x * kThreads) {
         const bool in = r < nr;
-        bool single = false, ruler = false;
+        bool single = false, ruler = false, head = false;
         int32_t nx = -1;
         if (in) {
-            const bool head = rhead[r];
-            nx = rnext1[r];
+            head = head_lo[r];
+            nx = next_lo[r];
             single = head && nx < 0;
-            ruler = !single && (head || (r & (stride2 - 1)) == 0);
+            ruler = !single && (head || (r & (stride - 1)) == 0);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, ruler);
         if (lane == 0) warp_cnt[wid] = __popc(mask);
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_rulers2(const long long *__restric
         if (threadIdx.x == 0) {
             int32_t c = 0;
             for (int w = 0; w < kThreads / 32; ++w) c += warp_cnt[w];
-            block_base = c ? (long long)atomicAdd((unsigned long long *)nr2, (unsigned long long)c) : 0;
+            block_base = c ? (long long)atomicAdd((unsigned long long *)cnt_up, (unsigned long long)c) : 0;
         }
         __syncthreads();
         int32_t before = 0;
@@ -276,73 +277,153 @@ __global__ void __launch_bounds__(kThreads) k_rulers2(const long long *__restric
         if (!in) continue;
         int32_t id = single ? -2 : -1;
         if (ruler) {
-            id = (int32_t)(base + __popc(mask & ((1u << lane) - 1u)));
-            relem2[id] = (int32_t)r;
+            const long long at = base + __popc(mask & ((1u << lane) - 1u));
+            if (in_range(at, cap_up, err)) {
+                id = (int32_t)at;
+                relem[id] = (int32_t)r;
+                head_up[id] = head;
+            }
         }
-        l2[r] = make_int2(nx, id);
+        l[r] = make_int2(nx, id);
     }
 }
 
-// Level-2 walks over the level-1 ruler lists, weighted by segment length.
-__global__ void __launch_bounds__(kThreads) k_chase2(const long long *__restrict__ nr_p,
-                                                     const long long *__restrict__ nr2_p,
-                                                     const int32_t *__restrict__ relem2, const int2 *__restrict__ l2,
-                                                     const int32_t *__restrict__ rw1, int32_t *owner2, int32_t *offs2,
-                                                     int32_t *rnext2, int32_t *rval2, int *err)
+// Walks of this level over the lists below, weighted by the segment weights below:
+// every node below learns its owner here and its weighted offset from it; every
+// node here its next node and its segment weight.
+__global__ void __launch_bounds__(kThreads) k_lvl_chase(const long long *__restrict__ cnt_lo_p,
+                                                        const long long *__restrict__ cnt_up_p,
+                                                        const int32_t *__restrict__ relem, const int2 *__restrict__ l,
+                                                        const int32_t *__restrict__ w_lo, int32_t *owner,
+                                                        int32_t *offs, int32_t *next_up, int32_t *w_up, int *err)
 {
-    const int64_t nr = *nr_p, nr2 = *nr2_p;
+    const int64_t nr = *cnt_lo_p, nr2 = *cnt_up_p;
     GRID_STRIDE(R, nr2)
     {
-        const int32_t r0 = relem2[R];
-        owner2[r0] = (int32_t)R;
-        offs2[r0] = 0;
-        int32_t acc = rw1[r0], nxr = -1;
-        int32_t t = l2[r0].x;
+        const int32_t r0 = relem[R];
+        owner[r0] = (int32_t)R;
+        offs[r0] = 0;
+        int32_t acc = w_lo[r0], nxr = -1;
+        int32_t t = l[r0].x;
         int64_t steps = 0;
         while (t >= 0) {
-            const int2 lk = l2[t];
+            const int2 lk = l[t];
             if (lk.y >= 0) { nxr = lk.y; break; }
-            owner2[t] = (int32_t)R;
-            offs2[t] = acc;
-            acc += rw1[t];
+            owner[t] = (int32_t)R;
+            offs[t] = acc;
+            acc += w_lo[t];
             t = lk.x;
             if (++steps > nr) { atomicOr(err, kErrChase); break; }
         }
-        rnext2[R] = nxr;
-        rval2[R] = acc;
+        next_up[R] = nxr;
+        w_up[R] = acc;
     }
 }
 
-// Suffix weight of every level-1 ruler from the level-2 result.
-__global__ void __launch_bounds__(kThreads) k_expand2(const long long *__restrict__ nr_p, const int2 *__restrict__ l2,
-                                                      const int32_t *__restrict__ rw1,
-                                                      const int32_t *__restrict__ owner2,
-                                                      const int32_t *__restrict__ offs2,
-                                                      const int32_t *__restrict__ sd2, int32_t *sd1)
+// Suffix weights of the nodes below from those of this level.
+__global__ void __launch_bounds__(kThreads) k_lvl_expand(const long long *__restrict__ cnt_lo_p,
+                                                         const int2 *__restrict__ l, const int32_t *__restrict__ w_lo,
+                                                         const int32_t *__restrict__ owner,
+                                                         const int32_t *__restrict__ offs,
+                                                         const int32_t *__restrict__ sd_up, int32_t *sd_lo)
 {
-    const int64_t nr = *nr_p;
+    const int64_t nr = *cnt_lo_p;
     GRID_STRIDE(r, nr)
     {
-        sd1[r] = l2[r].y == -2 ? rw1[r] : sd2[owner2[r]] - offs2[r];
+        sd_lo[r] = l[r].y == -2 ? w_lo[r] : sd_up[owner[r]] - offs[r];
     }
 }
 
-// One pointer-jumping round on the ruler lists: val = suffix weight.
-__global__ void __launch_bounds__(kThreads) k_jump(const long long *__restrict__ nr_p, const int32_t *__restrict__ nx_in,
-                                                   const int32_t *__restrict__ val_in, int32_t *nx_out, int32_t *val_out)
+// The top level: suffix weights of every node by pointer jumping, in one CTA. Up
+// to kTopCap nodes live in shared memory (each round reads every pointer and
+// value, synchronises, writes, and stops when no pointer moved); more nodes take
+// the same rounds over global double buffers.
+__global__ void __launch_bounds__(kTopThreads) k_top(const long long *__restrict__ cnt_p,
+                                                     const int32_t *__restrict__ next, const int32_t *__restrict__ w,
+                                                     int32_t *sd, int32_t *g0n, int32_t *g0v, int32_t *g1n,
+                                                     int32_t *g1v, int64_t gcap, int *err)
 {
-    const int64_t nr = *nr_p;
-    GRID_STRIDE(r, nr)
-    {
-        int32_t x = nx_in[r];
-        if (x >= 0) {
-            val_out[r] = val_in[r] + val_in[x];
-            nx_out[r] = nx_in[x];
-        } else {
-            val_out[r] = val_in[r];
-            nx_out[r] = -1;
+    extern __shared__ __align__(16) int32_t top_smem[];
+    const int64_t cnt = *cnt_p;
+    const int tid = threadIdx.x;
+    if (cnt <= kTopCap) {
+        const int n = (int)cnt;
+        int32_t *s_nx = top_smem, *s_v = top_smem + kTopCap;
+        for (int i = tid; i < n; i += kTopThreads) {
+            s_nx[i] = next[i];
+            s_v[i] = w[i];
         }
+        __syncthreads();
+        bool done = false;
+        for (int round = 0; round < 40 && !done; ++round) {
+            int32_t nn[kTopPer], nv[kTopPer];
+            int moved = 0;
+#pragma unroll
+            for (int k = 0; k < kTopPer; ++k) {
+                const int i = tid + k * kTopThreads;
+                nn[k] = -1;
+                if (i < n) {
+                    const int32_t x = s_nx[i];
+                    nv[k] = s_v[i];
+                    if (x >= 0) {
+                        nv[k] += s_v[x];
+                        nn[k] = s_nx[x];
+                        moved = 1;
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kTopPer; ++k) {
+                const int i = tid + k * kTopThreads;
+                if (i < n) {
+                    s_nx[i] = nn[k];
+                    s_v[i] = nv[k];
+                }
+            }
+            done = !__syncthreads_or(moved);
+        }
+        if (!done && tid == 0) atomicOr(err, kErrChase);
+        for (int i = tid; i < n; i += kTopThreads) sd[i] = s_v[i];
+        return;
     }
+    if (cnt > gcap) {
+        if (tid == 0) atomicOr(err, kErrIndex);
+        return;
+    }
+    const int32_t *rn = next, *rv = w;
+    int32_t *on = g0n, *ov = g0v, *sn = g1n, *sv = g1v;   // written this round, the round after
+    bool done = false;
+    for (int round = 0; round < 40 && !done; ++round) {
+        int moved = 0;
+        for (int64_t i = tid; i < cnt; i += kTopThreads) {
+            const int32_t x = rn[i];
+            int32_t v = rv[i], nx = -1;
+            if (x >= 0) {
+                v += rv[x];
+                nx = rn[x];
+                moved = 1;
+            }
+            on[i] = nx;
+            ov[i] = v;
+        }
+        done = !__syncthreads_or(moved);
+        rn = on;
+        rv = ov;
+        int32_t *tn = on, *tv = ov;
+        on = sn;
+        ov = sv;
+        sn = tn;
+        sv = tv;
+    }
+    if (!done && tid == 0) atomicOr(err, kErrChase);
+    for (int64_t i = tid; i < cnt; i += kTopThreads) sd[i] = rv[i];
+}
+
+cudaError_t prepare_rooting()
+{
+    return cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * kTopCap * sizeof(int32_t)));
 }
 
 // Component size at its root (1 for an isolated root, else tour length / 2 + 1)
@@ -577,7 +658,10 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     // upper bound on the number of rulers: a head per tour (a tour spans at least
     // two vertices) plus one per stride
     const int64_t rbound = n / 2 + ceil_div(2 * n, ruler_stride) + 1;
-    const int gr = grid_for(L, ceil_div(rbound, kThreads));
+    // the walk's grid: one ruler per thread (up to 16 resident waves), so that the
+    // block scheduler balances the long walks
+    const int64_t gwant = ceil_div(ceil_div(rbound, kThreads), chase_chains);
+    const int gr = (int)(gwant < 16ll * L.grid ? (gwant < 1 ? 1 : gwant) : 16ll * L.grid);
     if (chase_chains >= 4)
         k_chase<4><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.rnx1, d.rlen, d.err);
     else if (chase_chains == 2)
@@ -585,26 +669,52 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     else
         k_chase<1><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.rnx1, d.rlen, d.err);
     L.mark("k_chase");
-    long long *nr2 = d.counters + 3;
-    CK(cudaMemsetAsync(nr2, 0, sizeof(long long), L.s));
-    k_rulers2<<<gr, kThreads, 0, L.s>>>(nr, kStride2, d.relem, d.rhead, d.rnx1, d.l2, d.relem2, nr2);
-    L.mark("k_rulers2");
-    // level-2 rulers: heads of lists with several rulers (each holds a stride
-    // sample, so at most 2n / stride of them) plus one in kStride2 rulers
-    const int64_t rbound2 = ceil_div(2 * n, ruler_stride) + ceil_div(rbound, kStride2) + 1;
-    const int gr2 = grid_for(L, ceil_div(rbound2, kThreads));
-    k_chase2<<<gr2, kThreads, 0, L.s>>>(nr, nr2, d.relem2, d.l2, d.rlen, d.owner2, d.offs2, d.rnext[0], d.rval[0],
-                                        d.err);
-    L.mark("k_chase2");
-    int cur = 0;
-    const int rounds = jump_rounds(rbound2);
-    for (int i = 0; i < rounds; ++i) {
-        k_jump<<<gr2, kThreads, 0, L.s>>>(nr2, d.rnext[cur], d.rval[cur], d.rnext[cur ^ 1], d.rval[cur ^ 1]);
-        L.mark("k_jump");
-        cur ^= 1;
+    // Levels above the rulers: each samples the lists below again (heads of lists of
+    // several nodes, at most the stride samples two levels down, plus one node in
+    // kStride2); a third level is added when the second may exceed what one CTA
+    // ranks in shared memory. The top level is ranked by k_top.
+    int64_t bnd[kRankLevels + 1];
+    bnd[0] = rbound;
+    int64_t below2 = ceil_div(2 * n, ruler_stride);
+    int levels = 0;
+    for (int k = 0; k < kRankLevels; ++k) {
+        bnd[k + 1] = below2 + ceil_div(bnd[k], kStride2) + 1;
+        below2 = ceil_div(bnd[k], kStride2);
+        ++levels;
+        if (bnd[k + 1] <= kTopCap) break;
     }
-    k_expand2<<<gr, kThreads, 0, L.s>>>(nr, d.l2, d.rlen, d.owner2, d.offs2, d.rval[cur], d.sd1);
-    L.mark("k_expand2");
+    const long long *cnt[kRankLevels + 1];
+    cnt[0] = nr;
+    const int32_t *next_lo = d.rnx1, *w_lo = d.rlen;
+    const uint8_t *head_lo = d.rhead;
+    for (int k = 0; k < levels; ++k) {
+        const RankLevel &v = d.lv[k];
+        long long *c = d.counters + 11 + k;
+        CK(cudaMemsetAsync(c, 0, sizeof(long long), L.s));
+        k_lvl_rulers<<<grid_for(L, ceil_div(bnd[k], kThreads)), kThreads, 0, L.s>>>(
+            cnt[k], kStride2, next_lo, head_lo, v.l, v.relem, v.head, c, v.cap, d.err);
+        L.mark("k_lvl_rulers");
+        k_lvl_chase<<<grid_for(L, ceil_div(bnd[k + 1], kThreads)), kThreads, 0, L.s>>>(
+            cnt[k], c, v.relem, v.l, w_lo, v.owner, v.offs, v.next, v.w, d.err);
+        L.mark("k_lvl_chase");
+        cnt[k + 1] = c;
+        next_lo = v.next;
+        w_lo = v.w;
+        head_lo = v.head;
+    }
+    const RankLevel &top = d.lv[levels - 1];
+    k_top<<<1, kTopThreads, 2 * kTopCap * sizeof(int32_t), L.s>>>(cnt[levels], top.next, top.w, top.sd,
+                                                                   d.top_tmp[0], d.top_tmp[1], d.top_tmp[2],
+                                                                   d.top_tmp[3], d.top_tmp_cap, d.err);
+    L.mark("k_top");
+    for (int k = levels - 1; k >= 0; --k) {
+        const RankLevel &v = d.lv[k];
+        const int32_t *wl = k == 0 ? d.rlen : d.lv[k - 1].w;
+        int32_t *sdl = k == 0 ? d.sd1 : d.lv[k - 1].sd;
+        k_lvl_expand<<<grid_for(L, ceil_div(bnd[k], kThreads)), kThreads, 0, L.s>>>(cnt[k], v.l, wl, v.owner,
+                                                                                    v.offs, v.sd, sdl);
+        L.mark("k_lvl_expand");
+    }
     const int32_t *sd = d.sd1;
     long long *next_base = d.counters + 6;
     CK(cudaMemsetAsync(next_base, 0, sizeof(long long), L.s));

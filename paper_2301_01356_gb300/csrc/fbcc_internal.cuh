@@ -26,11 +26,27 @@ constexpr int kErrChase = 2;      // list-ranking chase longer than the list
 constexpr int kErrLookback = 4;   // scan look-back wait cap
 constexpr int kErrIndex = 8;      // a computed index fell outside its array (inconsistent input)
 constexpr int kUniteCap = 1 << 26;
+constexpr int kKeyChunk = 1024;   // arcs of a scanned list per key-scan work item
 constexpr int kLookbackCap = 1 << 22;
 
 // ---------------------------------------------------------------------------
 // Workspace: every O(n) / O(nnz) array of one solve (device pointers).
 // ---------------------------------------------------------------------------
+// One sampling level of the list ranking above the level-1 rulers: its nodes are
+// a sample of the lists of the level below (their heads plus one node in
+// kStride2), and every node carries the weight of the segment of the level below
+// that it owns.
+struct RankLevel {
+    int64_t cap;              // node capacity of this level
+    int2 *l;                  // per node below: {next node below, node id here; -1 none, -2 finished}
+    int32_t *relem;           // node below of every node here
+    int32_t *owner, *offs;    // per node below: its owning node here and its weighted offset from it
+    int32_t *next, *w;        // per node here: next node of its list (-1: last), segment weight
+    uint8_t *head;            // per node here: 1 if it heads its list
+    int32_t *sd;              // per node here: suffix weight to the end of its list
+};
+constexpr int kRankLevels = 2;
+
 struct Dev {
     // sizes the workspace was created for
     int64_t n_max, nnz_max;
@@ -56,13 +72,12 @@ struct Dev {
     int2 *link;               // {succ, ruler id or -1} per tree arc; after the walks a non-ruler
                               // arc holds {owning ruler, -distance from it}
     int32_t *relem;           // arc of ruler r
-    int32_t *rnext[2], *rval[2];  // ruler list: next ruler and suffix weight (double buffered)
     int32_t *rlen;            // ruler segment length
     int32_t *rnx1;            // next ruler in the tour (-1: last)
-    int2 *l2;                 // per ruler: {next ruler, level-2 ruler id, -1 none, -2 finished}
-    int32_t *relem2;          // level-1 ruler of level-2 ruler R
-    int32_t *owner2, *offs2;  // level-2 owner of every ruler and its weighted offset
     int32_t *sd1;             // suffix length (arcs to the tour's end) from every ruler
+    RankLevel lv[kRankLevels];// the ruler lists sampled again (levels 2 and 3)
+    int32_t *top_tmp[4];      // global double buffers of the top level's pointer jumping
+    int64_t top_tmp_cap;
     int32_t *csize;           // component size at its root (other entries unspecified)
     int32_t *vbase;           // first preorder number of the component at its root
     int2 *rec;                // tour record at every position (down/up arc, padding)
@@ -88,11 +103,19 @@ struct Dev {
     // Last-CC and outputs
     int32_t *nh;              // number of labels a vertex heads
     unsigned long long *key;  // smallest arc id (src < dst) of label L at [L]
-    uint8_t *scanv;           // vertex whose list must be scanned for keys
+    uint32_t *scanb;          // one bit per vertex: its list is scanned for keys (listed in klist)
+    int2 *klist;              // {u0, chunk} of every kKeyChunk-arc chunk of the scanned lists
+    int64_t klist_cap;
+    int32_t *kmin;            // per label whose head is its BCC's smallest vertex: the smallest
+                              // class member adjacent to the head (-1: another kind of label)
     uint32_t *key_bits;       // one bit per arc: arc is the key of its BCC
     int32_t *key_pre;         // exclusive popcount prefix per 32-bit word of key_bits
     int32_t *rank;            // canonical BCC index of label L at [L]
     int32_t *word;            // per vertex: BCC index of its label | bridge << 31
+    // Query index of the last solve (built by the first query after it)
+    int32_t *hoff;            // labels headed by the vertices before v (n+1 entries)
+    int32_t *hfill;           // fill cursor per head
+    int32_t *hlist;           // ranks of the labels each vertex heads, at [hoff[v], hoff[v+1])
     fbcc_stats *stats;        // device-side counts
 };
 
@@ -513,12 +536,20 @@ cudaError_t launch_validate(const Dev &d, const OffT *off, const int32_t *adj, i
 // out[i] = set bits in words[0..i), i in [0, len].
 cudaError_t launch_scan_popc(const Dev &d, const uint32_t *words, int32_t *out, int64_t len, const Launch &L);
 
-// Number of ruler-list pointer-jumping rounds for up to r rulers.
-inline int jump_rounds(int64_t r)
-{
-    int k = 0;
-    while ((1ll << k) < r + 1) ++k;
-    return k + 1;
-}
+// Biconnectivity queries over the last solve's labels and heads (fbcc_query.cu).
+cudaError_t launch_query_index(const Dev &d, int64_t n, cudaStream_t s);
+cudaError_t launch_query_pairs(const Dev &d, int64_t n, const int32_t *u, const int32_t *v, int64_t q, int32_t *out,
+                               int grid, cudaStream_t s);
+cudaError_t launch_query_count(const Dev &d, int64_t n, const int32_t *v, int64_t q, int64_t *out_off, int grid,
+                               cudaStream_t s);
+cudaError_t launch_query_list(const Dev &d, int64_t n, const int32_t *v, int64_t q, const int64_t *out_off,
+                              int32_t *out, int grid, cudaStream_t s);
+
+// The top level of the list ranking is ranked by one CTA in shared memory when it
+// holds at most kTopCap nodes (else by the same CTA in global memory).
+constexpr int kTopThreads = 1024;
+constexpr int kTopPer = 16;
+constexpr int kTopCap = kTopThreads * kTopPer;
+cudaError_t prepare_rooting();
 
 }  // namespace fbcc

@@ -19,11 +19,22 @@
 //    exactly when the vertex that labels it carries the flag;
 //  - canonical BCC numbers: the key of a BCC is its smallest arc id with
 //    src < dst, which orders BCCs exactly like their smallest edge ids. Its source
-//    is u0 = min(smin(l), head(l)) (the BCC's smallest vertex). If u0 lies in this BCC
-//    only, the key is u0's first arc; otherwise u0's list is scanned for the arcs
-//    of this BCC. Keys are set in a bitmap over arcs whose popcount prefix gives
-//    each BCC its rank. (A label is the id of its class's top vertex; smin[l]
-//    holds the class's smallest vertex id.)
+//    is u0 = min(smin(l), head(l)) (the BCC's smallest vertex), and its target the
+//    smallest neighbour of u0 in the BCC. Three cases:
+//      * u0 lies in this BCC only: every neighbour of u0 is in it, and the key is
+//        u0's first arc;
+//      * u0 is the head h and h's list is long (a hub): the neighbours of h in the
+//        BCC are exactly the class members adjacent to h (two adjacent vertices of
+//        one BCC put their edge in it), so each member smaller than the top (which
+//        is adjacent: the tree edge) tests its adjacency to h by a binary search
+//        of its own list, the smallest wins (kmin), and one search of h's list
+//        finds the key;
+//      * otherwise (u0 is a head with a short list, or a class member in several
+//        BCCs) u0's list is scanned, in chunks of kKeyChunk arcs, for the arcs of
+//        this BCC.
+//    Keys are set in a bitmap over arcs whose popcount prefix gives each BCC its
+//    rank. (A label is the id of its class's top vertex; smin[l] holds the class's
+//    smallest vertex id.)
 #include "fbcc_internal.cuh"
 
 namespace fbcc {
@@ -36,17 +47,25 @@ namespace fbcc {
 // together (the pass is bound by dependent-load latency, not bandwidth).
 constexpr int kVPer = 4;
 
+// Key of a label whose head is its BCC's smallest vertex: found by k_key_bits.
+constexpr unsigned long long kKeyHead = ~1ull;
+// Heads with at most this many arcs are scanned like the other listed vertices.
+constexpr int kHeadScan = 32;
+
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__restrict__ off,
                                                       const int2 *__restrict__ fp, const int32_t *__restrict__ lab,
                                                       const int32_t *__restrict__ nh,
                                                       const int32_t *__restrict__ smin,
-                                                      uint8_t *is_ap, unsigned long long *key, uint8_t *scanv,
-                                                      fbcc_stats *stats, int *err)
+                                                      uint8_t *is_ap, unsigned long long *key, int32_t *kmin,
+                                                      uint32_t *scanb, int2 *klist, int64_t klist_cap,
+                                                      long long *klist_n, fbcc_stats *stats, int *err)
 {
     long long nap = 0, ncc = 0;
     const int64_t T = (int64_t)gridDim.x * kThreads;
-    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
+    // the loop test is the warp's (its first lane's): the warp-wide reservation
+    // below needs every lane
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 - (threadIdx.x & 31) < n; v0 += T * kVPer) {
         int2 f[kVPer];
         int32_t h[kVPer], l[kVPer];
 #pragma unroll
@@ -77,7 +96,7 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
         }
         int32_t u0[kVPer], hu[kVPer];
         bool pu[kVPer];
-        OffT ou[kVPer];
+        OffT ou[kVPer], oe[kVPer];
 #pragma unroll
         for (int k = 0; k < kVPer; ++k) {
             if (!((lbl >> k) & 1u)) continue;
@@ -85,94 +104,275 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
             pu[k] = fp[u0[k]].y >= 0;
             hu[k] = nh[u0[k]];
             ou[k] = off[u0[k]];
+            oe[k] = off[u0[k] + 1];
         }
+        // u0 lists to scan: each new one takes ceil(deg / kKeyChunk) entries of klist,
+        // reserved with one atomic per warp and step
+        uint32_t fresh = 0;
+        int64_t nch[kVPer];
 #pragma unroll
         for (int k = 0; k < kVPer; ++k) {
+            nch[k] = 0;
             if (!((lbl >> k) & 1u)) continue;
             const int64_t v = v0 + k * T;
+            const int64_t deg = (int64_t)oe[k] - (int64_t)ou[k];
             if ((int)pu[k] + hu[k] == 1) {   // u0 lies in this BCC only: its first arc is the key
                 key[v] = (unsigned long long)ou[k];
-            } else {
+            } else if (f[k].y < sm[k] && deg > kHeadScan) {
+                // u0 is a head with a long list: the class members find their adjacency
+                // to it (the top is adjacent), and a search of its list the key
+                key[v] = kKeyHead;
+                kmin[v] = (int32_t)v;
+            } else {                         // u0's list is scanned, once for all its labels
                 key[v] = ~0ull;
-                scanv[u0[k]] = 1;
+                const uint32_t bit = 1u << (u0[k] & 31);
+                if (!(atomicOr(scanb + (u0[k] >> 5), bit) & bit)) {
+                    fresh |= 1u << k;
+                    nch[k] = (deg + kKeyChunk - 1) / kKeyChunk;
+                }
             }
+        }
+        long long mine = 0;
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) mine += nch[k];
+        long long inc = mine;
+        const int lane = threadIdx.x & 31;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const long long wtot = __shfl_sync(0xffffffffu, inc, 31);
+        long long at = 0;
+        if (lane == 31 && wtot) at = (long long)atomicAdd((unsigned long long *)klist_n, (unsigned long long)wtot);
+        at = __shfl_sync(0xffffffffu, at, 31) + inc - mine;
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            if (!((fresh >> k) & 1u)) continue;
+            for (int64_t c = 0; c < nch[k]; ++c, ++at)
+                if (in_range(at, klist_cap, err)) klist[at] = make_int2(u0[k], (int32_t)c);
         }
     }
     block_count((long long *)&stats->n_ap, nap);
     block_count((long long *)&stats->n_cc, ncc);
 }
 
-// Keys of BCCs whose smallest vertex u0 lies in several BCCs: scan u0's arcs to
-// larger neighbours; the smallest arc of each such BCC wins an atomicMin.
+// Labels whose head is their BCC's smallest vertex h: every class member x smaller
+// than the class's top (the top itself is adjacent to h through its tree edge)
+// tests whether it is adjacent to h (its parent is h, or a binary search of its
+// own sorted list finds h), and the smallest adjacent one wins.
 template <typename OffT>
-__global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
-                                                       int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
-                                                       const uint8_t *__restrict__ scanv,
-                                                       const uint8_t *__restrict__ dirb,
-                                                       const int32_t *__restrict__ lab,
-                                                       const int2 *__restrict__ fp,
-                                                       const int32_t *__restrict__ smin, unsigned long long *key,
-                                                       bool vec)
+__global__ void __launch_bounds__(kThreads) k_key_adj(int64_t n, const OffT *__restrict__ off,
+                                                      const int32_t *__restrict__ adj, const int2 *__restrict__ fp,
+                                                      const int32_t *__restrict__ lab, int32_t *kmin, int *err)
 {
-    __shared__ OffT win_all[kWarpsPerCta * kWarpWin];
-    OffT *win = win_all + (threadIdx.x >> 5) * kWarpWin;
-    ArcTile<OffT> at;
-    FOR_EACH_WARP_TILE(t, ntiles)
-    {
-        arc_tile_sources(off, nnz, tile_v, t, win, at);
-        if (!at.cnt) continue;
-        bool any = false;
-        uint32_t sel = 0;
-        int32_t prev = -1;
-        bool ps = false;
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
+        int32_t l[kVPer], py[kVPer];
 #pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            if (j >= at.cnt) continue;
-            if (at.src[j] != prev) {
-                prev = at.src[j];
-                ps = __ldg(scanv + prev) != 0;
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k * T;
+            l[k] = -1;
+            if (v < n) {
+                l[k] = lab[v];
+                py[k] = fp[v].y;
             }
-            if (ps) { sel |= 1u << j; any = true; }
         }
-        if (!any) continue;
-        int32_t d[kItems];
-        arc_tile_targets(adj, at.a0, at.cnt, vec, d);
-        const uint32_t bits = __ldg(dirb + (at.a0 >> 3));
-        int32_t cur = -1, last_l = -1;
+        int32_t km[kVPer];
+        uint32_t cand = 0;
 #pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            if (!((sel >> j) & 1u)) continue;
-            const int32_t u = at.src[j], w = d[j];
-            if (w < u) continue;
-            if (u != cur) { cur = u; last_l = -1; }
-            const int32_t x = (bits >> j) & 1u ? w : u;   // the endpoint later in preorder
-            const int32_t l = __ldg(lab + x);
-            if (l == last_l) continue;  // a later arc of the same BCC cannot be smaller
-            last_l = l;
-            const int32_t hd = __ldg(&fp[l].y), sm = __ldg(smin + l);
-            if ((hd < sm ? hd : sm) == u) atomicMin(key + l, (unsigned long long)(at.a0 + j));
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k * T;
+            if (v >= n || py[k] < 0 || v >= l[k] || !in_range(l[k], n, err)) continue;
+            km[k] = kmin[l[k]];
+            cand |= 1u << k;
+        }
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            if (!((cand >> k) & 1u)) continue;
+            const int64_t v = v0 + k * T;
+            if (km[k] < 0 || v >= km[k]) continue;
+            const int32_t h = fp[l[k]].y;
+            bool adjc = py[k] == h;
+            if (!adjc) {
+                int64_t lo = off[v], hi = off[v + 1];
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (adj[mid] < h) lo = mid + 1; else hi = mid;
+                }
+                adjc = lo < (int64_t)off[v + 1] && adj[lo] == h;
+            }
+            if (adjc) atomicMin(kmin + l[k], (int32_t)v);
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const int2 *__restrict__ fp,
-                                                       const int32_t *__restrict__ lab,
-                                                       const unsigned long long *__restrict__ key, uint32_t *key_bits,
-                                                       int64_t nnz, int *err)
+// Keys of BCCs whose smallest vertex u0 lies in several BCCs and is not a hub head:
+// the listed chunks of u0's arcs to larger neighbours are scanned, and the
+// smallest arc of each such BCC wins an atomicMin. A warp takes 32 chunks, one
+// per lane: a lane scans a chunk of at most kShortScan arcs alone (consecutive
+// arcs of one BCC bid once), longer chunks are then scanned by the whole warp
+// one at a time (the lanes of one label reduce to their smallest arc first).
+constexpr int kShortScan = 32;
+
+template <typename OffT>
+__device__ __forceinline__ int32_t key_label(const int32_t *__restrict__ adj, const uint8_t *__restrict__ dirb,
+                                             const int32_t *__restrict__ lab, const int2 *__restrict__ fp,
+                                             const int32_t *__restrict__ smin, int32_t u, int64_t a)
 {
-    // kVPer vertices per thread and step, each round of their loads issued together
+    const int32_t w = adj[a];
+    if (w <= u) return -1;
+    const int32_t x = dir_bit(dirb, a) ? w : u;   // the endpoint later in preorder
+    const int32_t l = __ldg(lab + x);
+    const int32_t hd = __ldg(&fp[l].y), sm = __ldg(smin + l);
+    return (hd < sm ? hd : sm) == u ? l : -1;
+}
+
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
+                                                       const long long *__restrict__ klist_n,
+                                                       const int2 *__restrict__ klist,
+                                                       const uint8_t *__restrict__ dirb,
+                                                       const int32_t *__restrict__ lab,
+                                                       const int2 *__restrict__ fp,
+                                                       const int32_t *__restrict__ smin, unsigned long long *key)
+{
+    const int64_t cnt = *klist_n;
+    const int lane = threadIdx.x & 31;
+    const int64_t cnt_pad = (cnt + 31) & ~31ll;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < cnt_pad; i += (int64_t)gridDim.x * kThreads) {
+        int32_t u = -1;
+        int64_t b = 0, end = 0;
+        if (i < cnt) {
+            const int2 e = klist[i];
+            u = e.x;
+            b = (int64_t)off[u] + (int64_t)e.y * kKeyChunk;
+            const int64_t lend = off[u + 1];
+            end = b + kKeyChunk < lend ? b + kKeyChunk : lend;
+        }
+        const bool lng = end - b > kShortScan;
+        if (!lng) {
+            int32_t last_l = -1;
+            for (int64_t a = b; a < end; ++a) {
+                const int32_t l = key_label<OffT>(adj, dirb, lab, fp, smin, u, a);
+                if (l < 0 || l == last_l) continue;   // a later arc of the same BCC cannot be smaller
+                last_l = l;
+                if ((unsigned long long)a < key[l]) atomicMin(key + l, (unsigned long long)a);
+            }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, lng);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int32_t uu = __shfl_sync(0xffffffffu, u, src);
+            const int64_t bb = __shfl_sync(0xffffffffu, b, src), ee = __shfl_sync(0xffffffffu, end, src);
+            for (int64_t a0 = bb; a0 < ee; a0 += 32) {
+                const int64_t a = a0 + lane;
+                const int32_t l = a < ee ? key_label<OffT>(adj, dirb, lab, fp, smin, uu, a) : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, l);
+                if (l >= 0 && lane == __ffs(peers) - 1 && (unsigned long long)a < key[l])
+                    atomicMin(key + l, (unsigned long long)a);
+            }
+        }
+    }
+}
+
+// First position in [lo, hi) whose neighbour id is >= w, or hi, found by the whole
+// warp together: each round probes 32 evenly spaced positions of the range and
+// keeps the piece where the ids cross w (a list of 10^6 takes four rounds of
+// dependent loads instead of twenty). Every lane takes part and gets the answer.
+__device__ __forceinline__ int64_t warp_lower_bound(const int32_t *__restrict__ adj, int64_t lo, int64_t hi,
+                                                    int32_t w)
+{
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t p = lo + (int64_t)lane * step;
+        const bool ge = p < hi ? __ldg(adj + p) >= w : true;
+        const unsigned m = __ballot_sync(0xffffffffu, ge);
+        const int k = m ? __ffs(m) - 1 : 32;
+        if (k == 0) return lo;                       // adj[lo] >= w already
+        const int64_t nhi = lo + (int64_t)k * step;  // the crossing lies in (p_{k-1}, p_k]
+        lo = lo + (int64_t)(k - 1) * step + 1;
+        hi = nhi < hi ? nhi : hi;
+    }
+    const bool ge = lo + lane < hi ? __ldg(adj + lo + lane) >= w : false;
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    return m ? lo + __ffs(m) - 1 : hi;
+}
+
+constexpr int kShortSearch = 64;   // lists up to this long are searched by one lane
+
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const OffT *__restrict__ off,
+                                                       const int32_t *__restrict__ adj, const int2 *__restrict__ fp,
+                                                       const int32_t *__restrict__ lab,
+                                                       const int32_t *__restrict__ kmin, unsigned long long *key,
+                                                       uint32_t *key_bits, int64_t nnz, int *err)
+{
+    // kVPer vertices per thread and step, each round of their loads issued together;
+    // the loop test is the warp's, since long head lists are searched warp-wide
     const int64_t T = (int64_t)gridDim.x * kThreads;
-    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 - lane < n; v0 += T * kVPer) {
         uint32_t lbl = 0;
+        int32_t hd[kVPer];
 #pragma unroll
         for (int k = 0; k < kVPer; ++k) {
             const int64_t v = v0 + k * T;
-            if (v < n && fp[v].y >= 0 && lab[v] == v) lbl |= 1u << k;
+            hd[k] = -1;
+            if (v < n) hd[k] = fp[v].y;
+            if (v < n && hd[k] >= 0 && lab[v] == v) lbl |= 1u << k;
         }
         unsigned long long ks[kVPer];
 #pragma unroll
         for (int k = 0; k < kVPer; ++k)
             if ((lbl >> k) & 1u) ks[k] = key[v0 + k * T];
+        // the head's arc to the smallest class member adjacent to it
+        int64_t lo[kVPer], hi[kVPer];
+        int32_t w[kVPer];
+        uint32_t srch = 0, lng = 0;
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            if (!((lbl >> k) & 1u) || ks[k] != kKeyHead) continue;
+            w[k] = kmin[v0 + k * T];
+            lo[k] = off[hd[k]];
+            hi[k] = off[hd[k] + 1];
+            srch |= 1u << k;
+            if (hi[k] - lo[k] > kShortSearch) lng |= 1u << k;
+        }
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            if (!((srch >> k) & 1u) || ((lng >> k) & 1u)) continue;
+            int64_t a = lo[k], b = hi[k];
+            while (a < b) {
+                const int64_t mid = (a + b) >> 1;
+                if (adj[mid] < w[k]) a = mid + 1; else b = mid;
+            }
+            lo[k] = a;
+        }
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            unsigned todo = __ballot_sync(0xffffffffu, (lng >> k) & 1u);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t a = __shfl_sync(0xffffffffu, lo[k], src), b = __shfl_sync(0xffffffffu, hi[k], src);
+                const int32_t ww = __shfl_sync(0xffffffffu, w[k], src);
+                const int64_t r = warp_lower_bound(adj, a, b, ww);
+                if (lane == src) lo[k] = r;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kVPer; ++k) {
+            if (!((srch >> k) & 1u)) continue;
+            if (lo[k] >= hi[k] || adj[lo[k]] != w[k]) {
+                atomicOr(err, kErrIndex);
+                lbl &= ~(1u << k);
+                continue;
+            }
+            ks[k] = (unsigned long long)lo[k];
+            key[v0 + k * T] = ks[k];
+        }
 #pragma unroll
         for (int k = 0; k < kVPer; ++k)
             if (((lbl >> k) & 1u) && in_range((int64_t)ks[k], nnz, err)) set_bit(key_bits, (int64_t)ks[k]);
@@ -295,7 +495,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, co
 
 // edge_bcc / is_bridge for every arc.
 template <typename OffT>
-__global__ void __launch_bounds__(kThreads, 6) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
+__global__ void __launch_bounds__(kThreads, 8) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                        int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
                                                        const int32_t *__restrict__ word,
                                                        const uint8_t *__restrict__ dirb, int32_t *edge_bcc,
@@ -362,16 +562,22 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     const int gv = grid_for(L, ceil_div(n, kThreads));
     const int64_t ntiles = ceil_div(nnz, kWTile);
     const int64_t nwords = ceil_div(nnz, 32);
-    CK(cudaMemsetAsync(d.scanv, 0, n, L.s));
-    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.lab, d.nh, d.smin, is_ap, d.key, d.scanv, d.stats, d.err);
+    long long *klist_n = d.counters + 10;
+    CK(cudaMemsetAsync(d.scanb, 0, ceil_div(n, 32) * sizeof(uint32_t), L.s));
+    CK(cudaMemsetAsync(d.kmin, 0xff, n * sizeof(int32_t), L.s));
+    CK(cudaMemsetAsync(klist_n, 0, sizeof(long long), L.s));
+    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.lab, d.nh, d.smin, is_ap, d.key, d.kmin, d.scanb,
+                                              d.klist, d.klist_cap, klist_n, d.stats, d.err);
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
-        k_key_scan<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.scanv, d.dirb,
-                                                                   d.lab, d.fp, d.smin, d.key, vec);
+        k_key_adj<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, d.err);
+        L.mark("k_key_adj");
+        k_key_scan<OffT><<<L.grid, kThreads, 0, L.s>>>(off, adj, klist_n, d.klist, d.dirb, d.lab, d.fp, d.smin,
+                                                       d.key);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
-        k_key_bits<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.lab, d.key, d.key_bits, nnz, d.err);
+        k_key_bits<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, d.key, d.key_bits, nnz, d.err);
         L.mark("k_key_bits");
         CK(cudaGetLastError());
         CK(launch_scan_popc(d, d.key_bits, d.key_pre, nwords, L));

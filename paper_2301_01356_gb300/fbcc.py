@@ -24,6 +24,7 @@ EXPORTS = (
     "fbcc_workspace_bytes", "fbcc_workspace_create", "fbcc_workspace_destroy", "fbcc_workspace_configure",
     "fbcc_solve", "fbcc_solve_host", "fbcc_solve_host_async", "fbcc_solve_noalloc", "fbcc_solve_batch", "fbcc_batch_workspace_bytes", "fbcc_validate",
     "fbcc_profile_count", "fbcc_profile_get", "fbcc_debug_read", "fbcc_status_string", "fbcc_last_cuda_error",
+    "fbcc_query_biconnected", "fbcc_query_bcc_count", "fbcc_query_bccs_of", "fbcc_workspace_create_in",
 )
 
 
@@ -71,6 +72,8 @@ def load(path: str = LIB_PATH):
         lib.fbcc_workspace_bytes.restype = ctypes.c_size_t
         lib.fbcc_workspace_create.argtypes = [I64, I64, ctypes.POINTER(P)]
         lib.fbcc_workspace_create.restype = INT
+        lib.fbcc_workspace_create_in.argtypes = [P, ctypes.c_size_t, I64, I64, I32, ctypes.POINTER(P)]
+        lib.fbcc_workspace_create_in.restype = INT
         lib.fbcc_workspace_destroy.argtypes = [P]
         lib.fbcc_workspace_destroy.restype = None
         lib.fbcc_workspace_configure.argtypes = [P, ctypes.POINTER(fbcc_config)]
@@ -93,6 +96,12 @@ def load(path: str = LIB_PATH):
         lib.fbcc_profile_get.restype = INT
         lib.fbcc_debug_read.argtypes = [P, ctypes.c_char_p, P, I64]
         lib.fbcc_debug_read.restype = INT
+        lib.fbcc_query_biconnected.argtypes = [P, P, P, I64, P, P]
+        lib.fbcc_query_biconnected.restype = INT
+        lib.fbcc_query_bcc_count.argtypes = [P, P, I64, P, P]
+        lib.fbcc_query_bcc_count.restype = INT
+        lib.fbcc_query_bccs_of.argtypes = [P, P, I64, P, P, P]
+        lib.fbcc_query_bccs_of.restype = INT
         lib.fbcc_status_string.argtypes = [INT]
         lib.fbcc_status_string.restype = ctypes.c_char_p
         lib.fbcc_last_cuda_error.argtypes = []
@@ -126,6 +135,14 @@ def fbcc_workspace_bytes(n: int, nnz: int) -> int:
 def fbcc_workspace_create(n_max: int, nnz_max: int) -> int:
     h = ctypes.c_void_p()
     _check(load().fbcc_workspace_create(n_max, nnz_max, ctypes.byref(h)), "fbcc_workspace_create")
+    return h.value
+
+
+def fbcc_workspace_create_in(mem, n_max: int, nnz_max: int, max_graphs: int = 0) -> int:
+    """A workspace inside the device tensor `mem` (uint8, from the caller's allocator)."""
+    h = ctypes.c_void_p()
+    _check(load().fbcc_workspace_create_in(_ptr(mem), int(mem.numel() * mem.element_size()), n_max, nnz_max,
+                                           max_graphs, ctypes.byref(h)), "fbcc_workspace_create_in")
     return h.value
 
 
@@ -227,6 +244,25 @@ def fbcc_batch_workspace_bytes(n_total: int, nnz_total: int, n_graphs: int) -> i
     return int(load().fbcc_batch_workspace_bytes(n_total, nnz_total, n_graphs))
 
 
+def fbcc_query_biconnected(ws: int, u, v, bcc, stream=None) -> None:
+    """bcc[i] = the BCC index u[i] and v[i] share in the last solve on ws, or -1
+    (device int32 tensors of equal length)."""
+    _check(load().fbcc_query_biconnected(ws, _ptr(u), _ptr(v), int(u.numel()), _ptr(bcc), _stream_handle(stream)),
+           "fbcc_query_biconnected")
+
+
+def fbcc_query_bcc_count(ws: int, v, out_off, stream=None) -> None:
+    """out_off (device int64, len(v) + 1): exclusive prefix of the BCC counts of v."""
+    _check(load().fbcc_query_bcc_count(ws, _ptr(v), int(v.numel()), _ptr(out_off), _stream_handle(stream)),
+           "fbcc_query_bcc_count")
+
+
+def fbcc_query_bccs_of(ws: int, v, out_off, out, stream=None) -> None:
+    """The BCC indices of every v[i] at out[out_off[i]:out_off[i + 1]]."""
+    _check(load().fbcc_query_bccs_of(ws, _ptr(v), int(v.numel()), _ptr(out_off), _ptr(out),
+                                     _stream_handle(stream)), "fbcc_query_bccs_of")
+
+
 # ---- convenience wrapper ---------------------------------------------------------
 
 class Solver:
@@ -269,6 +305,24 @@ class Solver:
             "is_bridge": self.is_bridge[:nnz].cpu().numpy(),
             **s,
         }
+
+    def biconnected(self, u, v, stream=None):
+        """Device int32 tensor: the BCC that u[i] and v[i] share in the last solve, or -1."""
+        import torch
+        out = torch.empty(u.numel(), dtype=torch.int32, device=self.device)
+        fbcc_query_biconnected(self.ws, u, v, out, stream)
+        return out
+
+    def bccs_of(self, v, stream=None):
+        """(offsets, ids): the BCCs of v[i] are ids[offsets[i]:offsets[i + 1]] (device
+        tensors; synchronises the stream once to size ids)."""
+        import torch
+        off = torch.empty(v.numel() + 1, dtype=torch.int64, device=self.device)
+        fbcc_query_bcc_count(self.ws, v, off, stream)
+        (stream or torch.cuda.current_stream()).synchronize()
+        ids = torch.empty(max(int(off[-1].item()), 1), dtype=torch.int32, device=self.device)
+        fbcc_query_bccs_of(self.ws, v, off, ids, stream)
+        return off, ids
 
     def close(self):
         if self.ws:

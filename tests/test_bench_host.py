@@ -30,6 +30,26 @@ def test_algorithmic_bytes_cover_every_kernel():
     assert not missing, missing
 
 
+def test_phase_bytes_and_assignment():
+    """The per-phase algorithmic bytes add up to the whole solve's, each arc pass
+    carries its phase's adjacency term, and the profiled launch list is split into
+    Algorithm 1's phases in launch order."""
+    import bench
+    n, nnz, ncc, B = 1000, 8000, 10, 8
+    pb = bench.phase_bytes(n, nnz, ncc, B)
+    A = 2 * (n - ncc)
+    assert set(pb) == set(bench.PHASES)
+    assert sum(pb.values()) == 4 * B * n + 21 * nnz + 48 * A + (16 + 16 + 40 + 28 + 12) * n
+    for k, ph in (("k_cc_hook", "first_cc"), ("k_w12", "tagging"), ("k_last_cc_cross", "last_cc")):
+        assert bench.algorithmic_bytes(k, n, nnz, ncc, B) >= B * n + 4 * nnz
+    assert bench.algorithmic_bytes("k_edge_out", n, nnz, ncc, B) == B * n + 9 * nnz
+    rows = [("k_cc_init", 1), ("k_cc_hook", 1), ("k_uf_compress", 1), ("k_link", 1), ("k_jump", 1),
+            ("k_first_of", 1), ("k_rmq_query", 1), ("k_ext_compact", 1), ("k_mark_big", 1),
+            ("k_final_label", 1), ("k_ap_keys", 1), ("k_edge_out", 1), ("k_finish", 1)]
+    assert bench.phases_of(rows) == ["first_cc"] * 3 + ["rooting"] * 2 + ["tagging"] * 2 + ["last_cc"] * 3 + \
+        ["outputs"] * 3
+
+
 def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     import torch.distributed as dist

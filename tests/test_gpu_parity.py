@@ -268,54 +268,6 @@ def test_grid_4096_full_size(torch_cuda, oracle):
         s.close()
 
 
-def test_rmat24_full_size_properties(torch_cuda):
-    """The power-law workload at full size (260M edges, 64-bit offsets, tuned
-    configuration), where the oracle takes minutes: properties every correct
-    answer has, checked over every arc and vertex.
-      - labels are 0..n_bcc-1 and BCC k's smallest edge id increases with k;
-      - an edge is a bridge iff its BCC has exactly one edge;
-      - a vertex is an articulation point iff its arcs carry two or more labels;
-      - both arcs of an edge carry the same label (checked on a sample of edges);
-      - bcc_head[k] has an arc in BCC k (sample), and the counts agree."""
-    from paper_2301_01356_gb300 import fbcc
-    g = gg.workload_rmat_24()
-    s = fbcc.Solver(g.n, g.nnz, **_tuned("rmat24"))
-    off, adj = to_dev(torch_cuda, g, off64=True)
-    got = s.solve(off, adj)
-    s.close()
-    assert got["device_status"] == 0
-    eb, br, ap = got["edge_bcc"], got["is_bridge"].astype(bool), got["is_ap"].astype(bool)
-    nb = got["n_bcc"]
-    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets))
-    dst = g.adj.astype(np.int64)
-    fwd = src < dst
-    lab = eb[fwd]                                  # one label per edge, in edge id order
-    assert lab.min() >= 0 and lab.max() == nb - 1
-    ks, first = np.unique(lab, return_index=True)
-    assert ks.size == nb and np.all(np.diff(first) > 0), "BCCs numbered by smallest edge id"
-    size = np.bincount(lab, minlength=nb)
-    assert np.array_equal(br[fwd], size[lab] == 1), "bridge iff a one-edge BCC"
-    assert int(br[fwd].sum()) == got["n_bridge"]
-    deg = np.diff(g.offsets)
-    nz = deg > 0
-    starts = g.offsets[:-1][nz]
-    lo = np.minimum.reduceat(eb, starts)
-    hi = np.maximum.reduceat(eb, starts)
-    ap_exp = np.zeros(g.n, bool)
-    ap_exp[np.nonzero(nz)[0]] = lo != hi
-    assert np.array_equal(ap, ap_exp), "articulation point iff two or more labels"
-    assert int(ap.sum()) == got["n_ap"]
-    rng = np.random.default_rng(0)
-    for a in rng.integers(0, g.nnz, 2000):
-        u, w = int(src[a]), int(dst[a])
-        b = g.offsets[w] + np.searchsorted(g.adj[g.offsets[w]:g.offsets[w + 1]], u)
-        assert eb[a] == eb[b], "both arcs of an edge in one BCC"
-    bh = got["bcc_head"]
-    for k in rng.integers(0, nb, 2000):
-        h = int(bh[k])
-        assert np.any(eb[g.offsets[h]:g.offsets[h + 1]] == k), "head lies in its BCC"
-
-
 @pytest.mark.parametrize("max_chunk_arcs", [1 << 28, 150_000])
 def test_bucketed_batch_runner(torch_cuda, oracle, max_chunk_arcs):
     """The config-4 recipe at small scale: every graph's result in the bucketed

@@ -23,7 +23,8 @@ def test_serving_results_equal_alone(torch_cuda, oracle):
               gg.grid(120, 90, p=0.7, seed=6)]
     pool = serving.Pool(torch_cuda, graphs)
     # small slots so that batches get cut and several are in flight
-    srv = serving.Server(pool, slots=3, max_n=40000, max_nnz=150000, max_graphs=16, keep_outputs=True)
+    srv = serving.Server(pool, streams=3, max_batch_n=40000, max_batch_nnz=150000, max_batch_graphs=16,
+                         keep_outputs=True)
     arrivals = serving.poisson_arrivals(400.0, 1.0, 9)
     rng = np.random.default_rng(9)
     ids = rng.integers(0, len(graphs), size=arrivals.size)
@@ -47,3 +48,31 @@ def test_serving_results_equal_alone(torch_cuda, oracle):
             assert np.array_equal(np.asarray(got[k]), np.asarray(e[k])), (r, k)
     alone.close()
     srv.close()
+
+
+def test_serving_admission_by_footprint(torch_cuda, oracle):
+    """A budget that holds one batch of the largest graph at a time: requests wait for
+    memory, the in-flight footprint plus the resident graphs never exceed it, every
+    result still equals the oracle, and the plain per-request loop serves the same
+    requests."""
+    from paper_2301_01356_gb300 import serving
+    graphs = [gg.grid(150, 150, p=0.65, seed=1), gg.uniform(20000, 50000, 2), gg.cycle_chain(8000, 7, 3, 900, 3)]
+    pool = serving.Pool(torch_cuda, graphs)
+    big = max(serving.batch_footprint(g.n, g.nnz, 1) + (g.n + g.nnz) * 4 for g in graphs)
+    budget = int(big * 1.6)
+    srv = serving.Server(pool, streams=4, hbm_budget=budget, keep_outputs=True)
+    arrivals = np.zeros(24)                    # all at once: admission decides
+    ids = np.arange(24) % len(graphs)
+    rep = srv.run(arrivals, ids)
+    assert rep["peak_device_bytes"] <= budget
+    assert rep["batches"] >= 3
+    exp = [oracle.solve(g.offsets, g.adj) for g in graphs]
+    for r in range(24):
+        got = srv.outputs[r]
+        for k in ("edge_bcc", "bcc_head", "is_ap", "is_bridge", "n_bcc", "n_ap", "n_bridge", "n_cc"):
+            assert np.array_equal(np.asarray(got[k]), np.asarray(exp[got["graph"]][k])), (r, k)
+    srv.close()
+    loop = serving.per_request_loop(pool, ids)
+    assert loop["requests"] == 24 and loop["graphs_per_s"] > 0
+    with pytest.raises(ValueError):
+        serving.Server(pool, hbm_budget=big // 4)

@@ -54,7 +54,9 @@ def _existing(torch, fbcc, g, off64):
     return out
 
 
-def test_noalloc_matches_fbcc_solve_on_consecutive_calls(torch_cuda):
+def test_noalloc_matches_fbcc_solve_on_consecutive_calls(torch_cuda, oracle):
+    """Both entry points run the same kernels, so each is also compared with the
+    oracle directly: a fault in the shared path cannot hide behind agreement."""
     from paper_2301_01356_gb300 import fbcc
     graphs = [
         (gg.grid(100, 120, p=0.62, extra_frac=0.001, seed=5), False),   # many small BCCs and components
@@ -64,10 +66,15 @@ def test_noalloc_matches_fbcc_solve_on_consecutive_calls(torch_cuda):
     for g, off64 in graphs:                      # consecutive calls share the static scratch
         got = _noalloc(torch_cuda, fbcc, g, off64)
         exp = _existing(torch_cuda, fbcc, g, off64)
+        ref = oracle.solve(g.offsets, g.adj)
         for k in KEYS:
             assert np.array_equal(got[k], exp[k]), f"{g.name}: {k}"
+            assert np.array_equal(got[k], ref[k]), f"{g.name}: {k} differs from the oracle"
         for k in ("n_bcc", "n_ap", "n_bridge", "n_cc", "device_status"):
             assert got[k] == exp[k], f"{g.name}: {k}"
+        for k in ("n_bcc", "n_ap", "n_bridge", "n_cc"):
+            assert got[k] == ref[k], f"{g.name}: {k} differs from the oracle"
+        assert got["device_status"] == 0
     # the same graph twice in a row gives the same answer again
     g, off64 = graphs[0]
     again = _noalloc(torch_cuda, fbcc, g, off64)
