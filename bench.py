@@ -146,7 +146,7 @@ class ClockSampler:
 # Algorithm 1's steps as the profiled kernels run them: a phase starts at its first
 # kernel and lasts until the next phase starts.
 PHASES = ("first_cc", "rooting", "tagging", "last_cc", "outputs")
-PHASE_START = {"k_link": "rooting", "k_first_of": "tagging", "k_ext_compact": "last_cc", "k_ap_keys": "outputs"}
+PHASE_START = {"k_link_prep": "rooting", "k_link": "rooting", "k_first_of": "tagging", "k_ext_compact": "last_cc", "k_ap_keys": "outputs"}
 
 
 def phase_bytes(n: int, nnz: int, n_cc: int, off_bytes: int) -> dict:
@@ -179,8 +179,8 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_cc_hook": arc_cc, "k_cc_local": arc_cc, "k_cc_hook_skip": arc_cc, "k_cc_hook_cross": 0,
         "k_cc_sample": 0, "k_mark_big": 0, "k_cc_pick_big": 0,
         # Rooting
-        "k_link": 8 * A, "k_succ_rulers": 16 * A, "k_chase": 8 * A, "k_lvl_rulers": 0, "k_lvl_chase": 0,
-        "k_top": 0, "k_lvl_expand": 0, "k_comp_size": 0, "k_place_records": 8 * A, "k_preorder": 8 * A + 16 * n,
+        "k_link_prep": 0, "k_link": 8 * A, "k_hub_order": 0, "k_succ_rulers": 16 * A, "k_chase": 8 * A, "k_lvl_rulers": 0, "k_lvl_chase": 0,
+        "k_top": 0, "k_lvl_expand": 0, "k_jump": 0, "k_comp_size": 0, "k_place_records": 8 * A, "k_preorder": 8 * A + 16 * n,
         # Tagging
         "k_first_of": 0, "k_w12": B * n + 4 * nnz + 8 * n, "k_rmq_prefix": 8 * n, "k_rmq_level": 0,
         "k_rmq_query": 24 * n,
@@ -302,10 +302,10 @@ def tuned_config(args) -> dict:
     """The autotuner's choice for this workload (tuning.json), overridden by any knob
     given on the command line."""
     from paper_2301_01356_gb300 import batch as B
-    cfg = dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0, lcc_sample=0)
+    cfg = dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0, lcc_sample=0, rank_variant=0, grid_ctas=0)
     if args.config == "tuned":
         cfg.update(B.load_tuning().get("graphs", {}).get(args.workload, {}).get("config", {}))
-    for k in ("ruler_stride", "cc_sample", "chase_chains", "cc_local", "lcc_sample"):
+    for k in ("ruler_stride", "cc_sample", "chase_chains", "cc_local", "lcc_sample", "rank_variant", "grid_ctas"):
         v = getattr(args, k)
         if v is not None:
             cfg[k] = v
@@ -365,6 +365,42 @@ def roofline_line(kernels: dict, phase_ms: dict, n: int, nnz: int, n_cc: int, of
             "algorithmic_bytes_per_launch": ab, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
             "ms_per_launch": kernels[dom]["ms_per_launch"],
             "solve_bytes": solve_b, "solve_gbs": solve_gbs, "solve_frac": solve_gbs / peak, "phases": phases}
+
+
+def time_queries(torch, solver, off, adj, n: int, nnz: int, g, count: int) -> dict:
+    """Biconnectivity queries on the solved workload (section 3.4's labels and heads):
+    `count` vertex pairs (half the two ends of random edges, half random pairs) and
+    the BCCs of `count` random vertices, timed with CUDA events after one warm-up
+    call (which also builds the per-head index of the solve)."""
+    from paper_2301_01356_gb300 import fbcc
+    rng = np.random.default_rng(12)
+    a = rng.integers(0, nnz, count // 2)
+    src = (np.searchsorted(g.offsets, a, side="right") - 1).astype(np.int32)   # the arcs' sources
+    u = np.concatenate([src, rng.integers(0, n, count - count // 2).astype(np.int32)])
+    v = np.concatenate([g.adj[a], rng.integers(0, n, count - count // 2).astype(np.int32)])
+    du, dv = torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()
+    nv = min(count, 2 * n)                       # a call lists the BCCs of at most 2 n vertices
+    dw = du[:nv].contiguous()
+    solver.enqueue(off, adj)
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    offs = torch.empty(nv + 1, dtype=torch.int64, device="cuda")
+    fbcc.fbcc_query_biconnected(solver.ws, du, dv, out)
+    fbcc.fbcc_query_bcc_count(solver.ws, dw, offs)
+    torch.cuda.synchronize()
+    ids = torch.empty(max(int(offs[-1].item()), 1), dtype=torch.int32, device="cuda")
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    fbcc.fbcc_query_biconnected(solver.ws, du, dv, out)
+    e[1].record()
+    fbcc.fbcc_query_bcc_count(solver.ws, dw, offs)
+    fbcc.fbcc_query_bccs_of(solver.ws, dw, offs, ids)
+    e[2].record()
+    torch.cuda.synchronize()
+    t_pair, t_list = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    return {"pairs": count, "biconnected_pairs_per_s": count / t_pair,
+            "pairs_sharing_a_bcc": int((out >= 0).sum().item()),
+            "vertices": nv, "bccs_of_vertices_per_s": nv / t_list, "bccs_listed": int(offs[-1].item()),
+            "api": "fbcc_query_biconnected; fbcc_query_bcc_count + fbcc_query_bccs_of (device arrays)"}
 
 
 def run_gpu(args, world, rank, local):
@@ -440,6 +476,8 @@ def run_gpu(args, world, rank, local):
                    "ms_per_launch": t / c} for k, (t, c) in prof.items()}
     roofline = roofline_line(kernels, phase_ms, n, nnz, st["n_cc"], off_np.itemsize, max_s * 1e3 / args.steps,
                              args.workload)
+
+    queries = time_queries(torch, solver, off, adj, n, nnz, g, args.query_count)
 
     # end to end through the public host API: pinned host in, pinned host out
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
@@ -529,6 +567,7 @@ def run_gpu(args, world, rank, local):
                          "api": "fbcc_solve_host, one call at a time"}},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
+        "queries": queries,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "parity_vs_oracle": parity,
@@ -821,7 +860,10 @@ def main(argv=None):
     ap.add_argument("--chase-chains", type=int, default=None, help="list ranking: walks per thread (1, 2, 4)")
     ap.add_argument("--cc-local", type=int, default=None, help="First-CC: shared-memory range in vertices (0 = off)")
     ap.add_argument("--lcc-sample", type=int, default=None, help="Last-CC: cross edges sampled per vertex (0 = off)")
+    ap.add_argument("--rank-variant", type=int, default=None, help="list ranking: 0 sampled levels, 1 pointer jumping")
+    ap.add_argument("--grid-ctas", type=int, default=None, help="CTAs of the persistent grid (0 = 8 per SM)")
     ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--query-count", type=int, default=1 << 24, help="queries timed after the solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one solve with direct launches and exit (for profilers; no timing)")

@@ -69,7 +69,7 @@ typedef struct {
 typedef struct {
     int32_t ruler_stride;  /* list ranking: one ruler per this many tree arcs (power of 2, >= 8) */
     int32_t cc_sample;     /* First-CC: neighbours per vertex hooked before the full pass (0 = off) */
-    int32_t grid_ctas;     /* CTAs of the persistent grid-stride kernels */
+    int32_t grid_ctas;     /* CTAs of the persistent grid-stride kernels; -k = k per SM (default 8 per SM) */
     int32_t use_graph;     /* 1 = replay a captured CUDA graph for repeated identical calls (default), -1 = never */
     int32_t profile;       /* 1 = record a CUDA event after every kernel (no graph); see fbcc_profile_get */
     int32_t chase_chains;  /* list ranking: walks a thread advances together (1, 2 or 4) */
@@ -78,6 +78,9 @@ typedef struct {
                               whose lists hold 2^31 arcs or more makes the solve report
                               FBCC_E_INVALID in device_status */
     int32_t lcc_sample;    /* Last-CC: cross edges per vertex united before the full pass (0 = off) */
+    int32_t rank_variant;  /* list ranking above the rulers: 0 = sample the ruler lists again and rank
+                              the top level in one CTA (default); 1 = pointer jumping (Wyllie) over
+                              the ruler lists, a fixed number of grid-wide rounds */
 } fbcc_config;
 
 /* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds.

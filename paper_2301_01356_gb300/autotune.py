@@ -1,12 +1,23 @@
 """Autotuner: the best configuration per graph-size bucket (and per benchmark graph).
 
-For every size bucket of a sample batch, each candidate configuration (ruler
-stride of the list ranking; First-CC variant: plain hooking, local-first in
-shared memory, or sampled; Last-CC sampling) is timed with CUDA events on the
-bucket's batched solve (mean of a few runs), the three fastest are timed again
-over many more runs (a sampled variant can be slow now and then, and a short
-mean can miss it), and the fastest of those is written to ``tuning.json`` beside
-this module, which ``batch.BatchRunner`` and ``bench.py`` read.
+The knobs, each a runtime choice of the library (fbcc_config):
+  - First-CC variant: plain hooking, local-first in shared memory over ranges of
+    8192 or 16384 vertices, or sampled (two neighbours per vertex first);
+  - Last-CC sampling (cross edges united per vertex before the full pass);
+  - ruler stride of the list ranking, walks a thread advances together
+    (chase_chains), and the ranking above the rulers (sampled levels with a
+    single-CTA top, or Wyllie pointer jumping);
+  - the persistent grid size in CTAs per SM.
+The thread-block shape (256 threads, 8 items per thread, 1024-position RMQ tiles)
+is a compile-time constant: the shared-memory layouts of every arc and tile pass
+are sized by it.
+
+Coordinate descent: starting from the defaults, each knob in turn is set to each of
+its values with the others held (mean CUDA-event time of a few runs), and the best
+is kept; the three best configurations seen are then timed again over many more
+runs (a sampled variant can be slow now and then, and a short mean can miss it),
+and the fastest is written to ``tuning.json`` beside this module, which
+``batch.BatchRunner`` and ``bench.py`` read.
 
     python -m paper_2301_01356_gb300.autotune [--graphs 512] [--out PATH]
 """
@@ -21,8 +32,16 @@ import numpy as np
 from . import batch as B
 from . import fbcc, graphgen as gg
 
-CANDIDATES = [dict(ruler_stride=s, cc_local=l, cc_sample=c, lcc_sample=q)
-              for s in (8, 16, 32) for (l, c) in ((0, 0), (8192, 0), (16384, 0), (0, 2)) for q in (0, 2)]
+DEFAULT = dict(ruler_stride=16, cc_local=0, cc_sample=0, lcc_sample=0, chase_chains=1, rank_variant=0, grid_ctas=0)
+KNOBS = [
+    ("cc", [dict(cc_local=0, cc_sample=0), dict(cc_local=8192, cc_sample=0), dict(cc_local=16384, cc_sample=0),
+            dict(cc_local=0, cc_sample=2)]),
+    ("ruler_stride", [dict(ruler_stride=s) for s in (8, 16, 32, 64)]),
+    ("lcc_sample", [dict(lcc_sample=q) for q in (0, 2)]),
+    ("chase_chains", [dict(chase_chains=c) for c in (1, 2)]),
+    ("rank_variant", [dict(rank_variant=r) for r in (0, 1)]),
+    ("grid_ctas", [dict(grid_ctas=g) for g in (0, -4, -16)]),   # -k: k CTAs per SM (0: 8 per SM)
+]
 
 
 def _time(fn, reps: int) -> float:
@@ -44,7 +63,30 @@ def _finalists(times: dict, k: int = 3) -> list:
     return sorted(times, key=times.get)[:k]
 
 
-def tune_batch(batch, reps: int = 8, candidates=CANDIDATES, buckets=B.BUCKETS, final_reps: int = 30) -> list:
+def _search(measure, reps: int, final_reps: int) -> tuple:
+    """Coordinate descent over KNOBS with `measure(cfg, reps)`; returns the best
+    configuration, its time and every time measured."""
+    times = {}
+
+    def t(cfg, r):
+        key = json.dumps(cfg, sort_keys=True)
+        if key not in times:
+            times[key] = measure(cfg, r)
+        return times[key]
+
+    cur = dict(DEFAULT)
+    for _, choices in KNOBS:
+        best = min(choices, key=lambda ch: t({**cur, **ch}, reps))
+        cur.update(best)
+    final = {}
+    for key in _finalists(times):   # the closest few again, long enough to see rare slow runs
+        final[key] = measure(json.loads(key), final_reps)
+    best = min(final, key=final.get)
+    times.update(final)
+    return json.loads(best), final[best], times
+
+
+def tune_batch(batch, reps: int = 8, buckets=B.BUCKETS, final_reps: int = 30) -> list:
     out = []
     sizes = batch.sizes()
     for lo, hi in buckets:
@@ -53,42 +95,28 @@ def tune_batch(batch, reps: int = 8, candidates=CANDIDATES, buckets=B.BUCKETS, f
             continue
         runner = B.BatchRunner(batch.subset(idx), buckets=((lo, hi),), tuning={})
 
-        def configure(cfg):
+        def measure(cfg, r):
             for b in runner.buckets:      # every chunk of the bucket
                 fbcc.fbcc_workspace_configure(b.ws, **cfg)
-        times = {}
-        for cfg in candidates:
-            configure(cfg)
-            times[json.dumps(cfg, sort_keys=True)] = _time(runner.run, reps)
-        final = {}
-        for key in _finalists(times):   # the closest few again, long enough to see rare slow runs
-            configure(json.loads(key))
-            final[key] = _time(runner.run, final_reps)
-        best = min(final, key=final.get)
-        times.update(final)
-        out.append({"lo": lo, "hi": hi, "graphs": int(idx.size), "config": json.loads(best), "ms": times[best],
-                    "candidates_ms": times})
+            return _time(runner.run, r)
+        best, ms, times = _search(measure, reps, final_reps)
+        out.append({"lo": lo, "hi": hi, "graphs": int(idx.size), "config": best, "ms": ms, "candidates_ms": times})
         runner.close()
     return out
 
 
-def tune_graph(g, off64: bool, reps: int = 8, candidates=CANDIDATES, final_reps: int = 30) -> dict:
+def tune_graph(g, off64: bool, reps: int = 8, final_reps: int = 30) -> dict:
     import torch
     off = torch.from_numpy(g.offsets.astype(np.int64 if off64 else np.int32)).cuda()
     adj = torch.from_numpy(g.adj).cuda()
     s = fbcc.Solver(g.n, g.nnz)
-    times = {}
-    for cfg in candidates:
+
+    def measure(cfg, r):
         s.configure(**cfg)
-        times[json.dumps(cfg, sort_keys=True)] = _time(lambda: s.enqueue(off, adj), reps)
-    final = {}
-    for key in _finalists(times):
-        s.configure(**json.loads(key))
-        final[key] = _time(lambda: s.enqueue(off, adj), final_reps)
+        return _time(lambda: s.enqueue(off, adj), r)
+    best, ms, times = _search(measure, reps, final_reps)
     s.close()
-    best = min(final, key=final.get)
-    times.update(final)
-    return {"config": json.loads(best), "ms": times[best], "candidates_ms": times}
+    return {"config": best, "ms": ms, "candidates_ms": times}
 
 
 def main(argv=None):

@@ -83,6 +83,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.uf = c.take<int32_t>(N);
     d.tile_v = c.take<int32_t>(ceil_div(Z, kWTile) + 2);
     d.fp = c.take<int2>(N);
+    d.parc = c.take<int32_t>(N);
     d.lastp = c.take<int32_t>(N);
     d.dirb = c.take<uint8_t>(ceil_div(Z, 8) + 8);
     d.bigb = c.take<uint32_t>(ceil_div(N, 32) + 2);
@@ -94,6 +95,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     const size_t shared_from = c.used;
     d.te_u = c.take<int32_t>(N);
     d.te_v = c.take<int32_t>(N);
+    d.te_a = c.take<int32_t>(N);
     const size_t xl_from = c.used;
     d.lhead = c.take<int32_t>(N);
     d.nxt = c.take<int32_t>(2 * N);
@@ -127,6 +129,11 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.csize = c.take<int32_t>(N + 1);
     d.vbase = c.take<int32_t>(N + 1);
     d.rec = c.take<int2>(2 * N);
+    d.hub_cap = Z / kHubDeg + 1 < kHubCap ? Z / kHubDeg + 1 : kHubCap;
+    d.hubidx = c.take<int32_t>(N);
+    d.hubhead = c.take<int32_t>(d.hub_cap * kHubSub);
+    d.hubnext = c.take<int32_t>(d.hub_cap * kHubSub);
+    d.hubvert = c.take<int32_t>(d.hub_cap);
     const size_t rooting_end = c.used;
     {
         const size_t at = (xl_from + 255) & ~size_t(255);
@@ -135,8 +142,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     }
     // tagging, Last-CC and output scratch (alive only after rooting has finished)
     c.used = shared_from;
-    d.pmin = c.take<int32_t>(N);
-    d.pmax = c.take<int32_t>(N);
+    d.pmm = c.take<int2>(N);
     d.tmin = c.take<int32_t>(d.st_levels * d.rmq_tiles_max);
     d.tmax = c.take<int32_t>(d.st_levels * d.rmq_tiles_max);
     d.vbits = c.take<uint8_t>(N);
@@ -146,6 +152,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.ext = c.take<uint8_t>(N);
     d.qlist = c.take<int32_t>(N);
     d.first4 = c.take<int32_t>(N);
+    d.fl = c.take<int2>(N);
     d.cr = c.take<int2>(N);
     d.lab = c.take<int32_t>(N);
     d.smin = c.take<int32_t>(N);
@@ -200,6 +207,7 @@ static fbcc_config default_config()
     c.chase_chains = 1;
     c.cc_local = 0;
     c.lcc_sample = 0;
+    c.rank_variant = 0;
     return c;
 }
 
@@ -209,7 +217,7 @@ static int device_grid(const fbcc_config &c)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return (sms > 0 ? sms : 1) * 8;
+    return (sms > 0 ? sms : 1) * (c.grid_ctas < 0 ? -c.grid_ctas : 8);
 }
 
 extern "C" {
@@ -303,7 +311,7 @@ fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
             if (cfg->ruler_stride < kMinStride || (cfg->ruler_stride & (cfg->ruler_stride - 1))) return FBCC_E_INVALID;
             c.ruler_stride = cfg->ruler_stride;
         }
-        if (cfg->cc_sample < 0 || cfg->grid_ctas < 0) return FBCC_E_INVALID;
+        if (cfg->cc_sample < 0 || cfg->grid_ctas < -64) return FBCC_E_INVALID;
         c.cc_sample = cfg->cc_sample;
         c.grid_ctas = cfg->grid_ctas;
         if (cfg->use_graph) c.use_graph = cfg->use_graph;
@@ -317,6 +325,8 @@ fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
         }
         if (cfg->lcc_sample < 0 || cfg->lcc_sample > 64) return FBCC_E_INVALID;
         c.lcc_sample = cfg->lcc_sample;
+        if (cfg->rank_variant < 0 || cfg->rank_variant > 1) return FBCC_E_INVALID;
+        c.rank_variant = cfg->rank_variant;
         if (cfg->chase_chains) {
             if (cfg->chase_chains != 1 && cfg->chase_chains != 2 && cfg->chase_chains != 4) return FBCC_E_INVALID;
             c.chase_chains = cfg->chase_chains;
@@ -391,7 +401,8 @@ cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *ad
     CK(cudaMemsetAsync(d.stats, 0, sizeof(fbcc_stats), s));
     if (n > 0) {
         CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, ws->cfg.cc_local, vec, L));
-        CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, ws->cfg.chase_chains, L));
+        CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, ws->cfg.chase_chains,
+                                ws->cfg.rank_variant, L));
         CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, ws->cfg.profile != 0, L));
         CK(launch_last_cc<OffT>(d, off, adj, n, nnz, ws->cfg.lcc_sample, vec, L));
         CK(launch_outputs<OffT>(d, off, adj, n, nnz, vec, edge_bcc, bcc_head, is_ap, is_bridge, B, L));

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(kThreads) k_cc_init(const OffT *__restrict__ o
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_hook(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                       int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
-                                                      int32_t *uf, int32_t *te_u, int32_t *te_v, int *err, bool vec)
+                                                      int32_t *uf, int32_t *te_u, int32_t *te_v, int32_t *te_a, int *err,
+                                                      bool vec)
 {
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
@@ -55,10 +56,7 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook(const OffT *__restrict__ o
                 rs = cur;
             }
             int32_t r = uf_unite(uf, rs, d[j], err);
-            if (r >= 0) {
-                te_u[r] = cur;
-                te_v[r] = d[j];
-            }
+            if (r >= 0) tree_edge(te_u, te_v, te_a, r, cur, d[j], at.a0 + j);
         }
     }
 }
@@ -67,17 +65,14 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook(const OffT *__restrict__ o
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_sample(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                         int64_t n, int k, int32_t *uf, int32_t *te_u, int32_t *te_v,
-                                                        int *err)
+                                                        int32_t *te_a, int *err)
 {
     for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
         int64_t b = off[v], e = off[v + 1];
         for (int64_t a = b; a < e && a < b + k; ++a) {
             int32_t w = adj[a];
             int32_t r = uf_unite(uf, (int32_t)v, w, err);
-            if (r >= 0) {
-                te_u[r] = (int32_t)v;
-                te_v[r] = w;
-            }
+            if (r >= 0) tree_edge(te_u, te_v, te_a, r, (int32_t)v, w, a);
         }
     }
 }
@@ -102,7 +97,8 @@ template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_hook_skip(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                            int64_t nnz, const int32_t *__restrict__ tile_v,
                                                            int64_t ntiles, int32_t *uf, int32_t *te_u, int32_t *te_v,
-                                                           const uint32_t *__restrict__ bigb, int *err, bool vec)
+                                                           int32_t *te_a, const uint32_t *__restrict__ bigb, int *err,
+                                                           bool vec)
 {
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
@@ -132,10 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_skip(const OffT *__restric
         for (int j = 0; j < kItems; ++j) {
             if (j >= at.cnt || ((sk >> j) & 1u)) continue;
             int32_t r = uf_unite(uf, at.src[j], d[j], err);
-            if (r >= 0) {
-                te_u[r] = at.src[j];
-                te_v[r] = d[j];
-            }
+            if (r >= 0) tree_edge(te_u, te_v, te_a, r, at.src[j], d[j], at.a0 + j);
         }
     }
 }
@@ -201,6 +194,7 @@ template <typename OffT>
 __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restrict__ off,
                                                             const int32_t *__restrict__ adj, int64_t n, int64_t nnz,
                                                             int V, int32_t *uf, int32_t *te_u, int32_t *te_v,
+                                                            int32_t *te_a,
                                                             int2 *xl, int64_t xl_cap, long long *nxl, int *err,
                                                             bool vec)
 {
@@ -289,8 +283,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const OffT *__restri
                     const int32_t h = ru > rv ? ru : rv, l = ru > rv ? rv : ru;
                     const int32_t old = atomicCAS(par + h, (unsigned short)h, (unsigned short)l);
                     if (old == h) {
-                        te_u[v0 + h] = (int32_t)(v0 + su[j]);
-                        te_v[v0 + h] = dw[j];
+                        tree_edge(te_u, te_v, te_a, (int32_t)(v0 + h), (int32_t)(v0 + su[j]), dw[j], a0 + j);
                         ru = rv;   // joined
                         break;
                     }
@@ -317,17 +310,15 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restri
                                                             const int32_t *__restrict__ tile_v, int64_t ntiles, int V,
                                                             const int2 *__restrict__ xl, int64_t xl_cap,
                                                             const long long *__restrict__ nxl, int32_t *uf,
-                                                            int32_t *te_u, int32_t *te_v, int *err, bool vec)
+                                                            int32_t *te_u, int32_t *te_v, int32_t *te_a, int *err,
+                                                            bool vec)
 {
     const long long nx = *nxl;
     if (nx <= xl_cap) {
         for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nx; i += (int64_t)gridDim.x * kThreads) {
             const int2 e = xl[i];
             const int32_t r = uf_unite(uf, e.x, e.y, err);
-            if (r >= 0) {
-                te_u[r] = e.x;
-                te_v[r] = e.y;
-            }
+            if (r >= 0) tree_edge(te_u, te_v, te_a, r, e.x, e.y, -1);   // (the list keeps no positions)
         }
         return;
     }
@@ -343,10 +334,7 @@ __global__ void __launch_bounds__(kThreads) k_cc_hook_cross(const OffT *__restri
         for (int j = 0; j < kItems; ++j) {
             if (j >= at.cnt || at.src[j] >= d[j] || at.src[j] / V == d[j] / V) continue;
             int32_t r = uf_unite(uf, at.src[j], d[j], err);
-            if (r >= 0) {
-                te_u[r] = at.src[j];
-                te_v[r] = d[j];
-            }
+            if (r >= 0) tree_edge(te_u, te_v, te_a, r, at.src[j], d[j], at.a0 + j);
         }
     }
 }
@@ -384,14 +372,15 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             const cudaError_t e = cudaMemsetAsync(nxl, 0, sizeof(long long), L.s);
             if (e != cudaSuccess) return e;
             k_cc_local<OffT><<<gl, kLocalThreads, cc_local_smem(cc_local, sizeof(OffT) == 8), L.s>>>(
-                off, adj, n, nnz, cc_local, d.uf, d.te_u, d.te_v, d.xl, d.xl_cap, nxl, d.err, vec);
+                off, adj, n, nnz, cc_local, d.uf, d.te_u, d.te_v, d.te_a, d.xl, d.xl_cap, nxl, d.err, vec);
             L.mark("k_cc_local");
             k_cc_hook_cross<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, cc_local, d.xl,
-                                                           d.xl_cap, nxl, d.uf, d.te_u, d.te_v, d.err, vec);
+                                                           d.xl_cap, nxl, d.uf, d.te_u, d.te_v, d.te_a, d.err, vec);
             L.mark("k_cc_hook_cross");
         } else if (cc_sample > 0) {
             int32_t *big = reinterpret_cast<int32_t *>(d.counters + 8);
-            k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, d.err);
+            k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, d.te_a,
+                                                        d.err);
             L.mark("k_cc_sample");
             k_uf_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
             L.mark("k_uf_compress");
@@ -400,11 +389,11 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             k_mark_big<<<gv, kThreads, 0, L.s>>>(d.uf, n, big, d.bigb);
             L.mark("k_mark_big");
             k_cc_hook_skip<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
-                                                          d.bigb, d.err, vec);
+                                                          d.te_a, d.bigb, d.err, vec);
             L.mark("k_cc_hook_skip");
         } else {
-            k_cc_hook<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v, d.err,
-                                                     vec);
+            k_cc_hook<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
+                                                     d.te_a, d.err, vec);
             L.mark("k_cc_hook");
         }
     }

@@ -46,8 +46,43 @@ __device__ __forceinline__ int32_t arc_dst(const int32_t *te_u, const int32_t *t
     return (a & 1) ? te_u[a >> 1] : te_v[a >> 1];
 }
 
+// Sub-list of edge h at a hub: a multiplicative hash of h, so that the sub-lists do
+// not follow the low bits of the arc ids, which pick the rulers of the ranking (with
+// h mod kHubSub, all of a hub's sampled arcs would fall into two sub-lists and the
+// walks through the others would be as long as the sub-lists).
+__device__ __forceinline__ int hub_sub(int64_t h)
+{
+    return (int)(((uint32_t)h * 2654435761u) >> 27);
+}
+
+// Empty arc lists, and a hub slot for every vertex of graph degree >= kHubDeg
+// (while slots last): its arcs go to kHubSub sub-lists, chosen by edge id, so that
+// the pushes of one hub spread over kHubSub words.
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_link_prep(int64_t n, const OffT *__restrict__ off, int32_t *lhead,
+                                                        int32_t *hubidx, int32_t *hubhead, int32_t *hubvert,
+                                                        int64_t hub_cap, long long *nhub)
+{
+    GRID_STRIDE(v, n)
+    {
+        lhead[v] = -1;
+        int32_t id = -1;
+        if ((int64_t)off[v + 1] - (int64_t)off[v] >= kHubDeg) {
+            const long long k = (long long)atomicAdd((unsigned long long *)nhub, 1ull);
+            if (k < hub_cap) {
+                id = (int32_t)k;
+                hubvert[id] = (int32_t)v;
+                for (int s = 0; s < kHubSub; ++s) hubhead[(int64_t)id * kHubSub + s] = -1;
+            }
+        }
+        hubidx[v] = id;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__restrict__ te_u,
-                                                   const int32_t *__restrict__ te_v, int32_t *lhead, int32_t *nxt)
+                                                   const int32_t *__restrict__ te_v,
+                                                   const int32_t *__restrict__ hubidx, int32_t *lhead,
+                                                   int32_t *hubhead, int32_t *nxt)
 {
     // four edges per thread and step: their eight exchanges in flight together
     constexpr int kPer = 4;
@@ -60,19 +95,55 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
             u[k] = h < n ? te_u[h] : -1;
             v[k] = u[k] >= 0 ? te_v[h] : -1;
         }
+        int32_t hu[kPer], hv[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            hu[k] = hv[k] = -1;
+            if (u[k] < 0) continue;
+            hu[k] = __ldg(hubidx + u[k]);
+            hv[k] = __ldg(hubidx + v[k]);
+        }
         int2 o[kPer];
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             if (u[k] < 0) continue;
             const int64_t h = h0 + k * T;
-            o[k].x = atomicExch(lhead + u[k], (int32_t)(2 * h));
-            o[k].y = atomicExch(lhead + v[k], (int32_t)(2 * h + 1));
+            const int s = hub_sub(h);   // the sub-list of both arcs of edge h
+            o[k].x = atomicExch(hu[k] >= 0 ? hubhead + (int64_t)hu[k] * kHubSub + s : lhead + u[k], (int32_t)(2 * h));
+            o[k].y = atomicExch(hv[k] >= 0 ? hubhead + (int64_t)hv[k] * kHubSub + s : lhead + v[k],
+                                (int32_t)(2 * h + 1));
         }
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             if (u[k] < 0) continue;
             *reinterpret_cast<int2 *>(nxt + 2 * (h0 + k * T)) = o[k];
         }
+    }
+}
+
+// A hub's sub-lists in one cyclic order: each non-empty sub-list is followed by the
+// next non-empty one (hubnext, -1 after the last), and the hub's list starts with
+// the first (lhead), so that the successor pass sees one list per vertex. A warp
+// per hub slot, a lane per sub-list.
+__global__ void __launch_bounds__(kThreads) k_hub_order(const long long *__restrict__ nhub_p, int64_t hub_cap,
+                                                        const int32_t *__restrict__ hubvert,
+                                                        const int32_t *__restrict__ hubhead, int32_t *hubnext,
+                                                        int32_t *lhead)
+{
+    const long long nh = *nhub_p;
+    const int64_t cnt = nh < hub_cap ? nh : hub_cap;
+    const int lane = threadIdx.x & 31;
+    static_assert(kHubSub == 32, "a lane per sub-list");
+    for (int64_t i = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; i < cnt;
+         i += ((int64_t)gridDim.x * kThreads) >> 5) {
+        const int32_t hd = hubhead[i * kHubSub + lane];
+        const unsigned m = __ballot_sync(0xffffffffu, hd >= 0);
+        const unsigned later = lane == 31 ? 0u : m & ~((2u << lane) - 1u);
+        const int nx = later ? __ffs(later) - 1 : -1;
+        const int32_t nh2 = __shfl_sync(0xffffffffu, hd, nx < 0 ? 0 : nx);
+        hubnext[i * kHubSub + lane] = nx < 0 ? -1 : nh2;
+        const int32_t first = __shfl_sync(0xffffffffu, hd, m ? __ffs(m) - 1 : 0);
+        if (lane == 0) lhead[hubvert[i]] = m ? first : -1;
     }
 }
 
@@ -89,7 +160,9 @@ __global__ void __launch_bounds__(kThreads) k_succ_rulers(int64_t n, const int32
                                                           const int32_t *__restrict__ te_v,
                                                           const int32_t *__restrict__ uf,
                                                           const int32_t *__restrict__ lhead,
-                                                          const int32_t *__restrict__ nxt, int stride, int2 *link,
+                                                          const int32_t *__restrict__ nxt,
+                                                          const int32_t *__restrict__ hubidx,
+                                                          const int32_t *__restrict__ hubnext, int stride, int2 *link,
                                                           uint8_t *rhead, int32_t *relem, long long *nr)
 {
     constexpr int kE = kItems / 2;   // forest edges per thread and step
@@ -129,7 +202,11 @@ __global__ void __launch_bounds__(kThreads) k_succ_rulers(int64_t n, const int32
             sc[j] = -1;
             if (eu[k] < 0) continue;
             const int32_t x = (j & 1) ? ev[k] : eu[k], y = (j & 1) ? eu[k] : ev[k];
-            const int32_t nxr = nx[j ^ 1];   // nxt of the reverse arc
+            int32_t nxr = nx[j ^ 1];   // nxt of the reverse arc
+            if (nxr < 0) {             // the reverse arc ends a (sub-)list of y
+                const int32_t hy = hubidx[y];
+                if (hy >= 0) nxr = hubnext[(int64_t)hy * kHubSub + hub_sub(h0 + k)];
+            }
             sc[j] = nxr >= 0 ? nxr : (uf[y] == y ? -1 : lhead[y]);
             if (uf[x] == x && lhead[x] == a) head |= 1u << j;
             if (((head >> j) & 1u) || (a & (stride - 1)) == 0) ruler |= 1u << j;
@@ -334,6 +411,24 @@ __global__ void __launch_bounds__(kThreads) k_lvl_expand(const long long *__rest
     }
 }
 
+// One grid-wide round of pointer jumping over the ruler lists: val = suffix weight.
+__global__ void __launch_bounds__(kThreads) k_jump(const long long *__restrict__ nr_p, const int32_t *__restrict__ nx_in,
+                                                   const int32_t *__restrict__ val_in, int32_t *nx_out, int32_t *val_out)
+{
+    const int64_t nr = *nr_p;
+    GRID_STRIDE(r, nr)
+    {
+        const int32_t x = nx_in[r];
+        if (x >= 0) {
+            val_out[r] = val_in[r] + val_in[x];
+            nx_out[r] = nx_in[x];
+        } else {
+            val_out[r] = val_in[r];
+            nx_out[r] = -1;
+        }
+    }
+}
+
 // The top level: suffix weights of every node by pointer jumping, in one CTA. Up
 // to kTopCap nodes live in shared memory (each round reads every pointer and
 // value, synchronises, writes, and stops when no pointer moved); more nodes take
@@ -525,14 +620,20 @@ __global__ void __launch_bounds__(kThreads) k_comp_size(int64_t n, const int32_t
     }
 }
 
+// Up-arc records hold kUpRec - child (below the padding markers -2 and -3).
+constexpr int32_t kUpRec = -4;
+
 // Tour positions of both arcs of every forest edge, and their tour records. The
 // position of arc s is its tour's base (2 * vbase at the root r) plus the tour
 // length L = 2 (size(r) - 1) minus its distance to the tour's end, which is the
 // owning ruler's suffix length minus the arc's distance from that ruler. The
 // earlier of the two arcs is the down arc: it stores {child, parent}; the up
-// arc stores {-1, its distance back to the down arc}.
+// arc stores {kUpRec - child, its distance back to the down arc}. parc[child] is
+// the CSR position of the arc parent -> child when First-CC hooked the edge from
+// that arc, else -1.
 __global__ void __launch_bounds__(kThreads) k_place_records(int64_t n, const int32_t *__restrict__ te_u,
                                                             const int32_t *__restrict__ te_v,
+                                                            const int32_t *__restrict__ te_a, int32_t *parc,
                                                             const int32_t *__restrict__ uf,
                                                             const int32_t *__restrict__ csize,
                                                             const int32_t *__restrict__ vbase,
@@ -552,12 +653,16 @@ __global__ void __launch_bounds__(kThreads) k_place_records(int64_t n, const int
         const int32_t d1 = lk.w >= 0 ? sd[lk.w] : sd[lk.z] + lk.w;
         if (!in_range(d0 - 1, L, err) || !in_range(d1 - 1, L, err)) continue;
         const int32_t p0 = base - d0, p1 = base - d1;
+        // the child learns the CSR position of the arc from its parent when the edge
+        // was hooked from that arc (u -> v)
         if (p0 < p1) {
             rec[p0] = make_int2(v, u);
-            rec[p1] = make_int2(-1, p1 - p0);
+            rec[p1] = make_int2(kUpRec - v, p1 - p0);
+            parc[v] = te_a[h];
         } else {
             rec[p1] = make_int2(u, v);
-            rec[p0] = make_int2(-1, p0 - p1);
+            rec[p0] = make_int2(kUpRec - u, p0 - p1);
+            parc[u] = -1;
         }
     }
 }
@@ -617,7 +722,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_preorder(int64_t n2, const int2
                 fp[vtx] = make_int2(fv, x);
                 s_ord[v[j] - base] = vtx;
                 s_porig[v[j] - base] = x;
-            } else if (r[j].x == -1) {
+            } else if (r[j].x <= kUpRec) {
                 const int32_t e = (int32_t)v[j], fv = e - (r[j].y - 1) / 2;
                 if (in_range(fv, n, err) && fv <= e) lastp[fv] = e;
             }
@@ -640,20 +745,27 @@ __global__ void __launch_bounds__(kThreads, 5) k_preorder(int64_t n2, const int2
 
 template <typename OffT>
 cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           int ruler_stride, int chase_chains, const Launch &L)
+                           int ruler_stride, int chase_chains, int rank_variant, const Launch &L)
 {
     (void)nnz;
     const int gv = grid_for(L, ceil_div(n, kThreads));
     const int ga = grid_for(L, ceil_div(2 * n, kThreads));
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-    CK(cudaMemsetAsync(d.lhead, 0xff, n * sizeof(int32_t), L.s));
-    k_link<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.lhead, d.nxt);
+    long long *nhub = d.counters + 14;
+    CK(cudaMemsetAsync(nhub, 0, sizeof(long long), L.s));
+    k_link_prep<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.lhead, d.hubidx, d.hubhead, d.hubvert, d.hub_cap, nhub);
+    L.mark("k_link_prep");
+    k_link<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.hubidx, d.lhead, d.hubhead, d.nxt);
     L.mark("k_link");
+    k_hub_order<<<grid_for(L, ceil_div(d.hub_cap * 32, kThreads)), kThreads, 0, L.s>>>(nhub, d.hub_cap, d.hubvert,
+                                                                                      d.hubhead, d.hubnext, d.lhead);
+    L.mark("k_hub_order");
     long long *nr = d.counters + 1;
     CK(cudaMemsetAsync(nr, 0, sizeof(long long), L.s));
-    k_succ_rulers<<<grid_for(L, ceil_div(n, kTile / 2)), kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.lhead, d.nxt, ruler_stride, d.link, d.rhead,
-                                            d.relem, nr);
+    k_succ_rulers<<<grid_for(L, ceil_div(n, kTile / 2)), kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.lhead, d.nxt,
+                                                                             d.hubidx, d.hubnext, ruler_stride,
+                                                                             d.link, d.rhead, d.relem, nr);
     L.mark("k_succ_rulers");
     // upper bound on the number of rulers: a head per tour (a tour spans at least
     // two vertices) plus one per stride
@@ -669,6 +781,23 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     else
         k_chase<1><<<gr, kThreads, 0, L.s>>>(n, nr, d.relem, d.link, d.rnx1, d.rlen, d.err);
     L.mark("k_chase");
+    if (rank_variant == 1) {
+        // Wyllie: pointer jumping over the level-1 ruler lists, a fixed number of
+        // grid-wide rounds (enough for the longest possible list), double-buffered in
+        // the level-2 arrays, which this variant leaves unused
+        int32_t *nb[2] = {d.lv[0].owner, reinterpret_cast<int32_t *>(d.lv[0].l)};
+        int32_t *vb[2] = {d.lv[0].offs, reinterpret_cast<int32_t *>(d.lv[0].l) + d.ruler_max};
+        const int gj = grid_for(L, ceil_div(rbound, kThreads));
+        const int rounds = jump_rounds(rbound);
+        const int32_t *nx = d.rnx1, *vl = d.rlen;
+        for (int i = 0; i < rounds; ++i) {
+            int32_t *onx = nb[i & 1], *ovl = i + 1 == rounds ? d.sd1 : vb[i & 1];
+            k_jump<<<gj, kThreads, 0, L.s>>>(nr, nx, vl, onx, ovl);
+            L.mark("k_jump");
+            nx = onx;
+            vl = ovl;
+        }
+    } else {
     // Levels above the rulers: each samples the lists below again (heads of lists of
     // several nodes, at most the stride samples two levels down, plus one node in
     // kStride2); a third level is added when the second may exceed what one CTA
@@ -715,6 +844,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
                                                                                     v.offs, v.sd, sdl);
         L.mark("k_lvl_expand");
     }
+    }
     const int32_t *sd = d.sd1;
     long long *next_base = d.counters + 6;
     CK(cudaMemsetAsync(next_base, 0, sizeof(long long), L.s));
@@ -722,7 +852,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
                                           d.fp, d.lastp, d.ord, d.porig, d.w1, d.w2, d.err);
     L.mark("k_comp_size");
     CK(cudaGetLastError());
-    k_place_records<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.csize, d.vbase, d.link, sd, d.rec, d.err);
+    k_place_records<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.te_a, d.parc, d.uf, d.csize, d.vbase, d.link, sd, d.rec, d.err);
     L.mark("k_place_records");
     CK(cudaGetLastError());
     const int64_t ntiles = ceil_div(2 * n, kTile);
@@ -736,8 +866,8 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
 }
 
 template cudaError_t launch_rooting<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
-                                             int, const Launch &);
+                                             int, int, const Launch &);
 template cudaError_t launch_rooting<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,
-                                             int, const Launch &);
+                                             int, int, const Launch &);
 
 }  // namespace fbcc

@@ -27,6 +27,11 @@ constexpr int kErrLookback = 4;   // scan look-back wait cap
 constexpr int kErrIndex = 8;      // a computed index fell outside its array (inconsistent input)
 constexpr int kUniteCap = 1 << 26;
 constexpr int kKeyChunk = 1024;   // arcs of a scanned list per key-scan work item
+// Forest-arc lists of vertices of graph degree >= kHubDeg (hubs) are split into
+// kHubSub sub-lists (by edge id), so that their pushes do not serialise on one word.
+constexpr int kHubDeg = 256;
+constexpr int kHubSub = 32;
+constexpr int64_t kHubCap = 1 << 16;
 constexpr int kLookbackCap = 1 << 22;
 
 // ---------------------------------------------------------------------------
@@ -60,6 +65,8 @@ struct Dev {
     // First-CC
     int32_t *uf;              // union-find parent (First-CC, then Last-CC)
     int32_t *te_u, *te_v;     // tree edge recorded at the vertex it hooked (-1: none)
+    int32_t *te_a;            // CSR position of the arc te_u -> te_v it was hooked from (-1: not known)
+    int32_t *parc;            // by vertex: CSR position of the arc parent -> vertex (-1: not known)
     uint32_t *bigb;           // sampling variants: one bit per vertex (First-CC) or position
                               // (Last-CC) in the sampled largest component, fixed for the full pass
     int2 *xl;                 // local-first First-CC: edges between vertex ranges {u, w}, u < w
@@ -68,6 +75,11 @@ struct Dev {
     // Rooting
     int32_t *lhead;           // first forest arc of every vertex's list (-1: none)
     int32_t *nxt;             // next arc in its source's list (2n ids; -1: last)
+    int32_t *hubidx;          // per vertex: its hub slot (-1: not a hub), see kHubDeg
+    int32_t *hubhead;         // per hub slot: kHubSub sub-list heads
+    int32_t *hubnext;         // per hub slot and sub-list: head of the next non-empty sub-list (-1: none)
+    int32_t *hubvert;         // vertex of every hub slot
+    int64_t hub_cap;          // hub slots
     uint8_t *rhead;           // by ruler id: 1 if the ruler heads its tour
     int2 *link;               // {succ, ruler id or -1} per tree arc; after the walks a non-ruler
                               // arc holds {owning ruler, -distance from it}
@@ -84,11 +96,12 @@ struct Dev {
     // Tagging (fp indexed by vertex; the rest by preorder number)
     int2 *fp;                 // {first, parent} by vertex (parent -1 at a root)
     int32_t *first4;          // first by vertex alone (the arc passes gather it: half of fp's bytes)
+    int2 *fl;                 // {first, last} by vertex (one gather gives the fence test a parent's interval)
     uint8_t *dirb;            // one bit per arc: the target's preorder number exceeds the source's
     int32_t *ord;             // vertex at preorder number p
     int32_t *porig;           // parent vertex of the vertex at preorder number p (-1 root)
     int32_t *w1, *w2;         // w1/w2 at preorder number p
-    int32_t *pmin, *pmax;     // in-tile prefix min/max of w1/w2
+    int2 *pmm;                // in-tile prefix {min of w1, max of w2}
     int32_t *tmin, *tmax;     // sparse tables over RMQ tiles: st_levels x rmq_tiles_max
     uint8_t *vbits;           // per vertex: bit0 = tree edge to parent is a bridge
     int32_t *low, *high;      // low/high by preorder number (written by profiled solves only)
@@ -185,6 +198,16 @@ __device__ __forceinline__ void uf_flatten_warp(int32_t *uf, int64_t v, bool in)
     if (in && (int)(threadIdx.x & 31) == leader) r = uf_root(uf, p);
     r = __shfl_sync(0xffffffffu, r, leader);
     if (in && r != p) uf[v] = r;
+}
+
+// Record the forest edge u-v at the root r it hooked, with the CSR position of
+// the arc u->v it came from (-1 when unknown or beyond 32 bits).
+__device__ __forceinline__ void tree_edge(int32_t *te_u, int32_t *te_v, int32_t *te_a, int32_t r, int32_t u,
+                                          int32_t v, int64_t a)
+{
+    te_u[r] = u;
+    te_v[r] = v;
+    te_a[r] = (a >= 0 && a < INT32_MAX) ? (int32_t)a : -1;
 }
 
 // Union of the sets of u and v by CAS-hooking the larger root under the smaller.
@@ -516,7 +539,7 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
 cudaError_t prepare_cc_local(int V);
 template <typename OffT>
 cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           int ruler_stride, int chase_chains, const Launch &L);
+                           int ruler_stride, int chase_chains, int rank_variant, const Launch &L);
 template <typename OffT>
 cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, bool keep_low_high, const Launch &L);
@@ -544,6 +567,14 @@ cudaError_t launch_query_count(const Dev &d, int64_t n, const int32_t *v, int64_
                                cudaStream_t s);
 cudaError_t launch_query_list(const Dev &d, int64_t n, const int32_t *v, int64_t q, const int64_t *out_off,
                               int32_t *out, int grid, cudaStream_t s);
+
+// Rounds of pointer jumping that rank lists of up to r nodes.
+inline int jump_rounds(int64_t r)
+{
+    int k = 0;
+    while ((1ll << k) < r + 1) ++k;
+    return k + 1;
+}
 
 // The top level of the list ranking is ranked by one CTA in shared memory when it
 // holds at most kTopCap nodes (else by the same CTA in global memory).

@@ -59,9 +59,10 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
                                                       const int32_t *__restrict__ smin,
                                                       uint8_t *is_ap, unsigned long long *key, int32_t *kmin,
                                                       uint32_t *scanb, int2 *klist, int64_t klist_cap,
-                                                      long long *klist_n, fbcc_stats *stats, int *err)
+                                                      long long *klist_n, long long *nhead_n, fbcc_stats *stats,
+                                                      int *err)
 {
-    long long nap = 0, ncc = 0;
+    long long nap = 0, ncc = 0, nhead = 0;
     const int64_t T = (int64_t)gridDim.x * kThreads;
     // the loop test is the warp's (its first lane's): the warp-wide reservation
     // below needs every lane
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
                 // to it (the top is adjacent), and a search of its list the key
                 key[v] = kKeyHead;
                 kmin[v] = (int32_t)v;
+                ++nhead;
             } else {                         // u0's list is scanned, once for all its labels
                 key[v] = ~0ull;
                 const uint32_t bit = 1u << (u0[k] & 31);
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
                 }
             }
         }
+        if (!__any_sync(0xffffffffu, fresh != 0)) continue;
         long long mine = 0;
 #pragma unroll
         for (int k = 0; k < kVPer; ++k) mine += nch[k];
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
     }
     block_count((long long *)&stats->n_ap, nap);
     block_count((long long *)&stats->n_cc, ncc);
+    block_count(nhead_n, nhead);
 }
 
 // Labels whose head is their BCC's smallest vertex h: every class member x smaller
@@ -163,8 +167,10 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_key_adj(int64_t n, const OffT *__restrict__ off,
                                                       const int32_t *__restrict__ adj, const int2 *__restrict__ fp,
-                                                      const int32_t *__restrict__ lab, int32_t *kmin, int *err)
+                                                      const int32_t *__restrict__ lab, int32_t *kmin,
+                                                      const long long *__restrict__ nhead_n, int *err)
 {
+    if (*nhead_n == 0) return;   // no label takes this path
     const int64_t T = (int64_t)gridDim.x * kThreads;
     for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
         int32_t l[kVPer], py[kVPer];
@@ -276,44 +282,17 @@ __global__ void __launch_bounds__(kThreads) k_key_scan(const OffT *__restrict__ 
     }
 }
 
-// First position in [lo, hi) whose neighbour id is >= w, or hi, found by the whole
-// warp together: each round probes 32 evenly spaced positions of the range and
-// keeps the piece where the ids cross w (a list of 10^6 takes four rounds of
-// dependent loads instead of twenty). Every lane takes part and gets the answer.
-__device__ __forceinline__ int64_t warp_lower_bound(const int32_t *__restrict__ adj, int64_t lo, int64_t hi,
-                                                    int32_t w)
-{
-    const int lane = threadIdx.x & 31;
-    while (hi - lo > 32) {
-        const int64_t step = (hi - lo + 31) / 32;
-        const int64_t p = lo + (int64_t)lane * step;
-        const bool ge = p < hi ? __ldg(adj + p) >= w : true;
-        const unsigned m = __ballot_sync(0xffffffffu, ge);
-        const int k = m ? __ffs(m) - 1 : 32;
-        if (k == 0) return lo;                       // adj[lo] >= w already
-        const int64_t nhi = lo + (int64_t)k * step;  // the crossing lies in (p_{k-1}, p_k]
-        lo = lo + (int64_t)(k - 1) * step + 1;
-        hi = nhi < hi ? nhi : hi;
-    }
-    const bool ge = lo + lane < hi ? __ldg(adj + lo + lane) >= w : false;
-    const unsigned m = __ballot_sync(0xffffffffu, ge);
-    return m ? lo + __ffs(m) - 1 : hi;
-}
-
-constexpr int kShortSearch = 64;   // lists up to this long are searched by one lane
-
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const OffT *__restrict__ off,
                                                        const int32_t *__restrict__ adj, const int2 *__restrict__ fp,
                                                        const int32_t *__restrict__ lab,
-                                                       const int32_t *__restrict__ kmin, unsigned long long *key,
+                                                       const int32_t *__restrict__ kmin,
+                                                       const int32_t *__restrict__ parc, unsigned long long *key,
                                                        uint32_t *key_bits, int64_t nnz, int *err)
 {
-    // kVPer vertices per thread and step, each round of their loads issued together;
-    // the loop test is the warp's, since long head lists are searched warp-wide
+    // kVPer vertices per thread and step, each round of their loads issued together
     const int64_t T = (int64_t)gridDim.x * kThreads;
-    const int lane = threadIdx.x & 31;
-    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 - lane < n; v0 += T * kVPer) {
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
         uint32_t lbl = 0;
         int32_t hd[kVPer];
 #pragma unroll
@@ -327,51 +306,34 @@ __global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const OffT *__
 #pragma unroll
         for (int k = 0; k < kVPer; ++k)
             if ((lbl >> k) & 1u) ks[k] = key[v0 + k * T];
-        // the head's arc to the smallest class member adjacent to it
-        int64_t lo[kVPer], hi[kVPer];
-        int32_t w[kVPer];
-        uint32_t srch = 0, lng = 0;
 #pragma unroll
         for (int k = 0; k < kVPer; ++k) {
             if (!((lbl >> k) & 1u) || ks[k] != kKeyHead) continue;
-            w[k] = kmin[v0 + k * T];
-            lo[k] = off[hd[k]];
-            hi[k] = off[hd[k] + 1];
-            srch |= 1u << k;
-            if (hi[k] - lo[k] > kShortSearch) lng |= 1u << k;
-        }
-#pragma unroll
-        for (int k = 0; k < kVPer; ++k) {
-            if (!((srch >> k) & 1u) || ((lng >> k) & 1u)) continue;
-            int64_t a = lo[k], b = hi[k];
-            while (a < b) {
-                const int64_t mid = (a + b) >> 1;
-                if (adj[mid] < w[k]) a = mid + 1; else b = mid;
+            // the head's arc to the smallest class member adjacent to it: the tree arc
+            // head -> top when the top is that member and First-CC kept its position,
+            // else a binary search of the head's list
+            const int64_t v = v0 + k * T;
+            const int32_t w = kmin[v], h = hd[k];
+            if (w == v) {
+                const int32_t pa = parc[v];
+                if (pa >= 0) {
+                    ks[k] = (unsigned long long)pa;
+                    key[v] = ks[k];
+                    continue;
+                }
             }
-            lo[k] = a;
-        }
-#pragma unroll
-        for (int k = 0; k < kVPer; ++k) {
-            unsigned todo = __ballot_sync(0xffffffffu, (lng >> k) & 1u);
-            while (todo) {
-                const int src = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const int64_t a = __shfl_sync(0xffffffffu, lo[k], src), b = __shfl_sync(0xffffffffu, hi[k], src);
-                const int32_t ww = __shfl_sync(0xffffffffu, w[k], src);
-                const int64_t r = warp_lower_bound(adj, a, b, ww);
-                if (lane == src) lo[k] = r;
+            int64_t lo = off[h], hi = off[h + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (adj[mid] < w) lo = mid + 1; else hi = mid;
             }
-        }
-#pragma unroll
-        for (int k = 0; k < kVPer; ++k) {
-            if (!((srch >> k) & 1u)) continue;
-            if (lo[k] >= hi[k] || adj[lo[k]] != w[k]) {
+            if (lo >= (int64_t)off[h + 1] || adj[lo] != w) {
                 atomicOr(err, kErrIndex);
                 lbl &= ~(1u << k);
                 continue;
             }
-            ks[k] = (unsigned long long)lo[k];
-            key[v0 + k * T] = ks[k];
+            ks[k] = (unsigned long long)lo;
+            key[v] = ks[k];
         }
 #pragma unroll
         for (int k = 0; k < kVPer; ++k)
@@ -562,22 +524,24 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     const int gv = grid_for(L, ceil_div(n, kThreads));
     const int64_t ntiles = ceil_div(nnz, kWTile);
     const int64_t nwords = ceil_div(nnz, 32);
-    long long *klist_n = d.counters + 10;
+    long long *klist_n = d.counters + 10, *nhead_n = d.counters + 13;
     CK(cudaMemsetAsync(d.scanb, 0, ceil_div(n, 32) * sizeof(uint32_t), L.s));
     CK(cudaMemsetAsync(d.kmin, 0xff, n * sizeof(int32_t), L.s));
     CK(cudaMemsetAsync(klist_n, 0, sizeof(long long), L.s));
+    CK(cudaMemsetAsync(nhead_n, 0, sizeof(long long), L.s));
     k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.lab, d.nh, d.smin, is_ap, d.key, d.kmin, d.scanb,
-                                              d.klist, d.klist_cap, klist_n, d.stats, d.err);
+                                              d.klist, d.klist_cap, klist_n, nhead_n, d.stats, d.err);
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
-        k_key_adj<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, d.err);
+        k_key_adj<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, nhead_n, d.err);
         L.mark("k_key_adj");
         k_key_scan<OffT><<<L.grid, kThreads, 0, L.s>>>(off, adj, klist_n, d.klist, d.dirb, d.lab, d.fp, d.smin,
                                                        d.key);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
-        k_key_bits<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, d.key, d.key_bits, nnz, d.err);
+        k_key_bits<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, d.parc, d.key, d.key_bits, nnz,
+                                                    d.err);
         L.mark("k_key_bits");
         CK(cudaGetLastError());
         CK(launch_scan_popc(d, d.key_bits, d.key_pre, nwords, L));

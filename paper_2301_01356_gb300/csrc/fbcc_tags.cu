@@ -20,10 +20,19 @@ namespace fbcc {
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kThreads)
 
-// first by vertex as a compact array for the arc passes' gathers.
-__global__ void __launch_bounds__(kThreads) k_first_of(int64_t n, const int2 *__restrict__ fp, int32_t *first4)
+// first by vertex as a compact array for the arc passes' gathers, and {first,
+// last} by vertex for the fence test (last gathered here from the preorder-indexed
+// array, in a pass with many loads in flight, so that the query kernel needs one
+// independent gather per parent instead of two dependent ones).
+__global__ void __launch_bounds__(kThreads) k_first_of(int64_t n, const int2 *__restrict__ fp,
+                                                       const int32_t *__restrict__ lastp, int32_t *first4, int2 *fl)
 {
-    GRID_STRIDE(v, n) first4[v] = fp[v].x;
+    GRID_STRIDE(v, n)
+    {
+        const int32_t f = fp[v].x;
+        first4[v] = f;
+        fl[v] = make_int2(f, (uint32_t)f < (uint64_t)n ? __ldg(lastp + f) : -1);
+    }
 }
 
 // w1/w2 over the arcs, one atomic per run of equal sources per thread, and the
@@ -109,10 +118,11 @@ __global__ void __launch_bounds__(kThreads) k_w12(const OffT *__restrict__ off, 
     }
 }
 
-// Per RMQ tile: inclusive prefix min of w1 and max of w2 from the tile start, and
-// the tile's min/max (level 0 of the tile sparse table).
+// Per RMQ tile: inclusive prefix min of w1 and max of w2 from the tile start (one
+// 8-byte pair per position: the query gathers both at once), and the tile's
+// min/max (level 0 of the tile sparse table).
 __global__ void __launch_bounds__(kThreads) k_rmq_prefix(int64_t n, const int32_t *__restrict__ w1,
-                                                         const int32_t *__restrict__ w2, int32_t *pmin, int32_t *pmax,
+                                                         const int32_t *__restrict__ w2, int2 *pmm,
                                                          int32_t *tmin, int32_t *tmax)
 {
     constexpr int kPer = kRmqTile / kThreads;  // 4 positions per thread
@@ -175,16 +185,13 @@ __global__ void __launch_bounds__(kThreads) k_rmq_prefix(int64_t n, const int32_
             b[j] = b[j] > emx ? b[j] : emx;
         }
         if (whole) {
-            *reinterpret_cast<int4 *>(pmin + p0) = make_int4(a[0], a[1], a[2], a[3]);
-            *reinterpret_cast<int4 *>(pmax + p0) = make_int4(b[0], b[1], b[2], b[3]);
+            int4 *o = reinterpret_cast<int4 *>(pmm + p0);
+            o[0] = make_int4(a[0], b[0], a[1], b[1]);
+            o[1] = make_int4(a[2], b[2], a[3], b[3]);
         } else {
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) {
-                if (p0 + j < n) {
-                    pmin[p0 + j] = a[j];
-                    pmax[p0 + j] = b[j];
-                }
-            }
+            for (int j = 0; j < kPer; ++j)
+                if (p0 + j < n) pmm[p0 + j] = make_int2(a[j], b[j]);
         }
         if (threadIdx.x == 0) {
             tmin[t] = tmn;
@@ -230,21 +237,22 @@ __global__ void __launch_bounds__(kThreads) k_rmq_level(int64_t ntiles, int j0, 
 // inside the tile are flattened in shared memory (pointer doubling); a pointer that
 // leaves the tile marks its target in `ext` for the cross-tile resolution.
 __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t *__restrict__ w1,
-                                                        const int32_t *__restrict__ w2, const int32_t *__restrict__ pmin,
-                                                        const int32_t *__restrict__ pmax, const int32_t *__restrict__ tmin,
+                                                        const int32_t *__restrict__ w2, const int2 *__restrict__ pmm,
+                                                        const int32_t *__restrict__ tmin,
                                                         const int32_t *__restrict__ tmax, int64_t st_stride,
                                                         const int32_t *__restrict__ ord,
                                                         const int32_t *__restrict__ porig,
-                                                        const int32_t *__restrict__ first4,
+                                                        const int2 *__restrict__ fl,
                                                         const int32_t *__restrict__ lastp, uint8_t *vbits, int32_t *lp,
                                                         uint8_t *ext, int32_t *low_out, int32_t *high_out, int *err)
 {
     constexpr int kPer = kRmqTile / kThreads;
     constexpr int kNChunk = kRmqTile / kChunk;
+    constexpr int kCLv = 5;                                 // sparse-table levels over the 32 chunks
     __shared__ int32_t s1[kRmqTile], s2[kRmqTile];          // w1, w2
     __shared__ int32_t pre1[kRmqTile], pre2[kRmqTile];      // prefix within the chunk
     __shared__ int32_t suf1[kRmqTile], suf2[kRmqTile];      // suffix within the chunk
-    __shared__ int32_t c1[kNChunk], c2[kNChunk];            // chunk extrema
+    __shared__ int32_t c1[kCLv][kNChunk], c2[kCLv][kNChunk];// sparse table of chunk extrema (level 0: chunks)
     __shared__ int32_t cs1[kNChunk], cs2[kNChunk];          // suffix over chunks (tile suffix helper)
     __shared__ int32_t sp[kRmqTile];                        // plain pointers of the tile
     const int64_t ntiles = (n + kRmqTile - 1) / kRmqTile;
@@ -269,11 +277,21 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                 if (lane + o < 32) { sx = a2 < sx ? a2 : sx; sy = b2 > sy ? b2 : sy; }
             }
             pre1[i] = px; pre2[i] = py; suf1[i] = sx; suf2[i] = sy;
-            if (lane == 31) { c1[c] = px; c2[c] = py; }
+            if (lane == 31) { c1[0][c] = px; c2[0][c] = py; }
         }
         __syncthreads();
         if (wid == 0) {
-            int32_t x = c1[lane], y = c2[lane];
+            // levels 1..4 of the chunk sparse table (level l covers 2^l chunks), and the
+            // suffix extrema over chunks
+            int32_t sa = c1[0][lane], sb = c2[0][lane];
+            for (int lv = 1; lv < kCLv; ++lv) {
+                const int h = 1 << (lv - 1);
+                const int32_t a = __shfl_down_sync(0xffffffffu, sa, h), b = __shfl_down_sync(0xffffffffu, sb, h);
+                if (lane + h < kNChunk) { sa = a < sa ? a : sa; sb = b > sb ? b : sb; }
+                c1[lv][lane] = sa;
+                c2[lv][lane] = sb;
+            }
+            int32_t x = c1[0][lane], y = c2[0][lane];
             for (int o = 1; o < 32; o <<= 1) {
                 int32_t a = __shfl_down_sync(0xffffffffu, x, o), b = __shfl_down_sync(0xffffffffu, y, o);
                 if (lane + o < 32) { x = a < x ? a : x; y = b > y ? b : y; }
@@ -282,6 +300,37 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
             cs2[lane] = y;
         }
         __syncthreads();
+        // every position's range end, vertex and parent, and then the parent's
+        // preorder interval and the range end's prefix extrema, all in flight
+        // before the range queries
+        int32_t ev[kPer], vv[kPer], xv[kPer], fxv[kPer], lxv[kPer];
+        int2 pe[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t p = base + threadIdx.x + k * kThreads;
+            ev[k] = (int32_t)p;
+            vv[k] = -1;
+            xv[k] = -1;
+            if (p < n) {
+                ev[k] = lastp[p];
+                vv[k] = ord[p];
+                xv[k] = porig[p];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t p = base + threadIdx.x + k * kThreads;
+            fxv[k] = -1;
+            lxv[k] = -1;
+            pe[k] = make_int2(INT32_MAX, INT32_MIN);
+            if (p >= n) continue;
+            if ((uint32_t)xv[k] < (uint64_t)n) {
+                const int2 f = __ldg(fl + xv[k]);
+                fxv[k] = f.x;
+                lxv[k] = f.y;
+            }
+            if (ev[k] >= base + kRmqTile && ev[k] < n) pe[k] = __ldg(pmm + ev[k]);
+        }
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             // this warp holds one chunk (lane = position in it): a sparse table of
@@ -290,7 +339,7 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
             const int i = threadIdx.x + k * kThreads;
             const int64_t p = base + i;
             const bool valid = p < n;
-            int32_t e = valid ? lastp[p] : (int32_t)p;
+            int32_t e = ev[k];
             if (valid && (e < p || e >= n)) { atomicOr(err, kErrIndex); e = (int32_t)p; }
             const int ci = i / kChunk;
             const int jl = (int)(e - base) - ci * kChunk;          // e's lane when inside the chunk
@@ -310,16 +359,19 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                 const int32_t ya = __shfl_sync(0xffffffffu, ra, src), yb = __shfl_sync(0xffffffffu, rb, src);
                 if (lv == kl) { lo = ya < ra ? ya : ra; hi = yb > rb ? yb : rb; }
             }
-            if (kl == 5) { lo = c1[ci]; hi = c2[ci]; }               // the whole chunk
+            if (kl == 5) { lo = c1[0][ci]; hi = c2[0][ci]; }         // the whole chunk
             if (!valid) continue;
             if (e < base + kRmqTile) {
                 const int je = (int)(e - base), ce = je / kChunk;
                 if (ci != ce) {
                     lo = suf1[i] < pre1[je] ? suf1[i] : pre1[je];
                     hi = suf2[i] > pre2[je] ? suf2[i] : pre2[je];
-                    for (int c = ci + 1; c < ce; ++c) {
-                        lo = c1[c] < lo ? c1[c] : lo;
-                        hi = c2[c] > hi ? c2[c] : hi;
+                    if (ce > ci + 1) {   // whole chunks ci+1 .. ce-1: two overlapping table ranges
+                        const int cl = ce - ci - 1, lv = 31 - __clz(cl), b = ce - (1 << lv);
+                        const int32_t x = c1[lv][ci + 1] < c1[lv][b] ? c1[lv][ci + 1] : c1[lv][b];
+                        const int32_t y = c2[lv][ci + 1] > c2[lv][b] ? c2[lv][ci + 1] : c2[lv][b];
+                        lo = x < lo ? x : lo;
+                        hi = y > hi ? y : hi;
                     }
                 }
             } else {
@@ -339,21 +391,21 @@ __global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t
                     lo = x < lo ? x : lo;
                     hi = y > hi ? y : hi;
                 }
-                lo = pmin[e] < lo ? pmin[e] : lo;
-                hi = pmax[e] > hi ? pmax[e] : hi;
+                lo = pe[k].x < lo ? pe[k].x : lo;
+                hi = pe[k].y > hi ? pe[k].y : hi;
             }
             if (low_out) {
                 low_out[p] = lo;
                 high_out[p] = hi;
             }
-            const int32_t v = ord[p], x = porig[p];
+            const int32_t v = vv[k], x = xv[k];
             int32_t ptr = (int32_t)p;
             if (in_range(v, n, err) && x < n) {
                 uint8_t bits = 0;
                 if (x >= 0) {
                     if (lo == (int32_t)p && hi <= e) bits |= 1;  // bridge: nothing leaves T_v
-                    const int32_t fx = __ldg(first4 + x);
-                    const bool fence = fx <= lo && (uint32_t)fx < (uint64_t)n && __ldg(lastp + fx) >= hi;
+                    const int32_t fx = fxv[k];
+                    const bool fence = !in_range(fx, n, err) || (fx <= lo && lxv[k] >= hi);
                     if (fence) bits |= 2;
                     else ptr = fx;                                // plain tree edge: in G'
                 }
@@ -391,16 +443,16 @@ template <typename OffT>
 cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, bool keep_low_high, const Launch &L)
 {
-    const int64_t ntiles = ceil_div(nnz, kWTile);
-    k_first_of<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(n, d.fp, d.first4);
+    k_first_of<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(n, d.fp, d.lastp, d.first4, d.fl);
     L.mark("k_first_of");
+    const int64_t ntiles = ceil_div(nnz, kWTile);
     if (nnz > 0) {
         k_w12<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
             off, adj, nnz, d.tile_v, ntiles, d.fp, d.first4, d.w1, d.w2, d.dirb, n, d.err, vec);
         L.mark("k_w12");
     }
     const int64_t rt = ceil_div(n, kRmqTile);
-    k_rmq_prefix<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax);
+    k_rmq_prefix<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmm, d.tmin, d.tmax);
     L.mark("k_rmq_prefix");
     int top = 0;   // levels 1 .. top are needed: 2^top <= rt
     while ((2ll << top) <= rt) ++top;
@@ -413,8 +465,8 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
     // Last-CC starts here: plain-edge pointers by preorder number
     cudaError_t e = cudaMemsetAsync(d.ext, 0, n, L.s);
     if (e != cudaSuccess) return e;
-    k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmin, d.pmax, d.tmin, d.tmax,
-                                                       d.rmq_tiles_max, d.ord, d.porig, d.first4, d.lastp,
+    k_rmq_query<<<grid_for(L, rt), kThreads, 0, L.s>>>(n, d.w1, d.w2, d.pmm, d.tmin, d.tmax,
+                                                       d.rmq_tiles_max, d.ord, d.porig, d.fl, d.lastp,
                                                        d.vbits, d.lp, d.ext, keep_low_high ? d.low : nullptr,
                                                        keep_low_high ? d.high : nullptr, d.err);
     L.mark("k_rmq_query");
