@@ -146,7 +146,7 @@ class ClockSampler:
 # Algorithm 1's steps as the profiled kernels run them: a phase starts at its first
 # kernel and lasts until the next phase starts.
 PHASES = ("first_cc", "rooting", "tagging", "last_cc", "outputs")
-PHASE_START = {"k_link_prep": "rooting", "k_link": "rooting", "k_first_of": "tagging", "k_ext_compact": "last_cc", "k_ap_keys": "outputs"}
+PHASE_START = {"k_cc_count": "rooting", "k_link": "rooting", "k_first_of": "tagging", "k_ext_compact": "last_cc", "k_ap_keys": "outputs"}
 
 
 def phase_bytes(n: int, nnz: int, n_cc: int, off_bytes: int) -> dict:
@@ -179,7 +179,7 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_cc_hook": arc_cc, "k_cc_local": arc_cc, "k_cc_hook_skip": arc_cc, "k_cc_hook_cross": 0,
         "k_cc_sample": 0, "k_mark_big": 0, "k_cc_pick_big": 0,
         # Rooting
-        "k_link_prep": 0, "k_link": 8 * A, "k_hub_order": 0, "k_succ_rulers": 16 * A, "k_chase": 8 * A, "k_lvl_rulers": 0, "k_lvl_chase": 0,
+        "k_cc_count": 0, "k_cc_place": 0, "k_permute_te": 0, "k_scan_i32": 0, "k_link": 8 * A, "k_hub_order": 0, "k_succ_rulers": 16 * A, "k_chase": 8 * A, "k_lvl_rulers": 0, "k_lvl_chase": 0,
         "k_top": 0, "k_lvl_expand": 0, "k_jump": 0, "k_comp_size": 0, "k_place_records": 8 * A, "k_preorder": 8 * A + 16 * n,
         # Tagging
         "k_first_of": 0, "k_w12": B * n + 4 * nnz + 8 * n, "k_rmq_prefix": 8 * n, "k_rmq_level": 0,
@@ -189,7 +189,7 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_last_cc_cross": B * n + 4 * nnz + 20 * n, "k_last_cc_cross_skip": B * n + 4 * nnz + 20 * n,
         "k_lcc_sample": 0, "k_pos_compress": 0, "k_pos_pick_big": 0, "k_final_label": 8 * n,
         # Outputs
-        "k_ap_keys": 12 * n, "k_key_adj": 0, "k_key_scan": 0, "k_key_bits": 0, "k_scan_popc": 0, "k_rank": 0, "k_fo": 0,
+        "k_ap_keys": 12 * n, "k_key_list": 0, "k_key_adj": 0, "k_key_scan": 0, "k_key_bits": 0, "k_scan_popc": 0, "k_rank": 0, "k_fo": 0,
         "k_edge_out": B * n + 9 * nnz, "k_bcc_base": 0, "k_batch_stats": 0, "k_finish": 0,
     }
     return table.get(kernel)
@@ -302,10 +302,12 @@ def tuned_config(args) -> dict:
     """The autotuner's choice for this workload (tuning.json), overridden by any knob
     given on the command line."""
     from paper_2301_01356_gb300 import batch as B
-    cfg = dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0, lcc_sample=0, rank_variant=0, grid_ctas=0)
+    cfg = dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0, lcc_sample=0, rank_variant=0, grid_ctas=0,
+               cc_order=0, hub_deg=0)
     if args.config == "tuned":
         cfg.update(B.load_tuning().get("graphs", {}).get(args.workload, {}).get("config", {}))
-    for k in ("ruler_stride", "cc_sample", "chase_chains", "cc_local", "lcc_sample", "rank_variant", "grid_ctas"):
+    for k in ("ruler_stride", "cc_sample", "chase_chains", "cc_local", "lcc_sample", "rank_variant", "grid_ctas",
+              "cc_order", "hub_deg"):
         v = getattr(args, k)
         if v is not None:
             cfg[k] = v
@@ -862,6 +864,8 @@ def main(argv=None):
     ap.add_argument("--lcc-sample", type=int, default=None, help="Last-CC: cross edges sampled per vertex (0 = off)")
     ap.add_argument("--rank-variant", type=int, default=None, help="list ranking: 0 sampled levels, 1 pointer jumping")
     ap.add_argument("--grid-ctas", type=int, default=None, help="CTAs of the persistent grid (0 = 8 per SM)")
+    ap.add_argument("--cc-order", type=int, default=None, help="rooting: forest renumbered by component (1 = on)")
+    ap.add_argument("--hub-deg", type=int, default=None, help="hub threshold in arcs (0 = 256, -1 = no hubs)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--query-count", type=int, default=1 << 24, help="queries timed after the solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -81,6 +81,14 @@ typedef struct {
     int32_t rank_variant;  /* list ranking above the rulers: 0 = sample the ruler lists again and rank
                               the top level in one CTA (default); 1 = pointer jumping (Wyllie) over
                               the ruler lists, a fixed number of grid-wide rounds */
+    int32_t cc_order;      /* rooting: 1 = renumber the spanning forest's edges component by component
+                              before the Euler tours are built, so that each tour's arcs are
+                              contiguous (0 = off) */
+    int32_t hub_deg;       /* rooting and keys: vertices of at least this many arcs are hubs, whose
+                              forest-arc lists are split to spread their atomic pushes, and the
+                              forest records each tree edge's CSR position (which lets a hub head
+                              name its BCC's key without searching its list); 0 = 256, -1 = off
+                              (graphs without hubs), else >= 32 */
 } fbcc_config;
 
 /* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds.

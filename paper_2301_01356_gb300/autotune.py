@@ -7,6 +7,8 @@ The knobs, each a runtime choice of the library (fbcc_config):
   - ruler stride of the list ranking, walks a thread advances together
     (chase_chains), and the ranking above the rulers (sampled levels with a
     single-CTA top, or Wyllie pointer jumping);
+  - the forest edges renumbered component by component before the tours (cc_order);
+  - hub handling (split forest-arc lists and kept tree-arc positions) on or off;
   - the persistent grid size in CTAs per SM.
 The thread-block shape (256 threads, 8 items per thread, 1024-position RMQ tiles)
 is a compile-time constant: the shared-memory layouts of every arc and tile pass
@@ -32,7 +34,8 @@ import numpy as np
 from . import batch as B
 from . import fbcc, graphgen as gg
 
-DEFAULT = dict(ruler_stride=16, cc_local=0, cc_sample=0, lcc_sample=0, chase_chains=1, rank_variant=0, grid_ctas=0)
+DEFAULT = dict(ruler_stride=16, cc_local=0, cc_sample=0, lcc_sample=0, chase_chains=1, rank_variant=0, grid_ctas=0,
+               cc_order=0, hub_deg=0)
 KNOBS = [
     ("cc", [dict(cc_local=0, cc_sample=0), dict(cc_local=8192, cc_sample=0), dict(cc_local=16384, cc_sample=0),
             dict(cc_local=0, cc_sample=2)]),
@@ -40,6 +43,8 @@ KNOBS = [
     ("lcc_sample", [dict(lcc_sample=q) for q in (0, 2)]),
     ("chase_chains", [dict(chase_chains=c) for c in (1, 2)]),
     ("rank_variant", [dict(rank_variant=r) for r in (0, 1)]),
+    ("cc_order", [dict(cc_order=o) for o in (0, 1)]),
+    ("hub_deg", [dict(hub_deg=h) for h in (0, -1)]),
     ("grid_ctas", [dict(grid_ctas=g) for g in (0, -4, -16)]),   # -k: k CTAs per SM (0: 8 per SM)
 ]
 

@@ -96,7 +96,13 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.te_u = c.take<int32_t>(N);
     d.te_v = c.take<int32_t>(N);
     d.te_a = c.take<int32_t>(N);
+    d.hub_cap = Z / kHubMinDeg + 1 < kHubCap ? Z / kHubMinDeg + 1 : kHubCap;
+    d.hubidx = c.take<int32_t>(N);            // (set by First-CC: not in the local-first list's space)
+    d.hubvert = c.take<int32_t>(d.hub_cap);
     const size_t xl_from = c.used;
+    d.te2_u = c.take<int32_t>(N);
+    d.te2_v = c.take<int32_t>(N);
+    d.te2_a = c.take<int32_t>(N);
     d.lhead = c.take<int32_t>(N);
     d.nxt = c.take<int32_t>(2 * N);
     d.rhead = c.take<uint8_t>(d.ruler_max);
@@ -129,11 +135,8 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.csize = c.take<int32_t>(N + 1);
     d.vbase = c.take<int32_t>(N + 1);
     d.rec = c.take<int2>(2 * N);
-    d.hub_cap = Z / kHubDeg + 1 < kHubCap ? Z / kHubDeg + 1 : kHubCap;
-    d.hubidx = c.take<int32_t>(N);
     d.hubhead = c.take<int32_t>(d.hub_cap * kHubSub);
     d.hubnext = c.take<int32_t>(d.hub_cap * kHubSub);
-    d.hubvert = c.take<int32_t>(d.hub_cap);
     const size_t rooting_end = c.used;
     {
         const size_t at = (xl_from + 255) & ~size_t(255);
@@ -158,7 +161,7 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.smin = c.take<int32_t>(N);
     d.nh = c.take<int32_t>(N);
     d.key = c.take<unsigned long long>(N);
-    d.scanb = c.take<uint32_t>(ceil_div(N, 32) + 1);
+    d.scanv = c.take<uint8_t>(N);
     d.klist_cap = N + ceil_div(Z, kKeyChunk) + 2;
     d.klist = c.take<int2>(d.klist_cap);
     d.kmin = c.take<int32_t>(N);
@@ -208,6 +211,8 @@ static fbcc_config default_config()
     c.cc_local = 0;
     c.lcc_sample = 0;
     c.rank_variant = 0;
+    c.cc_order = 0;
+    c.hub_deg = 0;
     return c;
 }
 
@@ -327,6 +332,10 @@ fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
         c.lcc_sample = cfg->lcc_sample;
         if (cfg->rank_variant < 0 || cfg->rank_variant > 1) return FBCC_E_INVALID;
         c.rank_variant = cfg->rank_variant;
+        if (cfg->cc_order < 0 || cfg->cc_order > 1) return FBCC_E_INVALID;
+        c.cc_order = cfg->cc_order;
+        if (cfg->hub_deg < -1 || (cfg->hub_deg > 0 && cfg->hub_deg < kHubMinDeg)) return FBCC_E_INVALID;
+        c.hub_deg = cfg->hub_deg;
         if (cfg->chase_chains) {
             if (cfg->chase_chains != 1 && cfg->chase_chains != 2 && cfg->chase_chains != 4) return FBCC_E_INVALID;
             c.chase_chains = cfg->chase_chains;
@@ -400,12 +409,14 @@ cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *ad
     CK(cudaMemsetAsync(d.err, 0, sizeof(int), s));
     CK(cudaMemsetAsync(d.stats, 0, sizeof(fbcc_stats), s));
     if (n > 0) {
-        CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, ws->cfg.cc_local, vec, L));
+        const int hub_deg = ws->cfg.hub_deg == 0 ? kHubDeg : ws->cfg.hub_deg;   // -1: no hubs
+        CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, ws->cfg.cc_local, hub_deg, vec, L));
         CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, ws->cfg.chase_chains,
-                                ws->cfg.rank_variant, L));
+                                ws->cfg.rank_variant, ws->cfg.cc_order, hub_deg > 0, L));
         CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, ws->cfg.profile != 0, L));
         CK(launch_last_cc<OffT>(d, off, adj, n, nnz, ws->cfg.lcc_sample, vec, L));
-        CK(launch_outputs<OffT>(d, off, adj, n, nnz, vec, edge_bcc, bcc_head, is_ap, is_bridge, B, L));
+        CK(launch_outputs<OffT>(d, off, adj, n, nnz, vec, hub_deg > 0, edge_bcc, bcc_head, is_ap, is_bridge, B,
+                                L));
     }
     k_finish<<<1, 1, 0, s>>>(d.err, d.stats);
     L.mark("k_finish");

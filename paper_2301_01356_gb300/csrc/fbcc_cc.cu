@@ -16,9 +16,12 @@ namespace fbcc {
 // tile_v[t] = source of arc t*kWTile; tile_v[ntiles] = source of the last arc.
 // Also resets the union-find and the tree-edge record.
 template <typename OffT>
+// Also finds the hubs (hub_deg > 0): a vertex of at least hub_deg arcs gets a hub
+// slot (while slots last), which rooting uses to split its forest-arc list.
 __global__ void __launch_bounds__(kThreads) k_cc_init(const OffT *__restrict__ off, int64_t n, int64_t nnz,
                                                       int32_t *tile_v, int64_t ntiles, int32_t *uf,
-                                                      int32_t *te_u)
+                                                      int32_t *te_u, int hub_deg, int32_t *hubidx,
+                                                      int32_t *hubvert, int64_t hub_cap, long long *nhub)
 {
     for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
         uf[v] = (int32_t)v;
@@ -27,6 +30,17 @@ __global__ void __launch_bounds__(kThreads) k_cc_init(const OffT *__restrict__ o
         if (e > b) {
             for (int64_t t = (b + kWTile - 1) / kWTile; t * kWTile < e; ++t) tile_v[t] = (int32_t)v;
             if (b <= nnz - 1 && nnz - 1 < e) tile_v[ntiles] = (int32_t)v;
+        }
+        if (hub_deg > 0) {
+            int32_t id = -1;
+            if (e - b >= hub_deg) {
+                const long long k = (long long)atomicAdd((unsigned long long *)nhub, 1ull);
+                if (k < hub_cap) {
+                    id = (int32_t)k;
+                    hubvert[id] = (int32_t)v;
+                }
+            }
+            hubidx[v] = id;
         }
     }
 }
@@ -357,12 +371,18 @@ cudaError_t prepare_cc_local(int V)
 
 template <typename OffT>
 cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                            int cc_sample, int cc_local, bool vec, const Launch &L)
+                            int cc_sample, int cc_local, int hub_deg, bool vec, const Launch &L)
 {
     const int64_t ntiles = ceil_div(nnz, kWTile);
     const int gv = grid_for(L, ceil_div(n, kThreads));
     const int ga = grid_for(L, ceil_div(ntiles, kWarpsPerCta));
-    k_cc_init<OffT><<<gv, kThreads, 0, L.s>>>(off, n, nnz, d.tile_v, ntiles, d.uf, d.te_u);
+    long long *nhub = d.counters + 14;
+    const cudaError_t e0 = cudaMemsetAsync(nhub, 0, sizeof(long long), L.s);
+    if (e0 != cudaSuccess) return e0;
+    // the tree edges' CSR positions are kept only where hubs are in use (their keys read them)
+    int32_t *te_a = hub_deg > 0 ? d.te_a : nullptr;
+    k_cc_init<OffT><<<gv, kThreads, 0, L.s>>>(off, n, nnz, d.tile_v, ntiles, d.uf, d.te_u, hub_deg, d.hubidx,
+                                              d.hubvert, d.hub_cap, nhub);
     L.mark("k_cc_init");
     if (nnz > 0) {
         if (cc_local > 0) {
@@ -372,14 +392,14 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             const cudaError_t e = cudaMemsetAsync(nxl, 0, sizeof(long long), L.s);
             if (e != cudaSuccess) return e;
             k_cc_local<OffT><<<gl, kLocalThreads, cc_local_smem(cc_local, sizeof(OffT) == 8), L.s>>>(
-                off, adj, n, nnz, cc_local, d.uf, d.te_u, d.te_v, d.te_a, d.xl, d.xl_cap, nxl, d.err, vec);
+                off, adj, n, nnz, cc_local, d.uf, d.te_u, d.te_v, te_a, d.xl, d.xl_cap, nxl, d.err, vec);
             L.mark("k_cc_local");
             k_cc_hook_cross<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, cc_local, d.xl,
-                                                           d.xl_cap, nxl, d.uf, d.te_u, d.te_v, d.te_a, d.err, vec);
+                                                           d.xl_cap, nxl, d.uf, d.te_u, d.te_v, te_a, d.err, vec);
             L.mark("k_cc_hook_cross");
         } else if (cc_sample > 0) {
             int32_t *big = reinterpret_cast<int32_t *>(d.counters + 8);
-            k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, d.te_a,
+            k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, te_a,
                                                         d.err);
             L.mark("k_cc_sample");
             k_uf_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
@@ -389,11 +409,11 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             k_mark_big<<<gv, kThreads, 0, L.s>>>(d.uf, n, big, d.bigb);
             L.mark("k_mark_big");
             k_cc_hook_skip<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
-                                                          d.te_a, d.bigb, d.err, vec);
+                                                          te_a, d.bigb, d.err, vec);
             L.mark("k_cc_hook_skip");
         } else {
             k_cc_hook<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
-                                                     d.te_a, d.err, vec);
+                                                     te_a, d.err, vec);
             L.mark("k_cc_hook");
         }
     }
@@ -768,9 +788,9 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
 }
 
 template cudaError_t launch_first_cc<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
-                                              int, bool, const Launch &);
+                                              int, int, bool, const Launch &);
 template cudaError_t launch_first_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,
-                                              int, bool, const Launch &);
+                                              int, int, bool, const Launch &);
 template cudaError_t launch_last_cc<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
                                              bool, const Launch &);
 template cudaError_t launch_last_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,

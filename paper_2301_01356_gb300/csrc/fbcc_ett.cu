@@ -46,6 +46,58 @@ __device__ __forceinline__ int32_t arc_dst(const int32_t *te_u, const int32_t *t
     return (a & 1) ? te_u[a >> 1] : te_v[a >> 1];
 }
 
+// Forest edges renumbered component by component (fbcc_config.cc_order; the paper
+// reorders the CSR after First-CC so that each connected component is contiguous):
+// vertex v, whose slot holds the edge that hooked v (if any), moves to position
+// base(root) + its rank among its component's vertices (in no particular order),
+// so that each Euler tour's arcs 2h, 2h+1 and their link entries are contiguous.
+// Counts and ranks per component: the lanes of a warp with the same root reduce
+// and take their slots with one atomic per group.
+__global__ void __launch_bounds__(kThreads) k_cc_count(int64_t n, const int32_t *__restrict__ uf, int32_t *cnt)
+{
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
+        const int32_t r = v < n ? uf[v] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, r);
+        if (r >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + r, __popc(peers));
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cc_place(int64_t n, const int32_t *__restrict__ uf,
+                                                       const int32_t *__restrict__ base, int32_t *fill,
+                                                       int32_t *pos)
+{
+    const int64_t n_pad = (n + 31) & ~31ll;
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
+        const int32_t r = v < n ? uf[v] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, r);
+        const int leader = __ffs(peers) - 1;
+        int32_t at = 0;
+        if (r >= 0 && lane == leader) at = base[r] + atomicAdd(fill + r, __popc(peers));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (r >= 0) pos[v] = at + __popc(peers & ((1u << lane) - 1u));
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_permute_te(int64_t n, const int32_t *__restrict__ pos,
+                                                         const int32_t *__restrict__ te_u,
+                                                         const int32_t *__restrict__ te_v,
+                                                         const int32_t *__restrict__ te_a, int32_t *u2, int32_t *v2,
+                                                         int32_t *a2, int *err)
+{
+    GRID_STRIDE(h, n)
+    {
+        const int32_t p = pos[h], u = te_u[h];
+        if (!in_range(p, n, err)) continue;
+        u2[p] = u;
+        if (u >= 0) {
+            v2[p] = te_v[h];
+            if (te_a) a2[p] = te_a[h];
+        }
+    }
+}
+
 // Sub-list of edge h at a hub: a multiplicative hash of h, so that the sub-lists do
 // not follow the low bits of the arc ids, which pick the rulers of the ranking (with
 // h mod kHubSub, all of a hub's sampled arcs would fall into two sub-lists and the
@@ -55,34 +107,16 @@ __device__ __forceinline__ int hub_sub(int64_t h)
     return (int)(((uint32_t)h * 2654435761u) >> 27);
 }
 
-// Empty arc lists, and a hub slot for every vertex of graph degree >= kHubDeg
-// (while slots last): its arcs go to kHubSub sub-lists, chosen by edge id, so that
-// the pushes of one hub spread over kHubSub words.
-template <typename OffT>
-__global__ void __launch_bounds__(kThreads) k_link_prep(int64_t n, const OffT *__restrict__ off, int32_t *lhead,
-                                                        int32_t *hubidx, int32_t *hubhead, int32_t *hubvert,
-                                                        int64_t hub_cap, long long *nhub)
-{
-    GRID_STRIDE(v, n)
-    {
-        lhead[v] = -1;
-        int32_t id = -1;
-        if ((int64_t)off[v + 1] - (int64_t)off[v] >= kHubDeg) {
-            const long long k = (long long)atomicAdd((unsigned long long *)nhub, 1ull);
-            if (k < hub_cap) {
-                id = (int32_t)k;
-                hubvert[id] = (int32_t)v;
-                for (int s = 0; s < kHubSub; ++s) hubhead[(int64_t)id * kHubSub + s] = -1;
-            }
-        }
-        hubidx[v] = id;
-    }
-}
-
+// Forest-arc lists: each vertex's arcs chained through nxt by atomicExch on its list
+// head. A hub (hubidx >= 0, found by First-CC; null when hubs are off) pushes onto
+// one of kHubSub sub-lists chosen by a hash of the edge id instead, so that the
+// exchanges of its many forest edges spread over kHubSub words; sub-list s of hub
+// slot i has its head at hubhead[s * hub_cap + i], so that a hub's heads lie in
+// different cache lines (atomics on one line are processed one at a time).
 __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__restrict__ te_u,
                                                    const int32_t *__restrict__ te_v,
                                                    const int32_t *__restrict__ hubidx, int32_t *lhead,
-                                                   int32_t *hubhead, int32_t *nxt)
+                                                   int32_t *hubhead, int64_t hub_cap, int32_t *nxt)
 {
     // four edges per thread and step: their eight exchanges in flight together
     constexpr int kPer = 4;
@@ -99,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             hu[k] = hv[k] = -1;
-            if (u[k] < 0) continue;
+            if (u[k] < 0 || !hubidx) continue;
             hu[k] = __ldg(hubidx + u[k]);
             hv[k] = __ldg(hubidx + v[k]);
         }
@@ -109,8 +143,8 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
             if (u[k] < 0) continue;
             const int64_t h = h0 + k * T;
             const int s = hub_sub(h);   // the sub-list of both arcs of edge h
-            o[k].x = atomicExch(hu[k] >= 0 ? hubhead + (int64_t)hu[k] * kHubSub + s : lhead + u[k], (int32_t)(2 * h));
-            o[k].y = atomicExch(hv[k] >= 0 ? hubhead + (int64_t)hv[k] * kHubSub + s : lhead + v[k],
+            o[k].x = atomicExch(hu[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hu[k] : lhead + u[k], (int32_t)(2 * h));
+            o[k].y = atomicExch(hv[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hv[k] : lhead + v[k],
                                 (int32_t)(2 * h + 1));
         }
 #pragma unroll
@@ -136,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_order(const long long *__restr
     static_assert(kHubSub == 32, "a lane per sub-list");
     for (int64_t i = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; i < cnt;
          i += ((int64_t)gridDim.x * kThreads) >> 5) {
-        const int32_t hd = hubhead[i * kHubSub + lane];
+        const int32_t hd = hubhead[(int64_t)lane * hub_cap + i];
         const unsigned m = __ballot_sync(0xffffffffu, hd >= 0);
         const unsigned later = lane == 31 ? 0u : m & ~((2u << lane) - 1u);
         const int nx = later ? __ffs(later) - 1 : -1;
@@ -203,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_succ_rulers(int64_t n, const int32
             if (eu[k] < 0) continue;
             const int32_t x = (j & 1) ? ev[k] : eu[k], y = (j & 1) ? eu[k] : ev[k];
             int32_t nxr = nx[j ^ 1];   // nxt of the reverse arc
-            if (nxr < 0) {             // the reverse arc ends a (sub-)list of y
+            if (nxr < 0 && hubidx) {   // the reverse arc ends a (sub-)list of y
                 const int32_t hy = hubidx[y];
                 if (hy >= 0) nxr = hubnext[(int64_t)hy * kHubSub + hub_sub(h0 + k)];
             }
@@ -658,11 +692,11 @@ __global__ void __launch_bounds__(kThreads) k_place_records(int64_t n, const int
         if (p0 < p1) {
             rec[p0] = make_int2(v, u);
             rec[p1] = make_int2(kUpRec - v, p1 - p0);
-            parc[v] = te_a[h];
+            if (parc) parc[v] = te_a[h];
         } else {
             rec[p1] = make_int2(u, v);
             rec[p0] = make_int2(kUpRec - u, p0 - p1);
-            parc[u] = -1;
+            if (parc) parc[u] = -1;
         }
     }
 }
@@ -745,26 +779,51 @@ __global__ void __launch_bounds__(kThreads, 5) k_preorder(int64_t n2, const int2
 
 template <typename OffT>
 cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           int ruler_stride, int chase_chains, int rank_variant, const Launch &L)
+                           int ruler_stride, int chase_chains, int rank_variant, int cc_order, bool hubs,
+                           const Launch &L)
 {
+    (void)off;
+    const int32_t *te_u = d.te_u, *te_v = d.te_v, *te_a = d.te_a;
+    if (cc_order) {
+        // counts, bases and positions live in the link array, which is free until the
+        // successor pass (4n int32 slots; 3n + 1 are needed)
+        int32_t *cnt = reinterpret_cast<int32_t *>(d.link), *fill = cnt + n + 1, *pos = fill + n;
+        cudaError_t e0 = cudaMemsetAsync(cnt, 0, (2 * n + 1) * sizeof(int32_t), L.s);
+        if (e0 != cudaSuccess) return e0;
+        const int gn = grid_for(L, ceil_div(n, kThreads));
+        k_cc_count<<<gn, kThreads, 0, L.s>>>(n, d.uf, cnt);
+        L.mark("k_cc_count");
+        e0 = launch_scan_i32(d, cnt, n, L);
+        if (e0 != cudaSuccess) return e0;
+        k_cc_place<<<gn, kThreads, 0, L.s>>>(n, d.uf, cnt, fill, pos);
+        L.mark("k_cc_place");
+        k_permute_te<<<gn, kThreads, 0, L.s>>>(n, pos, d.te_u, d.te_v, hubs ? d.te_a : nullptr, d.te2_u, d.te2_v,
+                                               d.te2_a, d.err);
+        L.mark("k_permute_te");
+        te_u = d.te2_u;
+        te_v = d.te2_v;
+        te_a = d.te2_a;
+    }
     (void)nnz;
     const int gv = grid_for(L, ceil_div(n, kThreads));
     const int ga = grid_for(L, ceil_div(2 * n, kThreads));
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-    long long *nhub = d.counters + 14;
-    CK(cudaMemsetAsync(nhub, 0, sizeof(long long), L.s));
-    k_link_prep<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.lhead, d.hubidx, d.hubhead, d.hubvert, d.hub_cap, nhub);
-    L.mark("k_link_prep");
-    k_link<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.hubidx, d.lhead, d.hubhead, d.nxt);
+    long long *nhub = d.counters + 14;   // hub slots taken by First-CC
+    const int32_t *hubidx = hubs ? d.hubidx : nullptr;
+    CK(cudaMemsetAsync(d.lhead, 0xff, n * sizeof(int32_t), L.s));
+    if (hubs) CK(cudaMemsetAsync(d.hubhead, 0xff, d.hub_cap * kHubSub * sizeof(int32_t), L.s));
+    k_link<<<gv, kThreads, 0, L.s>>>(n, te_u, te_v, hubidx, d.lhead, d.hubhead, d.hub_cap, d.nxt);
     L.mark("k_link");
-    k_hub_order<<<grid_for(L, ceil_div(d.hub_cap * 32, kThreads)), kThreads, 0, L.s>>>(nhub, d.hub_cap, d.hubvert,
-                                                                                      d.hubhead, d.hubnext, d.lhead);
-    L.mark("k_hub_order");
+    if (hubs) {
+        k_hub_order<<<grid_for(L, ceil_div(d.hub_cap * 32, kThreads)), kThreads, 0, L.s>>>(
+            nhub, d.hub_cap, d.hubvert, d.hubhead, d.hubnext, d.lhead);
+        L.mark("k_hub_order");
+    }
     long long *nr = d.counters + 1;
     CK(cudaMemsetAsync(nr, 0, sizeof(long long), L.s));
-    k_succ_rulers<<<grid_for(L, ceil_div(n, kTile / 2)), kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.uf, d.lhead, d.nxt,
-                                                                             d.hubidx, d.hubnext, ruler_stride,
+    k_succ_rulers<<<grid_for(L, ceil_div(n, kTile / 2)), kThreads, 0, L.s>>>(n, te_u, te_v, d.uf, d.lhead, d.nxt,
+                                                                             hubidx, d.hubnext, ruler_stride,
                                                                              d.link, d.rhead, d.relem, nr);
     L.mark("k_succ_rulers");
     // upper bound on the number of rulers: a head per tour (a tour spans at least
@@ -852,7 +911,7 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
                                           d.fp, d.lastp, d.ord, d.porig, d.w1, d.w2, d.err);
     L.mark("k_comp_size");
     CK(cudaGetLastError());
-    k_place_records<<<gv, kThreads, 0, L.s>>>(n, d.te_u, d.te_v, d.te_a, d.parc, d.uf, d.csize, d.vbase, d.link, sd, d.rec, d.err);
+    k_place_records<<<gv, kThreads, 0, L.s>>>(n, te_u, te_v, te_a, hubs ? d.parc : nullptr, d.uf, d.csize, d.vbase, d.link, sd, d.rec, d.err);
     L.mark("k_place_records");
     CK(cudaGetLastError());
     const int64_t ntiles = ceil_div(2 * n, kTile);
@@ -866,8 +925,8 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
 }
 
 template cudaError_t launch_rooting<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
-                                             int, int, const Launch &);
+                                             int, int, int, bool, const Launch &);
 template cudaError_t launch_rooting<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,
-                                             int, int, const Launch &);
+                                             int, int, int, bool, const Launch &);
 
 }  // namespace fbcc

@@ -29,7 +29,8 @@ constexpr int kUniteCap = 1 << 26;
 constexpr int kKeyChunk = 1024;   // arcs of a scanned list per key-scan work item
 // Forest-arc lists of vertices of graph degree >= kHubDeg (hubs) are split into
 // kHubSub sub-lists (by edge id), so that their pushes do not serialise on one word.
-constexpr int kHubDeg = 256;
+constexpr int kHubDeg = 256;      // the default threshold (fbcc_config.hub_deg)
+constexpr int kHubMinDeg = 32;    // the smallest threshold a configuration may set
 constexpr int kHubSub = 32;
 constexpr int64_t kHubCap = 1 << 16;
 constexpr int kLookbackCap = 1 << 22;
@@ -67,6 +68,7 @@ struct Dev {
     int32_t *te_u, *te_v;     // tree edge recorded at the vertex it hooked (-1: none)
     int32_t *te_a;            // CSR position of the arc te_u -> te_v it was hooked from (-1: not known)
     int32_t *parc;            // by vertex: CSR position of the arc parent -> vertex (-1: not known)
+    int32_t *te2_u, *te2_v, *te2_a;  // the forest edges renumbered component by component (cc_order)
     uint32_t *bigb;           // sampling variants: one bit per vertex (First-CC) or position
                               // (Last-CC) in the sampled largest component, fixed for the full pass
     int2 *xl;                 // local-first First-CC: edges between vertex ranges {u, w}, u < w
@@ -116,7 +118,7 @@ struct Dev {
     // Last-CC and outputs
     int32_t *nh;              // number of labels a vertex heads
     unsigned long long *key;  // smallest arc id (src < dst) of label L at [L]
-    uint32_t *scanb;          // one bit per vertex: its list is scanned for keys (listed in klist)
+    uint8_t *scanv;           // per vertex: its list is scanned for keys (listed in klist)
     int2 *klist;              // {u0, chunk} of every kKeyChunk-arc chunk of the scanned lists
     int64_t klist_cap;
     int32_t *kmin;            // per label whose head is its BCC's smallest vertex: the smallest
@@ -201,13 +203,14 @@ __device__ __forceinline__ void uf_flatten_warp(int32_t *uf, int64_t v, bool in)
 }
 
 // Record the forest edge u-v at the root r it hooked, with the CSR position of
-// the arc u->v it came from (-1 when unknown or beyond 32 bits).
+// the arc u->v it came from (-1 when unknown or beyond 32 bits; not kept when te_a
+// is null).
 __device__ __forceinline__ void tree_edge(int32_t *te_u, int32_t *te_v, int32_t *te_a, int32_t r, int32_t u,
                                           int32_t v, int64_t a)
 {
     te_u[r] = u;
     te_v[r] = v;
-    te_a[r] = (a >= 0 && a < INT32_MAX) ? (int32_t)a : -1;
+    if (te_a) te_a[r] = (a >= 0 && a < INT32_MAX) ? (int32_t)a : -1;
 }
 
 // Union of the sets of u and v by CAS-hooking the larger root under the smaller.
@@ -534,12 +537,13 @@ inline int grid_for(const Launch &L, int64_t items_per_cta_units)
 // Phase launchers (each returns the first launch error or cudaSuccess).
 template <typename OffT>
 cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                            int cc_sample, int cc_local, bool vec, const Launch &L);
+                            int cc_sample, int cc_local, int hub_deg, bool vec, const Launch &L);
 // Allow the local-first First-CC kernel its shared memory for ranges of V vertices.
 cudaError_t prepare_cc_local(int V);
 template <typename OffT>
 cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           int ruler_stride, int chase_chains, int rank_variant, const Launch &L);
+                           int ruler_stride, int chase_chains, int rank_variant, int cc_order, bool hubs,
+                           const Launch &L);
 template <typename OffT>
 cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, bool keep_low_high, const Launch &L);
@@ -548,7 +552,7 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
                            int lcc_sample, bool vec, const Launch &L);
 template <typename OffT>
 cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           bool vec, int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap,
+                           bool vec, bool hubs, int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap,
                            uint8_t *is_bridge, const Batch &B, const Launch &L);
 template <typename OffT>
 cudaError_t launch_validate(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
@@ -558,6 +562,8 @@ cudaError_t launch_validate(const Dev &d, const OffT *off, const int32_t *adj, i
 // (out has len+1 entries; in may alias out when in_place).
 // out[i] = set bits in words[0..i), i in [0, len].
 cudaError_t launch_scan_popc(const Dev &d, const uint32_t *words, int32_t *out, int64_t len, const Launch &L);
+// In place: a[i] = sum of a[0..i) for i in [0, len] (a has len + 1 entries).
+cudaError_t launch_scan_i32(const Dev &d, int32_t *a, int64_t len, const Launch &L);
 
 // Biconnectivity queries over the last solve's labels and heads (fbcc_query.cu).
 cudaError_t launch_query_index(const Dev &d, int64_t n, cudaStream_t s);

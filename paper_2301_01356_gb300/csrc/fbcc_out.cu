@@ -58,15 +58,12 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
                                                       const int32_t *__restrict__ nh,
                                                       const int32_t *__restrict__ smin,
                                                       uint8_t *is_ap, unsigned long long *key, int32_t *kmin,
-                                                      uint32_t *scanb, int2 *klist, int64_t klist_cap,
-                                                      long long *klist_n, long long *nhead_n, fbcc_stats *stats,
+                                                      uint8_t *scanv, long long *nhead_n, fbcc_stats *stats,
                                                       int *err)
 {
     long long nap = 0, ncc = 0, nhead = 0;
     const int64_t T = (int64_t)gridDim.x * kThreads;
-    // the loop test is the warp's (its first lane's): the warp-wide reservation
-    // below needs every lane
-    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 - (threadIdx.x & 31) < n; v0 += T * kVPer) {
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
         int2 f[kVPer];
         int32_t h[kVPer], l[kVPer];
 #pragma unroll
@@ -107,13 +104,8 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
             ou[k] = off[u0[k]];
             oe[k] = off[u0[k] + 1];
         }
-        // u0 lists to scan: each new one takes ceil(deg / kKeyChunk) entries of klist,
-        // reserved with one atomic per warp and step
-        uint32_t fresh = 0;
-        int64_t nch[kVPer];
 #pragma unroll
         for (int k = 0; k < kVPer; ++k) {
-            nch[k] = 0;
             if (!((lbl >> k) & 1u)) continue;
             const int64_t v = v0 + k * T;
             const int64_t deg = (int64_t)oe[k] - (int64_t)ou[k];
@@ -127,37 +119,51 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
                 ++nhead;
             } else {                         // u0's list is scanned, once for all its labels
                 key[v] = ~0ull;
-                const uint32_t bit = 1u << (u0[k] & 31);
-                if (!(atomicOr(scanb + (u0[k] >> 5), bit) & bit)) {
-                    fresh |= 1u << k;
-                    nch[k] = (deg + kKeyChunk - 1) / kKeyChunk;
-                }
+                scanv[u0[k]] = 1;
             }
         }
-        if (!__any_sync(0xffffffffu, fresh != 0)) continue;
+    }
+    block_count((long long *)&stats->n_ap, nap);
+    block_count((long long *)&stats->n_cc, ncc);
+    block_count(nhead_n, nhead);
+}
+
+// The marked lists to scan, as work items of kKeyChunk arcs each: every marked
+// vertex takes ceil(deg / kKeyChunk) consecutive entries of klist, reserved with
+// one atomic per warp (kVPer vertices per thread, striped like the other passes).
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_key_list(int64_t n, const OffT *__restrict__ off,
+                                                       const uint8_t *__restrict__ scanv, int2 *klist,
+                                                       int64_t klist_cap, long long *klist_n, int *err)
+{
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    const int lane = threadIdx.x & 31;
+    // the loop test is the warp's (its first lane's): the reservation needs every lane
+    for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 - lane < n; v0 += T * kVPer) {
+        int64_t nch[kVPer];
         long long mine = 0;
 #pragma unroll
-        for (int k = 0; k < kVPer; ++k) mine += nch[k];
+        for (int k = 0; k < kVPer; ++k) {
+            const int64_t v = v0 + k * T;
+            nch[k] = 0;
+            if (v < n && scanv[v]) nch[k] = ((int64_t)off[v + 1] - (int64_t)off[v] + kKeyChunk - 1) / kKeyChunk;
+            mine += nch[k];
+        }
+        if (!__any_sync(0xffffffffu, mine != 0)) continue;
         long long inc = mine;
-        const int lane = threadIdx.x & 31;
         for (int o = 1; o < 32; o <<= 1) {
             const long long y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         const long long wtot = __shfl_sync(0xffffffffu, inc, 31);
         long long at = 0;
-        if (lane == 31 && wtot) at = (long long)atomicAdd((unsigned long long *)klist_n, (unsigned long long)wtot);
+        if (lane == 31) at = (long long)atomicAdd((unsigned long long *)klist_n, (unsigned long long)wtot);
         at = __shfl_sync(0xffffffffu, at, 31) + inc - mine;
 #pragma unroll
-        for (int k = 0; k < kVPer; ++k) {
-            if (!((fresh >> k) & 1u)) continue;
+        for (int k = 0; k < kVPer; ++k)
             for (int64_t c = 0; c < nch[k]; ++c, ++at)
-                if (in_range(at, klist_cap, err)) klist[at] = make_int2(u0[k], (int32_t)c);
-        }
+                if (in_range(at, klist_cap, err)) klist[at] = make_int2((int32_t)(v0 + k * T), (int32_t)c);
     }
-    block_count((long long *)&stats->n_ap, nap);
-    block_count((long long *)&stats->n_cc, ncc);
-    block_count(nhead_n, nhead);
 }
 
 // Labels whose head is their BCC's smallest vertex h: every class member x smaller
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const OffT *__
             // else a binary search of the head's list
             const int64_t v = v0 + k * T;
             const int32_t w = kmin[v], h = hd[k];
-            if (w == v) {
+            if (w == v && parc) {
                 const int32_t pa = parc[v];
                 if (pa >= 0) {
                     ks[k] = (unsigned long long)pa;
@@ -516,8 +522,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_edge_out(const OffT *__restrict
 
 template <typename OffT>
 cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                           bool vec, int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
-                           const Batch &B, const Launch &L)
+                           bool vec, bool hubs, int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap,
+                           uint8_t *is_bridge, const Batch &B, const Launch &L)
 {
     cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
@@ -525,23 +531,25 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
     const int64_t ntiles = ceil_div(nnz, kWTile);
     const int64_t nwords = ceil_div(nnz, 32);
     long long *klist_n = d.counters + 10, *nhead_n = d.counters + 13;
-    CK(cudaMemsetAsync(d.scanb, 0, ceil_div(n, 32) * sizeof(uint32_t), L.s));
+    CK(cudaMemsetAsync(d.scanv, 0, n, L.s));
     CK(cudaMemsetAsync(d.kmin, 0xff, n * sizeof(int32_t), L.s));
     CK(cudaMemsetAsync(klist_n, 0, sizeof(long long), L.s));
     CK(cudaMemsetAsync(nhead_n, 0, sizeof(long long), L.s));
-    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.lab, d.nh, d.smin, is_ap, d.key, d.kmin, d.scanb,
-                                              d.klist, d.klist_cap, klist_n, nhead_n, d.stats, d.err);
+    k_ap_keys<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.fp, d.lab, d.nh, d.smin, is_ap, d.key, d.kmin, d.scanv,
+                                              nhead_n, d.stats, d.err);
     L.mark("k_ap_keys");
     CK(cudaGetLastError());
     if (nnz > 0) {
+        k_key_list<OffT><<<gv, kThreads, 0, L.s>>>(n, off, d.scanv, d.klist, d.klist_cap, klist_n, d.err);
+        L.mark("k_key_list");
         k_key_adj<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, nhead_n, d.err);
         L.mark("k_key_adj");
         k_key_scan<OffT><<<L.grid, kThreads, 0, L.s>>>(off, adj, klist_n, d.klist, d.dirb, d.lab, d.fp, d.smin,
                                                        d.key);
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
-        k_key_bits<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, d.parc, d.key, d.key_bits, nnz,
-                                                    d.err);
+        k_key_bits<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, hubs ? d.parc : nullptr, d.key,
+                                                    d.key_bits, nnz, d.err);
         L.mark("k_key_bits");
         CK(cudaGetLastError());
         CK(launch_scan_popc(d, d.key_bits, d.key_pre, nwords, L));
@@ -570,10 +578,10 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
 }
 
 template cudaError_t launch_outputs<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, bool,
-                                             int32_t *, int32_t *, uint8_t *, uint8_t *, const Batch &,
+                                             bool, int32_t *, int32_t *, uint8_t *, uint8_t *, const Batch &,
                                              const Launch &);
 template cudaError_t launch_outputs<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, bool,
-                                             int32_t *, int32_t *, uint8_t *, uint8_t *, const Batch &,
+                                             bool, int32_t *, int32_t *, uint8_t *, uint8_t *, const Batch &,
                                              const Launch &);
 
 }  // namespace fbcc

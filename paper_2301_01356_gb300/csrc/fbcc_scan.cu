@@ -40,6 +40,26 @@ __global__ void __launch_bounds__(kThreads) k_scan_popc(const uint32_t *words, i
     }
 }
 
+// In place: a[i] = a[0] + ... + a[i-1] for i in [0, len], a[len] = the total (a holds
+// len + 1 entries; the last is ignored on input).
+__global__ void __launch_bounds__(kThreads) k_scan_i32(int32_t *a, int64_t len, long long *ticket, uint64_t *status,
+                                                       int *err)
+{
+    const int64_t ntiles = (len + 1 + kTile - 1) / kTile;
+    while (true) {
+        int64_t t = scan_ticket(ticket);
+        if (t >= ntiles) return;
+        long long v[kItems];
+        const int64_t i0 = t * kTile + (int64_t)threadIdx.x * kItems;
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) v[j] = i0 + j < len ? a[i0 + j] : 0;
+        scan_tile_exclusive(v, t, status, err);   // (synchronises the CTA before any write below)
+#pragma unroll
+        for (int j = 0; j < kItems; ++j)
+            if (i0 + j <= len) a[i0 + j] = (int32_t)v[j];
+    }
+}
+
 static cudaError_t reset_scan(const Dev &d, int64_t len, const Launch &L)
 {
     const int64_t ntiles = (len + 1 + kTile - 1) / kTile;
@@ -55,6 +75,16 @@ cudaError_t launch_scan_popc(const Dev &d, const uint32_t *words, int32_t *out, 
     const int64_t ntiles = (len + 1 + kTile - 1) / kTile;
     k_scan_popc<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(words, out, len, d.counters, d.scan_status, d.err);
     L.mark("k_scan_popc");
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_i32(const Dev &d, int32_t *a, int64_t len, const Launch &L)
+{
+    cudaError_t e = reset_scan(d, len, L);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (len + 1 + kTile - 1) / kTile;
+    k_scan_i32<<<grid_for(L, ntiles), kThreads, 0, L.s>>>(a, len, d.counters, d.scan_status, d.err);
+    L.mark("k_scan_i32");
     return cudaGetLastError();
 }
 

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_rmq_level(int64_t ntiles, int j0, 
 // of pointers to smaller preorder numbers whose root is its top vertex. Chains
 // inside the tile are flattened in shared memory (pointer doubling); a pointer that
 // leaves the tile marks its target in `ext` for the cross-tile resolution.
-__global__ void __launch_bounds__(kThreads) k_rmq_query(int64_t n, const int32_t *__restrict__ w1,
+__global__ void __launch_bounds__(kThreads, 4) k_rmq_query(int64_t n, const int32_t *__restrict__ w1,
                                                         const int32_t *__restrict__ w2, const int2 *__restrict__ pmm,
                                                         const int32_t *__restrict__ tmin,
                                                         const int32_t *__restrict__ tmax, int64_t st_stride,

@@ -107,7 +107,9 @@ def test_repeated_solves_and_configs(torch_cuda, oracle):
     e1, e2 = oracle.solve(g1.offsets, g1.adj), oracle.solve(g2.offsets, g2.adj)
     for cfg in ({}, {"ruler_stride": 8}, {"ruler_stride": 256}, {"cc_sample": 2}, {"use_graph": -1},
                 {"grid_ctas": 3}, {"chase_chains": 4}, {"chase_chains": 2}, {"cc_local": 1024},
-                {"cc_local": 16384}, {"lcc_sample": 2}, {"lcc_sample": 1, "cc_sample": 2}):
+                {"cc_local": 16384}, {"lcc_sample": 2}, {"lcc_sample": 1, "cc_sample": 2}, {"rank_variant": 1},
+                {"grid_ctas": -4}, {"cc_order": 1}, {"cc_order": 1, "cc_local": 1024, "rank_variant": 1},
+                {"hub_deg": -1}, {"hub_deg": 32}, {"hub_deg": 32, "cc_sample": 2, "cc_order": 1}):
         s = fbcc.Solver(20000, 50000, **cfg)
         for _ in range(2):
             for g, e in ((g1, e1), (g2, e2), (g1, e1)):
@@ -262,7 +264,7 @@ def test_grid_4096_full_size(torch_cuda, oracle):
     g = gg.workload_grid_4096()
     exp = oracle.solve(g.offsets, g.adj)
     off, adj = to_dev(torch_cuda, g, off64=False)
-    for cfg in (_tuned("grid4096"), {}):
+    for cfg in (_tuned("grid4096"), {}, {**_tuned("grid4096"), "cc_order": 1}):
         s = fbcc.Solver(g.n, g.nnz, **cfg)
         assert_same(s.solve(off, adj), exp, f"grid 4096 {cfg}")
         s.close()
