@@ -176,8 +176,8 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
     table = {
         # First-CC
         "k_cc_init": 4 * n, "k_uf_compress": 4 * n,
-        "k_cc_hook": arc_cc, "k_cc_local": arc_cc, "k_cc_hook_skip": arc_cc, "k_cc_hook_cross": 0,
-        "k_cc_sample": 0, "k_mark_big": 0, "k_cc_pick_big": 0,
+        "k_cc_hook": arc_cc, "k_cc_local": arc_cc, "k_cc_hook_rest": arc_cc, "k_cc_hook_cross": 0,
+        "k_cc_sample": 0, "k_mark_big": 0, "k_cc_pick_big": 0, "k_cc_hook_chunks": 0,
         # Rooting
         "k_cc_count": 0, "k_cc_place": 0, "k_permute_te": 0, "k_scan_i32": 0, "k_link": 8 * A, "k_hub_order": 0, "k_succ_rulers": 16 * A, "k_chase": 8 * A, "k_lvl_rulers": 0, "k_lvl_chase": 0,
         "k_top": 0, "k_lvl_expand": 0, "k_jump": 0, "k_comp_size": 0, "k_place_records": 8 * A, "k_preorder": 8 * A + 16 * n,
@@ -186,8 +186,9 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_rmq_query": 24 * n,
         # Last-CC
         "k_ext_compact": 0, "k_ext_halve": 0, "k_ext_finish": 0, "k_plain_label": 0,
-        "k_last_cc_cross": B * n + 4 * nnz + 20 * n, "k_last_cc_cross_skip": B * n + 4 * nnz + 20 * n,
-        "k_lcc_sample": 0, "k_pos_compress": 0, "k_pos_pick_big": 0, "k_final_label": 8 * n,
+        "k_last_cc_cross": B * n + 4 * nnz + 20 * n, "k_last_cc_cross_rest": B * n + 4 * nnz + 20 * n,
+        "k_lcc_sample": 0, "k_last_cc_cross_chunks": 0, "k_pos_compress": 0, "k_pos_pick_big": 0,
+        "k_final_label": 8 * n,
         # Outputs
         "k_ap_keys": 12 * n, "k_key_list": 0, "k_key_adj": 0, "k_key_scan": 0, "k_key_bits": 0, "k_scan_popc": 0, "k_rank": 0, "k_fo": 0,
         "k_edge_out": B * n + 9 * nnz, "k_bcc_base": 0, "k_batch_stats": 0, "k_finish": 0,

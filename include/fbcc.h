@@ -68,7 +68,10 @@ typedef struct {
 /* Tuning knobs; zero in a field means "library default". */
 typedef struct {
     int32_t ruler_stride;  /* list ranking: one ruler per this many tree arcs (power of 2, >= 8) */
-    int32_t cc_sample;     /* First-CC: neighbours per vertex hooked before the full pass (0 = off) */
+    int32_t cc_sample;     /* First-CC: first neighbours per vertex hooked before the full pass (0 = off).
+                              The full pass then goes by vertex and skips the largest sampled
+                              component, or, when that component holds under half of a
+                              degree-weighted vote, runs over all arcs as without sampling */
     int32_t grid_ctas;     /* CTAs of the persistent grid-stride kernels; -k = k per SM (default 8 per SM) */
     int32_t use_graph;     /* 1 = replay a captured CUDA graph for repeated identical calls (default), -1 = never */
     int32_t profile;       /* 1 = record a CUDA event after every kernel (no graph); see fbcc_profile_get */
@@ -77,7 +80,8 @@ typedef struct {
                               shared memory first (power of 2, 1024..16384; 0 = off); a range
                               whose lists hold 2^31 arcs or more makes the solve report
                               FBCC_E_INVALID in device_status */
-    int32_t lcc_sample;    /* Last-CC: cross edges per vertex united before the full pass (0 = off) */
+    int32_t lcc_sample;    /* Last-CC: first arcs per vertex tested and united before the full pass
+                              (0 = off, 1..4); the full pass then chooses as for cc_sample */
     int32_t rank_variant;  /* list ranking above the rulers: 0 = sample the ruler lists again and rank
                               the top level in one CTA (default); 1 = pointer jumping (Wyllie) over
                               the ruler lists, a fixed number of grid-wide rounds */
@@ -298,6 +302,11 @@ fbcc_status fbcc_profile_get(const fbcc_workspace *ws, int32_t i, const char **n
  *   "vbits" (uint8)            bit 0: the tree edge to the parent is a bridge;
  *                              bit 1: it is a fence edge
  *   "err" (count 1)            the device error bits of the last solve
+ *   "sampled" (count up to 4)  the sampling votes of the last solves that sampled:
+ *                              First-CC's largest root and whether it won at least
+ *                              half of the votes (1) or the tiled pass ran (0), then
+ *                              the same two for Last-CC (a plain-component root by
+ *                              preorder number, -1 when no arc voted)
  *   "dirb" (uint8, count up to ceil(nnz_max / 8))  one bit per arc, least
  *                              significant first: the target's preorder number
  *                              exceeds the source's

@@ -2,8 +2,9 @@
 
 The knobs, each a runtime choice of the library (fbcc_config):
   - First-CC variant: plain hooking, local-first in shared memory over ranges of
-    8192 or 16384 vertices, or sampled (two neighbours per vertex first);
-  - Last-CC sampling (cross edges united per vertex before the full pass);
+    8192 or 16384 vertices, or sampled (one or two neighbours per vertex first);
+  - Last-CC sampling (the first arcs of every vertex tested and their cross
+    edges united before the full pass);
   - ruler stride of the list ranking, walks a thread advances together
     (chase_chains), and the ranking above the rulers (sampled levels with a
     single-CTA top, or Wyllie pointer jumping);
@@ -38,9 +39,9 @@ DEFAULT = dict(ruler_stride=16, cc_local=0, cc_sample=0, lcc_sample=0, chase_cha
                cc_order=0, hub_deg=0)
 KNOBS = [
     ("cc", [dict(cc_local=0, cc_sample=0), dict(cc_local=8192, cc_sample=0), dict(cc_local=16384, cc_sample=0),
-            dict(cc_local=0, cc_sample=2)]),
+            dict(cc_local=0, cc_sample=1), dict(cc_local=0, cc_sample=2)]),
     ("ruler_stride", [dict(ruler_stride=s) for s in (8, 16, 32, 64)]),
-    ("lcc_sample", [dict(lcc_sample=q) for q in (0, 2)]),
+    ("lcc_sample", [dict(lcc_sample=q) for q in (0, 2, 4)]),
     ("chase_chains", [dict(chase_chains=c) for c in (1, 2)]),
     ("rank_variant", [dict(rank_variant=r) for r in (0, 1)]),
     ("cc_order", [dict(cc_order=o) for o in (0, 1)]),

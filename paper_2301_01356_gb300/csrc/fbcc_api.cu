@@ -328,7 +328,7 @@ fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
             c.cc_local = cfg->cc_local;
         }
-        if (cfg->lcc_sample < 0 || cfg->lcc_sample > 64) return FBCC_E_INVALID;
+        if (cfg->lcc_sample < 0 || cfg->lcc_sample > 4) return FBCC_E_INVALID;
         c.lcc_sample = cfg->lcc_sample;
         if (cfg->rank_variant < 0 || cfg->rank_variant > 1) return FBCC_E_INVALID;
         c.rank_variant = cfg->rank_variant;
@@ -758,6 +758,7 @@ extern "C" fbcc_status fbcc_debug_read(const fbcc_workspace *ws, const char *nam
     else if (!strcmp(name, "ord")) src = d.ord;
     else if (!strcmp(name, "porig")) src = d.porig;
     else if (!strcmp(name, "err")) { src = d.err; if (count > 1) return FBCC_E_INVALID; }
+    else if (!strcmp(name, "sampled")) { src = d.counters + 8; if (count > 4) return FBCC_E_INVALID; }
     else if (!strcmp(name, "vbits")) { src = d.vbits; elem = 1; }
     else return FBCC_E_INVALID;
     API_CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");

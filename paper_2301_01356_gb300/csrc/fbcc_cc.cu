@@ -51,8 +51,9 @@ template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_hook(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                       int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
                                                       int32_t *uf, int32_t *te_u, int32_t *te_v, int32_t *te_a, int *err,
-                                                      bool vec)
+                                                      bool vec, const int32_t *__restrict__ sampled)
 {
+    if (sampled && sampled[1]) return;   // after a strong sample the by-vertex pass runs instead
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
     const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -91,58 +92,116 @@ __global__ void __launch_bounds__(kThreads) k_cc_sample(const OffT *__restrict__
     }
 }
 
-// Full pass after sampling: arcs whose source sat in the sampled largest
-// component are skipped (the same edge is still seen from its other endpoint,
-// unless both endpoints are in that component, where it cannot join anything
-// new). Membership is a bitmap taken before the pass: the component's root can
-// change during the pass (a component with a smaller id joins it), and a test
-// against the live root would then stop skipping.
+// Membership of the sampled largest component, as a bitmap taken before the full
+// pass: the component's root can change during the pass (a component with a
+// smaller id joins it), and a test against the live root would then stop skipping.
 __global__ void __launch_bounds__(kThreads) k_mark_big(const int32_t *__restrict__ uf, int64_t n,
                                                        const int32_t *__restrict__ big, uint32_t *bigb)
 {
-    const int32_t root = *big;
+    if (!big[1]) return;   // a weak sample: nothing is skipped (see pick_big)
+    const int32_t root = big[0];
     const int64_t n_pad = (n + 31) & ~31ll;
     for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
         const unsigned m = __ballot_sync(0xffffffffu, v < n && uf[v] == root);
         if ((threadIdx.x & 31) == 0) bigb[v >> 5] = m;
     }
 }
-template <typename OffT>
-__global__ void __launch_bounds__(kThreads) k_cc_hook_skip(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
-                                                           int64_t nnz, const int32_t *__restrict__ tile_v,
-                                                           int64_t ntiles, int32_t *uf, int32_t *te_u, int32_t *te_v,
-                                                           int32_t *te_a, const uint32_t *__restrict__ bigb, int *err,
-                                                           bool vec)
+
+// The full pass after sampling, by vertex: only vertices outside the sampled
+// component (membership frozen in a bitmap before the pass, see k_mark_big) hook
+// their arcs, in both directions (an edge from a skipped vertex is seen from its
+// other end, unless both ends are in the sampled component, where it cannot join
+// anything new). A lane takes a list of up to kRestShort arcs alone; longer lists
+// are then hooked by the whole warp, one list at a time, and a list above
+// kRestLong arcs (a hub left outside the sample) is cut into chunks of kRestChunk
+// arcs that a second launch spreads over the whole grid, so that no warp walks a
+// hub's list alone. Where sampling gathered nearly every vertex, this touches the
+// offsets and the bitmap and little else.
+constexpr int kRestShort = 32;
+constexpr int kRestLong = 2048;
+constexpr int kRestChunk = 1024;
+
+// Queues the chunks of vertex v's list of len arcs (whole warp, v and len the same
+// in every lane): {v, chunk index} entries. Without room for all of them the warp
+// keeps the list (false); entries it had reserved below the capacity are marked
+// empty, and the drain reads at most `cap` entries.
+__device__ __forceinline__ bool rest_queue(int2 *lq, int64_t cap, long long *nq, int32_t v, int64_t len, int lane)
 {
-    __shared__ OffT win[kCtaWin];
-    ArcTile<OffT> at;
-    const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
-    for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
-        arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
-        if (!at.cnt) continue;
-        bool any = false;
-        uint32_t sk = 0;   // arcs whose source was in the sampled component
-        int32_t last_src = -1;
-        bool last_skip = true;
-#pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            if (j < at.cnt) {
-                if (at.src[j] != last_src) {
-                    last_src = at.src[j];
-                    last_skip = test_bit(bigb, last_src);
-                }
-                if (last_skip) sk |= 1u << j;
-                any |= !last_skip;
+    const int64_t nch = (len + kRestChunk - 1) / kRestChunk;
+    long long k = 0;
+    if (lane == 0) k = (long long)atomicAdd((unsigned long long *)nq, (unsigned long long)nch);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k + nch > cap) {
+        for (int64_t c = k + lane; c < cap; c += 32) lq[c] = make_int2(-1, 0);
+        return false;
+    }
+    for (int64_t c = lane; c < nch; c += 32) lq[k + c] = make_int2(v, (int32_t)c);
+    return true;
+}
+
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_cc_hook_rest(const OffT *__restrict__ off,
+                                                           const int32_t *__restrict__ adj, int64_t n, int32_t *uf,
+                                                           int32_t *te_u, int32_t *te_v, int32_t *te_a,
+                                                           const uint32_t *__restrict__ bigb, int2 *lq, int64_t lq_cap,
+                                                           long long *lq_n, const int32_t *__restrict__ sampled,
+                                                           int *err)
+{
+    if (!sampled[1]) return;   // a weak sample: the tiled full pass runs instead
+    const int lane = threadIdx.x & 31;
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
+        int64_t b = 0, e = 0;
+        if (v < n && !test_bit(bigb, v)) {
+            b = off[v];
+            e = off[v + 1];
+        }
+        const bool lng = e - b > kRestShort;
+        if (!lng) {
+            for (int64_t a = b; a < e; ++a) {
+                const int32_t w = adj[a];
+                const int32_t r = uf_unite(uf, (int32_t)v, w, err);
+                if (r >= 0) tree_edge(te_u, te_v, te_a, r, (int32_t)v, w, a);
             }
         }
-        if (!any) continue;
-        int32_t d[kItems];
-        arc_tile_targets(adj, at.a0, at.cnt, vec, d);
-#pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            if (j >= at.cnt || ((sk >> j) & 1u)) continue;
-            int32_t r = uf_unite(uf, at.src[j], d[j], err);
-            if (r >= 0) tree_edge(te_u, te_v, te_a, r, at.src[j], d[j], at.a0 + j);
+        unsigned todo = __ballot_sync(0xffffffffu, lng);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int32_t u = (int32_t)__shfl_sync(0xffffffffu, v, src);
+            const int64_t bb = __shfl_sync(0xffffffffu, b, src), ee = __shfl_sync(0xffffffffu, e, src);
+            if (ee - bb > kRestLong && rest_queue(lq, lq_cap, lq_n, u, ee - bb, lane)) continue;
+            for (int64_t a = bb + lane; a < ee; a += 32) {
+                const int32_t w = adj[a];
+                const int32_t r = uf_unite(uf, u, w, err);
+                if (r >= 0) tree_edge(te_u, te_v, te_a, r, u, w, a);
+            }
+        }
+    }
+}
+
+// The queued chunks of long lists, a warp per chunk.
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_cc_hook_chunks(const OffT *__restrict__ off,
+                                                             const int32_t *__restrict__ adj,
+                                                             const int2 *__restrict__ lq, int64_t lq_cap,
+                                                             const long long *__restrict__ lq_n, int32_t *uf,
+                                                             int32_t *te_u, int32_t *te_v, int32_t *te_a,
+                                                             const int32_t *__restrict__ sampled, int *err)
+{
+    if (!sampled[1]) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nq = *lq_n < lq_cap ? *lq_n : lq_cap;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t i = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; i < nq; i += warps) {
+        const int2 q = lq[i];
+        if (q.x < 0) continue;
+        const int64_t b = off[q.x] + (int64_t)q.y * kRestChunk, end = off[q.x + 1];
+        const int64_t e = b + kRestChunk < end ? b + kRestChunk : end;
+        for (int64_t a = b + lane; a < e; a += 32) {
+            const int32_t w = adj[a];
+            const int32_t r = uf_unite(uf, q.x, w, err);
+            if (r >= 0) tree_edge(te_u, te_v, te_a, r, q.x, w, a);
         }
     }
 }
@@ -156,26 +215,42 @@ __global__ void __launch_bounds__(kThreads) k_uf_compress(int32_t *uf, int64_t n
         uf_flatten_warp(uf, v, v < n);
 }
 
-// The root of the component holding most sampled vertices: a vote over a fixed
-// subset of vertices (a single CTA).
-__global__ void __launch_bounds__(kThreads) k_cc_pick_big(int32_t *uf, int64_t n, int32_t *big)
+// The component that a sample left largest, by a vote of the sources of a fixed
+// sample of arcs (tile_v: the source of every kWTile-th arc), so that a vertex
+// weighs as much as its list, the work that skipping it saves. A single CTA
+// writes big[0] = the winning root (-1: none) and big[1] = whether it holds at
+// least half of the votes: below that the by-vertex pass would go through most
+// arcs anyway, slower than the tiled full pass, which then runs instead. `cand`
+// maps a vertex to its vote (-1: none).
+template <typename Cand>
+__device__ __forceinline__ void pick_big(const int32_t *__restrict__ tile_v, int64_t ntiles, Cand cand_of,
+                                         int32_t *big)
 {
     __shared__ int32_t cand[kThreads];
     __shared__ int32_t cnt[kThreads];
-    int64_t step = n / kThreads > 0 ? n / kThreads : 1;
-    int64_t v = (int64_t)threadIdx.x * step;
-    cand[threadIdx.x] = v < n ? uf_find(uf, (int32_t)v) : -1;
+    const int64_t t = (int64_t)threadIdx.x * ntiles / kThreads;
+    cand[threadIdx.x] = cand_of(tile_v[t]);
     __syncthreads();
-    int c = 0;
-    for (int i = 0; i < kThreads; ++i) c += cand[i] == cand[threadIdx.x];
+    int c = 0, votes = 0;
+    for (int i = 0; i < kThreads; ++i) {
+        c += cand[i] == cand[threadIdx.x];
+        votes += cand[i] >= 0;
+    }
     cnt[threadIdx.x] = cand[threadIdx.x] >= 0 ? c : 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         int best = 0;
         for (int i = 1; i < kThreads; ++i)
             if (cnt[i] > cnt[best]) best = i;
-        *big = cand[best] >= 0 ? cand[best] : 0;
+        big[0] = cand[best];
+        big[1] = cand[best] >= 0 && 2 * cnt[best] >= votes;
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cc_pick_big(int32_t *uf, const int32_t *__restrict__ tile_v,
+                                                          int64_t ntiles, int32_t *big)
+{
+    pick_big(tile_v, ntiles, [&](int32_t v) { return uf_find(uf, v); }, big);
 }
 
 // Local-first variant: each CTA owns a range of V consecutive vertex ids and
@@ -404,16 +479,27 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             L.mark("k_cc_sample");
             k_uf_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
             L.mark("k_uf_compress");
-            k_cc_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, n, big);
+            k_cc_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, d.tile_v, ntiles, big);
             L.mark("k_cc_pick_big");
             k_mark_big<<<gv, kThreads, 0, L.s>>>(d.uf, n, big, d.bigb);
             L.mark("k_mark_big");
-            k_cc_hook_skip<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
-                                                          te_a, d.bigb, d.err, vec);
-            L.mark("k_cc_hook_skip");
+            // the long lists' chunks go to the local-first list's space (unused here)
+            long long *nlq = d.counters + 15;
+            const cudaError_t e = cudaMemsetAsync(nlq, 0, sizeof(long long), L.s);
+            if (e != cudaSuccess) return e;
+            k_cc_hook_rest<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, d.uf, d.te_u, d.te_v, te_a, d.bigb, d.xl,
+                                                           d.xl_cap, nlq, big, d.err);
+            L.mark("k_cc_hook_rest");
+            k_cc_hook_chunks<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, d.xl, d.xl_cap, nlq, d.uf, d.te_u, d.te_v,
+                                                             te_a, big, d.err);
+            L.mark("k_cc_hook_chunks");
+            // after a weak sample (see pick_big) the tiled pass; otherwise it returns at once
+            k_cc_hook<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
+                                                     te_a, d.err, vec, big);
+            L.mark("k_cc_hook");
         } else {
             k_cc_hook<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
-                                                     te_a, d.err, vec);
+                                                     te_a, d.err, vec, nullptr);
             L.mark("k_cc_hook");
         }
     }
@@ -549,8 +635,9 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
                                                             int64_t ntiles, const int2 *__restrict__ cr,
                                                             const int32_t *__restrict__ lastp,
                                                             const uint8_t *__restrict__ dirb, int32_t *uf, int *err,
-                                                            bool vec)
+                                                            bool vec, const int32_t *__restrict__ sampled)
 {
+    if (sampled && sampled[1]) return;   // after a strong sample the by-vertex pass runs instead
     __shared__ OffT win[kCtaWin];
     ArcTile<OffT> at;
     const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -584,36 +671,48 @@ __global__ void __launch_bounds__(kThreads) k_last_cc_cross(const OffT *__restri
 }
 
 // Sampling variant of the cross-edge pass (the Afforest idea applied to G'):
-// first every vertex unites along its first `k` cross edges, then the component
-// holding most sampled positions is found, and the full pass skips every source
-// in it (membership fixed before the pass, see k_mark_big). A skipped arc still reaches its other endpoint's side, so here
-// cross edges are tested from both ends: towards a later vertex w as above, and
-// towards an earlier one iff first[u] > last[w] (u after T_w; a parent arc and a
-// back edge to an ancestor fail it).
+// first the first K arcs of every vertex are tested and their cross edges united,
+// then the component holding most sampled positions is found, and a pass by
+// vertex goes through the arcs of every vertex outside it (membership fixed
+// before that pass, see k_mark_big). A skipped vertex's edges are still seen from
+// their other ends, so here cross edges are tested from both ends: towards a later
+// vertex w as above, and towards an earlier one iff first[u] > last[w] (u after
+// T_w; a parent arc and a back edge to an ancestor fail it).
 __device__ __forceinline__ bool cross_from(int32_t fu, int32_t lastu, int32_t fw, bool later,
                                            const int32_t *__restrict__ lastp)
 {
     return later ? fw > lastu : fu > __ldg(lastp + fw);
 }
 
-template <typename OffT>
+// One vertex per thread, its K arcs' gathers issued together before the unions
+// (a tree root has no cross edges and is passed over).
+template <typename OffT, int K>
 __global__ void __launch_bounds__(kThreads) k_lcc_sample(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
-                                                         int64_t n, int k, const int2 *__restrict__ fp,
+                                                         int64_t n, const int2 *__restrict__ fp,
                                                          const int2 *__restrict__ cr, const int32_t *__restrict__ lastp,
                                                          const uint8_t *__restrict__ dirb, int32_t *uf, int *err)
 {
     for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
-        if (fp[v].y < 0) continue;   // a root has no cross edges
+        if (fp[v].y < 0) continue;
+        const int64_t b = off[v];
+        const int64_t deg = off[v + 1] - b;
+        const int cnt = deg < K ? (int)deg : K;
         const int2 cs = cr[v];
+        int32_t w[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j] = j < cnt ? adj[b + j] : 0;
         const int32_t lastu = __ldg(lastp + cs.x);
-        int found = 0;
-        const int64_t b = off[v], e = off[v + 1];
-        for (int64_t a = b; a < e && a < b + 4 * k && found < k; ++a) {
-            const int32_t w = adj[a];
-            const int2 cd = __ldg(cr + w);
-            if (cd.y == cs.y || !cross_from(cs.x, lastu, cd.x, dir_bit(dirb, a), lastp)) continue;
-            uf_unite(uf, cs.y, cd.y, err);
-            ++found;
+        int2 cd[K];
+        bool later[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            cd[j] = j < cnt ? __ldg(cr + w[j]) : cs;
+            later[j] = j < cnt && dir_bit(dirb, b + j);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (cd[j].y == cs.y || !cross_from(cs.x, lastu, cd[j].x, later[j], lastp)) continue;
+            uf_unite(uf, cs.y, cd[j].y, err);
         }
     }
 }
@@ -626,75 +725,105 @@ __global__ void __launch_bounds__(kThreads) k_pos_compress(int32_t *uf, int64_t 
         uf_flatten_warp(uf, p, p < n);
 }
 
+// The full cross-edge pass after sampling, by vertex: a vertex whose plain root
+// is outside the sampled component tests all its arcs, in both directions; a lane
+// takes a list of up to kRestShort arcs alone, longer lists are then tested by the
+// whole warp, one list at a time, and lists above kRestLong arcs go to the chunk
+// queue (see rest_queue). Where sampling gathered nearly every vertex, this reads
+// fp, cr and the bitmap and little else.
+__device__ __forceinline__ void cross_unite_warp(const int32_t *__restrict__ adj, const int2 *__restrict__ cr,
+                                                 const int32_t *__restrict__ lastp, const uint8_t *__restrict__ dirb,
+                                                 int32_t *uf, int *err, int32_t fu, int32_t ru, int32_t lu,
+                                                 int64_t b, int64_t e, int lane)
+{
+    for (int64_t a = b + lane; a < e; a += 32) {
+        const int2 cd = __ldg(cr + adj[a]);
+        if (cd.y == ru || !cross_from(fu, lu, cd.x, dir_bit(dirb, a), lastp)) continue;
+        uf_unite(uf, ru, cd.y, err);
+    }
+}
+
 template <typename OffT>
-__global__ void __launch_bounds__(kThreads) k_last_cc_cross_skip(const OffT *__restrict__ off,
-                                                                 const int32_t *__restrict__ adj, int64_t nnz,
-                                                                 const int32_t *__restrict__ tile_v, int64_t ntiles,
+__global__ void __launch_bounds__(kThreads) k_last_cc_cross_rest(const OffT *__restrict__ off,
+                                                                 const int32_t *__restrict__ adj, int64_t n,
+                                                                 const int2 *__restrict__ fp,
                                                                  const int2 *__restrict__ cr,
                                                                  const int32_t *__restrict__ lastp,
                                                                  const uint8_t *__restrict__ dirb, int32_t *uf,
-                                                                 const uint32_t *__restrict__ bigb, int *err, bool vec)
+                                                                 const uint32_t *__restrict__ bigb, int2 *lq,
+                                                                 int64_t lq_cap, long long *lq_n,
+                                                                 const int32_t *__restrict__ sampled, int *err)
 {
-    __shared__ OffT win[kCtaWin];
-    ArcTile<OffT> at;
-    const int64_t nct = (ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
-    for (int64_t t = blockIdx.x; t < nct; t += gridDim.x) {
-        arc_cta_tile_sources(off, nnz, tile_v, ntiles, t, win, at);
-        if (!at.cnt) continue;
-        int2 cs[kItems];
-        int32_t lu[kItems];
-        bool any = false;
-        int32_t cur = -1;
-        bool skip = true;
-        int2 c = make_int2(0, 0);
+    if (!sampled[1]) return;   // a weak sample: the tiled full pass runs instead
+    const int lane = threadIdx.x & 31;
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
+        int64_t b = 0, e = 0;
+        int2 cs = make_int2(0, 0);
         int32_t lastu = 0;
-#pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            if (j < at.cnt && at.src[j] != cur) {
-                cur = at.src[j];
-                c = __ldg(cr + cur);
-                skip = test_bit(bigb, c.y);
-                if (!skip) lastu = __ldg(lastp + c.x);
+        if (v < n && fp[v].y >= 0) {
+            cs = cr[v];
+            if (!test_bit(bigb, cs.y)) {
+                b = off[v];
+                e = off[v + 1];
+                lastu = __ldg(lastp + cs.x);
             }
-            cs[j] = c;
-            lu[j] = lastu;
-            if (j < at.cnt && !skip) any = true;
-            else lu[j] = -1;   // marks a skipped arc
         }
-        if (!any) continue;
-        const uint32_t bits = __ldg(dirb + (at.a0 >> 3));
-        int32_t d[kItems];
-        arc_tile_targets(adj, at.a0, at.cnt, vec, d);
-#pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            if (j >= at.cnt || lu[j] < 0) continue;
-            const int2 cd = __ldg(cr + d[j]);
-            if (cd.y == cs[j].y || !cross_from(cs[j].x, lu[j], cd.x, (bits >> j) & 1u, lastp)) continue;
-            uf_unite(uf, cs[j].y, cd.y, err);
+        const bool lng = e - b > kRestShort;
+        if (!lng) {
+            for (int64_t a = b; a < e; ++a) {
+                const int2 cd = __ldg(cr + adj[a]);
+                if (cd.y == cs.y || !cross_from(cs.x, lastu, cd.x, dir_bit(dirb, a), lastp)) continue;
+                uf_unite(uf, cs.y, cd.y, err);
+            }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, lng);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t bb = __shfl_sync(0xffffffffu, b, src), ee = __shfl_sync(0xffffffffu, e, src);
+            if (ee - bb > kRestLong &&
+                rest_queue(lq, lq_cap, lq_n, (int32_t)__shfl_sync(0xffffffffu, v, src), ee - bb, lane))
+                continue;
+            cross_unite_warp(adj, cr, lastp, dirb, uf, err, __shfl_sync(0xffffffffu, cs.x, src),
+                             __shfl_sync(0xffffffffu, cs.y, src), __shfl_sync(0xffffffffu, lastu, src), bb, ee, lane);
         }
     }
 }
 
-// The root holding most of a fixed sample of positions (a single CTA).
-__global__ void __launch_bounds__(kThreads) k_pos_pick_big(int32_t *uf, const int32_t *__restrict__ porig, int64_t n,
-                                                           int32_t *big)
+// The queued chunks of long lists, a warp per chunk.
+template <typename OffT>
+__global__ void __launch_bounds__(kThreads) k_last_cc_cross_chunks(const OffT *__restrict__ off,
+                                                                   const int32_t *__restrict__ adj,
+                                                                   const int2 *__restrict__ cr,
+                                                                   const int32_t *__restrict__ lastp,
+                                                                   const uint8_t *__restrict__ dirb,
+                                                                   const int2 *__restrict__ lq, int64_t lq_cap,
+                                                                   const long long *__restrict__ lq_n, int32_t *uf,
+                                                                   const int32_t *__restrict__ sampled, int *err)
 {
-    __shared__ int32_t cand[kThreads];
-    __shared__ int32_t cnt[kThreads];
-    const int64_t step = n / kThreads > 0 ? n / kThreads : 1;
-    const int64_t p = (int64_t)threadIdx.x * step;
-    cand[threadIdx.x] = (p < n && porig[p] >= 0) ? uf_find(uf, (int32_t)p) : -1;
-    __syncthreads();
-    int c = 0;
-    for (int i = 0; i < kThreads; ++i) c += cand[i] == cand[threadIdx.x];
-    cnt[threadIdx.x] = cand[threadIdx.x] >= 0 ? c : 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int best = 0;
-        for (int i = 1; i < kThreads; ++i)
-            if (cnt[i] > cnt[best]) best = i;
-        *big = cand[best];   // -1 when nothing was sampled: then nothing is skipped
+    if (!sampled[1]) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nq = *lq_n < lq_cap ? *lq_n : lq_cap;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t i = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; i < nq; i += warps) {
+        const int2 q = lq[i];
+        if (q.x < 0) continue;
+        const int2 cs = cr[q.x];
+        const int64_t b = off[q.x] + (int64_t)q.y * kRestChunk, end = off[q.x + 1];
+        cross_unite_warp(adj, cr, lastp, dirb, uf, err, cs.x, cs.y, __ldg(lastp + cs.x), b,
+                         b + kRestChunk < end ? b + kRestChunk : end, lane);
     }
+}
+
+// The same vote in Last-CC: an arc's source votes for the union-find root of its
+// plain component (a tree root, alone in its plain component with no cross edge,
+// does not vote).
+__global__ void __launch_bounds__(kThreads) k_pos_pick_big(int32_t *uf, const int32_t *__restrict__ tile_v,
+                                                           int64_t ntiles, const int2 *__restrict__ fp,
+                                                           const int2 *__restrict__ cr, int32_t *big)
+{
+    pick_big(tile_v, ntiles, [&](int32_t v) { return fp[v].y >= 0 ? uf_find(uf, cr[v].y) : -1; }, big);
 }
 
 // Final labels. Every position's skeleton component root r (its top vertex has
@@ -762,21 +891,35 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
     L.mark("k_plain_label");
     if (nnz > 0 && lcc_sample > 0) {
         int32_t *big = reinterpret_cast<int32_t *>(d.counters + 9);
-        k_lcc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, lcc_sample, d.fp, d.cr, d.lastp, d.dirb, d.uf,
-                                                     d.err);
+        switch (lcc_sample) {
+        case 1: k_lcc_sample<OffT, 1><<<gv, kThreads, 0, L.s>>>(off, adj, n, d.fp, d.cr, d.lastp, d.dirb, d.uf, d.err); break;
+        case 2: k_lcc_sample<OffT, 2><<<gv, kThreads, 0, L.s>>>(off, adj, n, d.fp, d.cr, d.lastp, d.dirb, d.uf, d.err); break;
+        case 3: k_lcc_sample<OffT, 3><<<gv, kThreads, 0, L.s>>>(off, adj, n, d.fp, d.cr, d.lastp, d.dirb, d.uf, d.err); break;
+        default: k_lcc_sample<OffT, 4><<<gv, kThreads, 0, L.s>>>(off, adj, n, d.fp, d.cr, d.lastp, d.dirb, d.uf, d.err); break;
+        }
         L.mark("k_lcc_sample");
         k_pos_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
         L.mark("k_pos_compress");
-        k_pos_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, d.porig, n, big);
+        k_pos_pick_big<<<1, kThreads, 0, L.s>>>(d.uf, d.tile_v, ntiles, d.fp, d.cr, big);
         L.mark("k_pos_pick_big");
         k_mark_big<<<gv, kThreads, 0, L.s>>>(d.uf, n, big, d.bigb);
         L.mark("k_mark_big");
-        k_last_cc_cross_skip<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
-            off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, d.bigb, d.err, vec);
-        L.mark("k_last_cc_cross_skip");
+        // the long lists' chunks go to the key list's space (used only by the outputs)
+        long long *nlq = d.counters + 3;
+        CK(cudaMemsetAsync(nlq, 0, sizeof(long long), L.s));
+        k_last_cc_cross_rest<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, d.fp, d.cr, d.lastp, d.dirb, d.uf, d.bigb,
+                                                             d.klist, d.klist_cap, nlq, big, d.err);
+        L.mark("k_last_cc_cross_rest");
+        k_last_cc_cross_chunks<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, d.cr, d.lastp, d.dirb, d.klist,
+                                                               d.klist_cap, nlq, d.uf, big, d.err);
+        L.mark("k_last_cc_cross_chunks");
+        // after a weak sample the tiled pass; otherwise it returns at once
+        k_last_cc_cross<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
+            off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, d.err, vec, big);
+        L.mark("k_last_cc_cross");
     } else if (nnz > 0) {
         k_last_cc_cross<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(
-            off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, d.err, vec);
+            off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, d.err, vec, nullptr);
         L.mark("k_last_cc_cross");
     }
     CK(cudaMemsetAsync(d.smin, 0x7f, n * sizeof(int32_t), L.s));

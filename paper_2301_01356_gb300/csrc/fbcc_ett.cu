@@ -113,15 +113,41 @@ __device__ __forceinline__ int hub_sub(int64_t h)
 // exchanges of its many forest edges spread over kHubSub words; sub-list s of hub
 // slot i has its head at hubhead[s * hub_cap + i], so that a hub's heads lie in
 // different cache lines (atomics on one line are processed one at a time).
+// Pushes arc a onto the list whose head is *head, aggregated over runs of
+// neighbouring lanes that push onto the same list (a hub's tree arcs, which come
+// in runs of consecutive edge ids): a run chains its arcs in lane order and its
+// first lane exchanges the head once. A run costs a shuffle and a ballot to find,
+// where matching equal keys anywhere in the warp costs far more and pays only on
+// hub-heavy forests. Every lane calls it; lanes with head == nullptr push nothing.
+// Returns the successor of a in its list.
+__device__ __forceinline__ int32_t push_arc_warp(int32_t *head, int32_t a)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long key =
+        head ? (unsigned long long)head : ~0ull - (unsigned long long)lane;   // an idle lane is its own run
+    const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+    const unsigned upto = starts & ((2u << lane) - 1u);   // run starts at or below this lane (2u << 31 wraps to 0)
+    const int first = 31 - __clz(upto);
+    const bool last = lane == 31 || ((starts >> (lane + 1)) & 1u);
+    int32_t old = 0;
+    if (head && lane == first) old = atomicExch(head, a);   // the run's first arc heads its chain
+    old = __shfl_sync(0xffffffffu, old, first);
+    const int32_t next_a = __shfl_down_sync(0xffffffffu, a, 1);
+    return last ? old : next_a;
+}
+
 __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__restrict__ te_u,
                                                    const int32_t *__restrict__ te_v,
                                                    const int32_t *__restrict__ hubidx, int32_t *lhead,
                                                    int32_t *hubhead, int64_t hub_cap, int32_t *nxt)
 {
-    // four edges per thread and step: their eight exchanges in flight together
+    // four edges per thread and step (their loads in flight together); the pushes
+    // are aggregated per warp, see push_arc_warp
     constexpr int kPer = 4;
     const int64_t T = (int64_t)gridDim.x * kThreads;
-    for (int64_t h0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; h0 < n; h0 += T * kPer) {
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t h0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; h0 < n_pad; h0 += T * kPer) {
         int32_t u[kPer], v[kPer];
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
@@ -137,20 +163,19 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
             hu[k] = __ldg(hubidx + u[k]);
             hv[k] = __ldg(hubidx + v[k]);
         }
-        int2 o[kPer];
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
-            if (u[k] < 0) continue;
             const int64_t h = h0 + k * T;
             const int s = hub_sub(h);   // the sub-list of both arcs of edge h
-            o[k].x = atomicExch(hu[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hu[k] : lhead + u[k], (int32_t)(2 * h));
-            o[k].y = atomicExch(hv[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hv[k] : lhead + v[k],
-                                (int32_t)(2 * h + 1));
-        }
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            if (u[k] < 0) continue;
-            *reinterpret_cast<int2 *>(nxt + 2 * (h0 + k * T)) = o[k];
+            int32_t *pu = nullptr, *pv = nullptr;
+            if (u[k] >= 0) {
+                pu = hu[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hu[k] : lhead + u[k];
+                pv = hv[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hv[k] : lhead + v[k];
+            }
+            int2 o;
+            o.x = push_arc_warp(pu, (int32_t)(2 * h));
+            o.y = push_arc_warp(pv, (int32_t)(2 * h + 1));
+            if (u[k] >= 0) *reinterpret_cast<int2 *>(nxt + 2 * h) = o;
         }
     }
 }

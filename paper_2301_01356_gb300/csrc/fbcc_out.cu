@@ -23,15 +23,15 @@
 //    smallest neighbour of u0 in the BCC. Three cases:
 //      * u0 lies in this BCC only: every neighbour of u0 is in it, and the key is
 //        u0's first arc;
-//      * u0 is the head h and h's list is long (a hub): the neighbours of h in the
-//        BCC are exactly the class members adjacent to h (two adjacent vertices of
-//        one BCC put their edge in it), so each member smaller than the top (which
-//        is adjacent: the tree edge) tests its adjacency to h by a binary search
-//        of its own list, the smallest wins (kmin), and one search of h's list
-//        finds the key;
-//      * otherwise (u0 is a head with a short list, or a class member in several
-//        BCCs) u0's list is scanned, in chunks of kKeyChunk arcs, for the arcs of
-//        this BCC.
+//      * u0 is the head h, h's list is long and h heads few labels for its
+//        length: the neighbours of h in the BCC are exactly the class members
+//        adjacent to h (two adjacent vertices of one BCC put their edge in it),
+//        so each member smaller than the top (which is adjacent: the tree edge)
+//        tests its adjacency to h by a binary search of its own list, the
+//        smallest wins (kmin), and one search of h's list finds the key;
+//      * otherwise (u0 is a head with a short list or with many labels for its
+//        list, or a class member in several BCCs) u0's list is scanned, in
+//        chunks of kKeyChunk arcs, for the arcs of its BCCs.
 //    Keys are set in a bitmap over arcs whose popcount prefix gives each BCC its
 //    rank. (A label is the id of its class's top vertex; smin[l] holds the class's
 //    smallest vertex id.)
@@ -49,8 +49,12 @@ constexpr int kVPer = 4;
 
 // Key of a label whose head is its BCC's smallest vertex: found by k_key_bits.
 constexpr unsigned long long kKeyHead = ~1ull;
-// Heads with at most this many arcs are scanned like the other listed vertices.
+// Heads with at most this many arcs are scanned like the other listed vertices,
+// and so are heads with at most kScanPerLabel arcs per label they head: one scan
+// of such a list finds all their labels' keys for fewer loads than a search of it
+// per label (a hub whose leaf children are each a bridge BCC).
 constexpr int kHeadScan = 32;
+constexpr int kScanPerLabel = 8;
 
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__restrict__ off,
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) k_ap_keys(int64_t n, const OffT *__r
             const int64_t deg = (int64_t)oe[k] - (int64_t)ou[k];
             if ((int)pu[k] + hu[k] == 1) {   // u0 lies in this BCC only: its first arc is the key
                 key[v] = (unsigned long long)ou[k];
-            } else if (f[k].y < sm[k] && deg > kHeadScan) {
+            } else if (f[k].y < sm[k] && deg > kHeadScan && deg > (int64_t)kScanPerLabel * hu[k]) {
                 // u0 is a head with a long list: the class members find their adjacency
                 // to it (the top is adjacent), and a search of its list the key
                 key[v] = kKeyHead;

@@ -31,5 +31,5 @@ def test_knob_values_are_valid_configurations():
             assert cfg["ruler_stride"] >= 8 and cfg["ruler_stride"] & (cfg["ruler_stride"] - 1) == 0
             assert cfg["cc_local"] == 0 or 1024 <= cfg["cc_local"] <= 16384
             assert cfg["chase_chains"] in (1, 2, 4) and cfg["rank_variant"] in (0, 1) and cfg["cc_order"] in (0, 1)
-            assert -64 <= cfg["grid_ctas"] <= 0 and 0 <= cfg["lcc_sample"] <= 64
+            assert -64 <= cfg["grid_ctas"] <= 0 and 0 <= cfg["lcc_sample"] <= 4
             assert cfg["hub_deg"] in (-1, 0) or cfg["hub_deg"] >= 32

@@ -49,10 +49,30 @@ def check(torch, solver, oracle, g, off64=True, what=None):
     return got
 
 
+def wheel_behind_bridge(k):
+    """0 - 1 a bridge, 1 the hub of a wheel on the cycle 2..k+1: the hub (degree k+1)
+    heads one label, whose key a search of the hub's list finds."""
+    u = [0] + [1] * k + list(range(2, k + 1)) + [k + 1]
+    v = [1] + list(range(2, k + 2)) + list(range(3, k + 2)) + [2]
+    return gg.from_edges(k + 2, u, v)
+
+
+def windmill_behind_bridge(k):
+    """0 - 1 a bridge, then k triangles sharing vertex 1: the hub (degree 2k+1) heads
+    k labels, whose keys one scan of its list finds."""
+    u, v = [0], [1]
+    for i in range(k):
+        a, b = 2 + 2 * i, 3 + 2 * i
+        u += [1, 1, a]
+        v += [a, b, b]
+    return gg.from_edges(2 * k + 2, u, v)
+
+
 def small_graphs():
     out = [gg.cycle(3), gg.cycle(50), gg.path(2), gg.path(300), gg.star(40), gg.complete(12),
            gg.grid(7, 9), gg.grid(6, 6, torus=True), gg.cycles_chain_exact([3, 4, 5, 6], 3),
-           gg.from_edges(6, [], []), gg.from_edges(3, [1], [2]), gg.random_tree(500, 3)]
+           gg.from_edges(6, [], []), gg.from_edges(3, [1], [2]), gg.random_tree(500, 3),
+           wheel_behind_bridge(200), windmill_behind_bridge(100)]
     for seed in range(12):
         rng = np.random.default_rng(seed)
         n = int(rng.integers(5, 400))
@@ -107,7 +127,7 @@ def test_repeated_solves_and_configs(torch_cuda, oracle):
     e1, e2 = oracle.solve(g1.offsets, g1.adj), oracle.solve(g2.offsets, g2.adj)
     for cfg in ({}, {"ruler_stride": 8}, {"ruler_stride": 256}, {"cc_sample": 2}, {"use_graph": -1},
                 {"grid_ctas": 3}, {"chase_chains": 4}, {"chase_chains": 2}, {"cc_local": 1024},
-                {"cc_local": 16384}, {"lcc_sample": 2}, {"lcc_sample": 1, "cc_sample": 2}, {"rank_variant": 1},
+                {"cc_local": 16384}, {"lcc_sample": 2}, {"lcc_sample": 1, "cc_sample": 2}, {"lcc_sample": 4}, {"rank_variant": 1},
                 {"grid_ctas": -4}, {"cc_order": 1}, {"cc_order": 1, "cc_local": 1024, "rank_variant": 1},
                 {"hub_deg": -1}, {"hub_deg": 32}, {"hub_deg": 32, "cc_sample": 2, "cc_order": 1}):
         s = fbcc.Solver(20000, 50000, **cfg)
@@ -115,6 +135,48 @@ def test_repeated_solves_and_configs(torch_cuda, oracle):
             for g, e in ((g1, e1), (g2, e2), (g1, e1)):
                 off, adj = to_dev(torch_cuda, g)
                 assert_same(s.solve(off, adj), e, f"{cfg} {g.name}")
+        s.close()
+
+
+def test_sampled_cc_long_lists_outside_the_sampled_component(torch_cuda, oracle):
+    """Sampled First-CC and Last-CC: vertices outside the sampled largest component go
+    through their own lists, a lane per short list, the whole warp per list above 32
+    arcs (a star's centre, a clique, R-MAT hubs) and the whole grid, in chunks, per
+    list above 2048 arcs (a star of 5000 leaves, the two sides of K_{2,3000}) -- every
+    output still equals the oracle, for every sample size."""
+    from paper_2301_01356_gb300 import fbcc
+    k2 = 3000                                  # K_{2,3000}: two lists of 3000 arcs, queued as chunks
+    bip = gg.from_edges(k2 + 2, np.r_[np.zeros(k2, np.int64), np.ones(k2, np.int64)],
+                        np.r_[np.arange(2, k2 + 2), np.arange(2, k2 + 2)])
+    g = gg.disjoint_union(gg.uniform(20000, 60000, 3), gg.star(300), gg.complete(40), gg.path(50),
+                          gg.from_edges(4, [], []), gg.rmat(12, 16, 0.57, 0.19, 0.19, 5), gg.star(5000), bip)
+    e = oracle.solve(g.offsets, g.adj)
+    for cfg in ({"cc_sample": 1}, {"cc_sample": 2}, {"cc_sample": 2, "lcc_sample": 2}, {"lcc_sample": 1},
+                {"lcc_sample": 3}, {"lcc_sample": 4}, {"cc_sample": 1, "lcc_sample": 4}):
+        s = fbcc.Solver(g.n, g.nnz, **cfg)
+        off, adj = to_dev(torch_cuda, g)
+        for _ in range(2):
+            assert_same(s.solve(off, adj), e, f"{cfg}")
+        s.close()
+
+
+def test_sampling_vote_picks_the_pass(torch_cuda, oracle):
+    """After sampling, a vote of arc sources decides the rest: a connected graph's
+    sample wins it and the pass goes by vertex; 200 equal components leave no
+    component with half the votes, and the tiled full pass runs instead. Both
+    give the oracle's outputs."""
+    from paper_2301_01356_gb300 import fbcc
+    one = gg.uniform(30000, 150000, 8)
+    many = gg.disjoint_union(*[gg.uniform(150, 600, 100 + i) for i in range(200)])
+    for g, strong in ((one, 1), (many, 0)):
+        e = oracle.solve(g.offsets, g.adj)
+        s = fbcc.Solver(g.n, g.nnz, cc_sample=2, lcc_sample=4, use_graph=-1)
+        off, adj = to_dev(torch_cuda, g)
+        assert_same(s.solve(off, adj), e, g.name)
+        votes = fbcc.fbcc_debug_read(s.ws, "sampled", 4)
+        assert votes[1] == strong and votes[3] == strong, (g.name, votes)
+        if strong:
+            assert votes[0] >= 0
         s.close()
 
 
