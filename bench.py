@@ -178,6 +178,9 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_cc_init": 4 * n, "k_uf_compress": 4 * n,
         "k_cc_hook": arc_cc, "k_cc_local": arc_cc, "k_cc_hook_rest": arc_cc, "k_cc_hook_cross": 0,
         "k_cc_sample": 0, "k_mark_big": 0, "k_cc_pick_big": 0, "k_cc_hook_chunks": 0,
+        # (the LDD rounds spread the arc pass over up to 64 launches: its bytes stay with the phase)
+        "k_ldd_init": 0, "k_ldd_fill": 0, "k_ldd_expand": 0, "k_ldd_chunks": 0, "k_ldd_unite": 0, "k_ldd_minroot": 0,
+        "k_ldd_reroot": 0,
         # Rooting
         "k_cc_count": 0, "k_cc_place": 0, "k_permute_te": 0, "k_scan_i32": 0, "k_link": 8 * A, "k_hub_order": 0, "k_succ_rulers": 16 * A, "k_chase": 8 * A, "k_lvl_rulers": 0, "k_lvl_chase": 0,
         "k_top": 0, "k_lvl_expand": 0, "k_jump": 0, "k_comp_size": 0, "k_place_records": 8 * A, "k_preorder": 8 * A + 16 * n,
@@ -304,11 +307,11 @@ def tuned_config(args) -> dict:
     given on the command line."""
     from paper_2301_01356_gb300 import batch as B
     cfg = dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0, lcc_sample=0, rank_variant=0, grid_ctas=0,
-               cc_order=0, hub_deg=0)
+               cc_order=0, hub_deg=0, cc_ldd=0)
     if args.config == "tuned":
         cfg.update(B.load_tuning().get("graphs", {}).get(args.workload, {}).get("config", {}))
     for k in ("ruler_stride", "cc_sample", "chase_chains", "cc_local", "lcc_sample", "rank_variant", "grid_ctas",
-              "cc_order", "hub_deg"):
+              "cc_order", "hub_deg", "cc_ldd"):
         v = getattr(args, k)
         if v is not None:
             cfg[k] = v
@@ -867,6 +870,7 @@ def main(argv=None):
     ap.add_argument("--grid-ctas", type=int, default=None, help="CTAs of the persistent grid (0 = 8 per SM)")
     ap.add_argument("--cc-order", type=int, default=None, help="rooting: forest renumbered by component (1 = on)")
     ap.add_argument("--hub-deg", type=int, default=None, help="hub threshold in arcs (0 = 256, -1 = no hubs)")
+    ap.add_argument("--cc-ldd", type=int, default=None, help="First-CC by LDD + union-find: 1/beta (0 = off)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--query-count", type=int, default=1 << 24, help="queries timed after the solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -93,6 +93,10 @@ typedef struct {
                               forest records each tree edge's CSR position (which lets a hub head
                               name its BCC's key without searching its list); 0 = 256, -1 = off
                               (graphs without hubs), else >= 32 */
+    int32_t cc_ldd;        /* First-CC by low-diameter decomposition, then union-find (section 5,
+                              "Connectivity"): 0 = off, else 1/beta of the exponential shifts
+                              (1..64; the decomposition takes ceil(cc_ldd * ln n) rounds, at most
+                              63). cc_local takes precedence over it, it over cc_sample */
 } fbcc_config;
 
 /* Device bytes a workspace for graphs of up to n vertices and nnz arcs holds.
@@ -306,7 +310,10 @@ fbcc_status fbcc_profile_get(const fbcc_workspace *ws, int32_t i, const char **n
  *                              First-CC's largest root and whether it won at least
  *                              half of the votes (1) or the tiled pass ran (0), then
  *                              the same two for Last-CC (a plain-component root by
- *                              preorder number, -1 when no arc voted)
+ *                              preorder number, -1 when no arc voted); after an LDD
+ *                              First-CC the second value is 1 when its list of edges
+ *                              between clusters held them all, 0 when the full hook
+ *                              pass ran
  *   "dirb" (uint8, count up to ceil(nnz_max / 8))  one bit per arc, least
  *                              significant first: the target's preorder number
  *                              exceeds the source's

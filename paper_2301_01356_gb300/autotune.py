@@ -2,7 +2,8 @@
 
 The knobs, each a runtime choice of the library (fbcc_config):
   - First-CC variant: plain hooking, local-first in shared memory over ranges of
-    8192 or 16384 vertices, or sampled (one or two neighbours per vertex first);
+    8192 or 16384 vertices, sampled (one or two neighbours per vertex first), or a
+    low-diameter decomposition before union-find (1/beta = 2 or 8);
   - Last-CC sampling (the first arcs of every vertex tested and their cross
     edges united before the full pass);
   - ruler stride of the list ranking, walks a thread advances together
@@ -36,10 +37,12 @@ from . import batch as B
 from . import fbcc, graphgen as gg
 
 DEFAULT = dict(ruler_stride=16, cc_local=0, cc_sample=0, lcc_sample=0, chase_chains=1, rank_variant=0, grid_ctas=0,
-               cc_order=0, hub_deg=0)
+               cc_order=0, hub_deg=0, cc_ldd=0)
 KNOBS = [
-    ("cc", [dict(cc_local=0, cc_sample=0), dict(cc_local=8192, cc_sample=0), dict(cc_local=16384, cc_sample=0),
-            dict(cc_local=0, cc_sample=1), dict(cc_local=0, cc_sample=2)]),
+    ("cc", [dict(cc_local=0, cc_sample=0, cc_ldd=0), dict(cc_local=8192, cc_sample=0, cc_ldd=0),
+            dict(cc_local=16384, cc_sample=0, cc_ldd=0), dict(cc_local=0, cc_sample=1, cc_ldd=0),
+            dict(cc_local=0, cc_sample=2, cc_ldd=0), dict(cc_local=0, cc_sample=0, cc_ldd=2),
+            dict(cc_local=0, cc_sample=0, cc_ldd=8)]),
     ("ruler_stride", [dict(ruler_stride=s) for s in (8, 16, 32, 64)]),
     ("lcc_sample", [dict(lcc_sample=q) for q in (0, 2, 4)]),
     ("chase_chains", [dict(chase_chains=c) for c in (1, 2)]),

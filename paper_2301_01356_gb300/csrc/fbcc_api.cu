@@ -137,9 +137,13 @@ size_t carve(Dev &d, char *base, int64_t N, int64_t Z)
     d.rec = c.take<int2>(2 * N);
     d.hubhead = c.take<int32_t>(d.hub_cap * kHubSub);
     d.hubnext = c.take<int32_t>(d.hub_cap * kHubSub);
-    const size_t rooting_end = c.used;
+    size_t rooting_end = c.used;
     {
         const size_t at = (xl_from + 255) & ~size_t(255);
+        // First-CC's scratch in this space (LDD: three arrays of N ids and a byte per
+        // vertex, counters and at least a few hundred list entries) always fits
+        const size_t ldd_min = 13 * (size_t)N + 16384;
+        if (rooting_end - at < ldd_min) rooting_end = c.used = at + ldd_min;
         d.xl = base ? reinterpret_cast<int2 *>(base + at) : nullptr;
         d.xl_cap = (int64_t)((rooting_end - at) / sizeof(int2));
     }
@@ -213,6 +217,7 @@ static fbcc_config default_config()
     c.rank_variant = 0;
     c.cc_order = 0;
     c.hub_deg = 0;
+    c.cc_ldd = 0;
     return c;
 }
 
@@ -336,6 +341,8 @@ fbcc_status fbcc_workspace_configure(fbcc_workspace *ws, const fbcc_config *cfg)
         c.cc_order = cfg->cc_order;
         if (cfg->hub_deg < -1 || (cfg->hub_deg > 0 && cfg->hub_deg < kHubMinDeg)) return FBCC_E_INVALID;
         c.hub_deg = cfg->hub_deg;
+        if (cfg->cc_ldd < 0 || cfg->cc_ldd > 64) return FBCC_E_INVALID;
+        c.cc_ldd = cfg->cc_ldd;
         if (cfg->chase_chains) {
             if (cfg->chase_chains != 1 && cfg->chase_chains != 2 && cfg->chase_chains != 4) return FBCC_E_INVALID;
             c.chase_chains = cfg->chase_chains;
@@ -410,7 +417,8 @@ cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *ad
     CK(cudaMemsetAsync(d.stats, 0, sizeof(fbcc_stats), s));
     if (n > 0) {
         const int hub_deg = ws->cfg.hub_deg == 0 ? kHubDeg : ws->cfg.hub_deg;   // -1: no hubs
-        CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, ws->cfg.cc_local, hub_deg, vec, L));
+        CK(launch_first_cc<OffT>(d, off, adj, n, nnz, ws->cfg.cc_sample, ws->cfg.cc_local, ws->cfg.cc_ldd,
+                                 hub_deg, vec, L));
         CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, ws->cfg.chase_chains,
                                 ws->cfg.rank_variant, ws->cfg.cc_order, hub_deg > 0, L));
         CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, ws->cfg.profile != 0, L));

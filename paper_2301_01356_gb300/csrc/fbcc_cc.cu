@@ -118,27 +118,6 @@ __global__ void __launch_bounds__(kThreads) k_mark_big(const int32_t *__restrict
 // hub's list alone. Where sampling gathered nearly every vertex, this touches the
 // offsets and the bitmap and little else.
 constexpr int kRestShort = 32;
-constexpr int kRestLong = 2048;
-constexpr int kRestChunk = 1024;
-
-// Queues the chunks of vertex v's list of len arcs (whole warp, v and len the same
-// in every lane): {v, chunk index} entries. Without room for all of them the warp
-// keeps the list (false); entries it had reserved below the capacity are marked
-// empty, and the drain reads at most `cap` entries.
-__device__ __forceinline__ bool rest_queue(int2 *lq, int64_t cap, long long *nq, int32_t v, int64_t len, int lane)
-{
-    const int64_t nch = (len + kRestChunk - 1) / kRestChunk;
-    long long k = 0;
-    if (lane == 0) k = (long long)atomicAdd((unsigned long long *)nq, (unsigned long long)nch);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    if (k + nch > cap) {
-        for (int64_t c = k + lane; c < cap; c += 32) lq[c] = make_int2(-1, 0);
-        return false;
-    }
-    for (int64_t c = lane; c < nch; c += 32) lq[k + c] = make_int2(v, (int32_t)c);
-    return true;
-}
-
 template <typename OffT>
 __global__ void __launch_bounds__(kThreads) k_cc_hook_rest(const OffT *__restrict__ off,
                                                            const int32_t *__restrict__ adj, int64_t n, int32_t *uf,
@@ -446,7 +425,7 @@ cudaError_t prepare_cc_local(int V)
 
 template <typename OffT>
 cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                            int cc_sample, int cc_local, int hub_deg, bool vec, const Launch &L)
+                            int cc_sample, int cc_local, int cc_ldd, int hub_deg, bool vec, const Launch &L)
 {
     const int64_t ntiles = ceil_div(nnz, kWTile);
     const int gv = grid_for(L, ceil_div(n, kThreads));
@@ -472,6 +451,15 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
             k_cc_hook_cross<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, cc_local, d.xl,
                                                            d.xl_cap, nxl, d.uf, d.te_u, d.te_v, te_a, d.err, vec);
             L.mark("k_cc_hook_cross");
+        } else if (cc_ldd > 0) {
+            int32_t *flag = reinterpret_cast<int32_t *>(d.counters + 8);
+            const cudaError_t e = launch_ldd_forest<OffT>(d, off, adj, n, nnz, cc_ldd, te_a, flag, L);
+            if (e != cudaSuccess) return e;
+            // when the list of edges between clusters overflowed, every arc as without
+            // LDD; otherwise it returns at once
+            k_cc_hook<OffT><<<ga, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.uf, d.te_u, d.te_v,
+                                                     te_a, d.err, vec, flag);
+            L.mark("k_cc_hook");
         } else if (cc_sample > 0) {
             int32_t *big = reinterpret_cast<int32_t *>(d.counters + 8);
             k_cc_sample<OffT><<<gv, kThreads, 0, L.s>>>(off, adj, n, cc_sample, d.uf, d.te_u, d.te_v, te_a,
@@ -505,6 +493,7 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
     }
     k_uf_compress<<<gv, kThreads, 0, L.s>>>(d.uf, n);
     L.mark("k_uf_compress");
+    if (nnz > 0 && cc_local <= 0 && cc_ldd > 0) return launch_ldd_reroot(d, n, L);
     return cudaGetLastError();
 }
 
@@ -931,9 +920,9 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
 }
 
 template cudaError_t launch_first_cc<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
-                                              int, int, bool, const Launch &);
+                                              int, int, int, bool, const Launch &);
 template cudaError_t launch_first_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,
-                                              int, int, bool, const Launch &);
+                                              int, int, int, bool, const Launch &);
 template cudaError_t launch_last_cc<int32_t>(const Dev &, const int32_t *, const int32_t *, int64_t, int64_t, int,
                                              bool, const Launch &);
 template cudaError_t launch_last_cc<int64_t>(const Dev &, const int64_t *, const int32_t *, int64_t, int64_t, int,

@@ -230,6 +230,29 @@ __device__ __forceinline__ int32_t uf_unite(int32_t *uf, int32_t u, int32_t v, i
     return -1;
 }
 
+// Lists above kRestLong arcs, in passes that go by vertex, are cut into chunks of
+// kRestChunk arcs that a second launch spreads over the whole grid.
+constexpr int kRestLong = 2048;
+constexpr int kRestChunk = 1024;
+
+// Queues the chunks of vertex v's list of len arcs (whole warp, v and len the same
+// in every lane): {v, chunk index} entries. Without room for all of them the warp
+// keeps the list (false); entries it had reserved below the capacity are marked
+// empty, and the drain reads at most `cap` entries.
+__device__ __forceinline__ bool rest_queue(int2 *lq, int64_t cap, long long *nq, int32_t v, int64_t len, int lane)
+{
+    const int64_t nch = (len + kRestChunk - 1) / kRestChunk;
+    long long k = 0;
+    if (lane == 0) k = (long long)atomicAdd((unsigned long long *)nq, (unsigned long long)nch);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k + nch > cap) {
+        for (int64_t c = k + lane; c < cap; c += 32) lq[c] = make_int2(-1, 0);
+        return false;
+    }
+    for (int64_t c = lane; c < nch; c += 32) lq[k + c] = make_int2(v, (int32_t)c);
+    return true;
+}
+
 __device__ __forceinline__ int32_t warp_sum_i32(int32_t x)
 {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -504,7 +527,7 @@ __device__ __forceinline__ bool dir_bit(const uint8_t *dirb, int64_t a)
 // Host side
 // ---------------------------------------------------------------------------
 // Per-kernel timing of a solve (fbcc_config.profile): an event after every launch.
-constexpr int kProfMax = 160;
+constexpr int kProfMax = 320;
 struct Prof {
     int count = 0;
     const char *names[kProfMax];
@@ -537,7 +560,14 @@ inline int grid_for(const Launch &L, int64_t items_per_cta_units)
 // Phase launchers (each returns the first launch error or cudaSuccess).
 template <typename OffT>
 cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
-                            int cc_sample, int cc_local, int hub_deg, bool vec, const Launch &L);
+                            int cc_sample, int cc_local, int cc_ldd, int hub_deg, bool vec, const Launch &L);
+// First-CC by LDD: the clusters' forest edges and the union of the edges between
+// clusters (flag[1] = 0 when their list overflowed and a full hook pass must
+// follow); after the flatten, the roots moved to each component's smallest vertex.
+template <typename OffT>
+cudaError_t launch_ldd_forest(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                              int inv_beta, int32_t *te_a, int32_t *flag, const Launch &L);
+cudaError_t launch_ldd_reroot(const Dev &d, int64_t n, const Launch &L);
 // Allow the local-first First-CC kernel its shared memory for ranges of V vertices.
 cudaError_t prepare_cc_local(int V);
 template <typename OffT>

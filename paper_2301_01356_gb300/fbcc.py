@@ -40,7 +40,8 @@ class fbcc_config(ctypes.Structure):
     _fields_ = [("ruler_stride", ctypes.c_int32), ("cc_sample", ctypes.c_int32),
                 ("grid_ctas", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("chase_chains", ctypes.c_int32), ("cc_local", ctypes.c_int32), ("lcc_sample", ctypes.c_int32),
-                ("rank_variant", ctypes.c_int32), ("cc_order", ctypes.c_int32), ("hub_deg", ctypes.c_int32)]
+                ("rank_variant", ctypes.c_int32), ("cc_order", ctypes.c_int32), ("hub_deg", ctypes.c_int32),
+                ("cc_ldd", ctypes.c_int32)]
 
 
 class FbccError(RuntimeError):
@@ -153,9 +154,9 @@ def fbcc_workspace_destroy(ws: int) -> None:
 
 def fbcc_workspace_configure(ws: int, ruler_stride=0, cc_sample=0, grid_ctas=0, use_graph=0, profile=0,
                              chase_chains=0, cc_local=0, lcc_sample=0, rank_variant=0, cc_order=0,
-                             hub_deg=0) -> None:
+                             hub_deg=0, cc_ldd=0) -> None:
     cfg = fbcc_config(ruler_stride, cc_sample, grid_ctas, use_graph, profile, chase_chains, cc_local, lcc_sample,
-                      rank_variant, cc_order, hub_deg)
+                      rank_variant, cc_order, hub_deg, cc_ldd)
     _check(load().fbcc_workspace_configure(ws, ctypes.byref(cfg)), "fbcc_workspace_configure")
 
 

@@ -5,7 +5,7 @@ import json
 def test_coordinate_descent_finds_a_separable_optimum():
     from paper_2301_01356_gb300 import autotune as A
     want = dict(cc_local=16384, cc_sample=0, ruler_stride=32, lcc_sample=2, chase_chains=2, rank_variant=1,
-                grid_ctas=-4, cc_order=1, hub_deg=-1)
+                grid_ctas=-4, cc_order=1, hub_deg=-1, cc_ldd=0)
     calls = []
 
     def measure(cfg, reps):
@@ -33,3 +33,4 @@ def test_knob_values_are_valid_configurations():
             assert cfg["chase_chains"] in (1, 2, 4) and cfg["rank_variant"] in (0, 1) and cfg["cc_order"] in (0, 1)
             assert -64 <= cfg["grid_ctas"] <= 0 and 0 <= cfg["lcc_sample"] <= 4
             assert cfg["hub_deg"] in (-1, 0) or cfg["hub_deg"] >= 32
+            assert 0 <= cfg["cc_ldd"] <= 64 and (cfg["cc_ldd"] == 0 or cfg["cc_local"] == cfg["cc_sample"] == 0)

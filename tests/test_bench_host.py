@@ -209,7 +209,7 @@ def test_tuned_config_and_overrides():
     from paper_2301_01356_gb300 import batch as B
     tuned = B.load_tuning()["graphs"]["grid4096"]["config"]
     none = dict(ruler_stride=None, cc_sample=None, chase_chains=None, cc_local=None, lcc_sample=None,
-                rank_variant=None, grid_ctas=None, cc_order=None, hub_deg=None)
+                rank_variant=None, grid_ctas=None, cc_order=None, hub_deg=None, cc_ldd=None)
     a = argparse.Namespace(config="tuned", workload="grid4096", **none)
     cfg = bench.tuned_config(a)
     assert all(cfg[k] == v for k, v in tuned.items())
@@ -217,7 +217,7 @@ def test_tuned_config_and_overrides():
     assert bench.tuned_config(a)["ruler_stride"] == 8
     a = argparse.Namespace(config="default", workload="grid4096", **none)
     assert bench.tuned_config(a) == dict(ruler_stride=16, cc_sample=0, chase_chains=1, cc_local=0, lcc_sample=0,
-                                         rank_variant=0, grid_ctas=0, cc_order=0, hub_deg=0)
+                                         rank_variant=0, grid_ctas=0, cc_order=0, hub_deg=0, cc_ldd=0)
 
 
 def test_bucket_summary_groups_chunks():

@@ -129,7 +129,8 @@ def test_repeated_solves_and_configs(torch_cuda, oracle):
                 {"grid_ctas": 3}, {"chase_chains": 4}, {"chase_chains": 2}, {"cc_local": 1024},
                 {"cc_local": 16384}, {"lcc_sample": 2}, {"lcc_sample": 1, "cc_sample": 2}, {"lcc_sample": 4}, {"rank_variant": 1},
                 {"grid_ctas": -4}, {"cc_order": 1}, {"cc_order": 1, "cc_local": 1024, "rank_variant": 1},
-                {"hub_deg": -1}, {"hub_deg": 32}, {"hub_deg": 32, "cc_sample": 2, "cc_order": 1}):
+                {"hub_deg": -1}, {"hub_deg": 32}, {"hub_deg": 32, "cc_sample": 2, "cc_order": 1},
+                {"cc_ldd": 1}, {"cc_ldd": 4}, {"cc_ldd": 16, "cc_order": 1}, {"cc_ldd": 2, "hub_deg": 32}):
         s = fbcc.Solver(20000, 50000, **cfg)
         for _ in range(2):
             for g, e in ((g1, e1), (g2, e2), (g1, e1)):
@@ -152,7 +153,8 @@ def test_sampled_cc_long_lists_outside_the_sampled_component(torch_cuda, oracle)
                           gg.from_edges(4, [], []), gg.rmat(12, 16, 0.57, 0.19, 0.19, 5), gg.star(5000), bip)
     e = oracle.solve(g.offsets, g.adj)
     for cfg in ({"cc_sample": 1}, {"cc_sample": 2}, {"cc_sample": 2, "lcc_sample": 2}, {"lcc_sample": 1},
-                {"lcc_sample": 3}, {"lcc_sample": 4}, {"cc_sample": 1, "lcc_sample": 4}):
+                {"lcc_sample": 3}, {"lcc_sample": 4}, {"cc_sample": 1, "lcc_sample": 4}, {"cc_ldd": 2},
+                {"cc_ldd": 8, "lcc_sample": 2}):
         s = fbcc.Solver(g.n, g.nnz, **cfg)
         off, adj = to_dev(torch_cuda, g)
         for _ in range(2):
@@ -177,6 +179,26 @@ def test_sampling_vote_picks_the_pass(torch_cuda, oracle):
         assert votes[1] == strong and votes[3] == strong, (g.name, votes)
         if strong:
             assert votes[0] >= 0
+        s.close()
+
+
+def test_ldd_forest_and_list_overflow(torch_cuda, oracle):
+    """First-CC by LDD + union-find: the clusters' reaching edges plus the hooks over
+    the edges between clusters span every component with its smallest vertex as root
+    (the forest is checked in the phase tests), and the outputs equal the oracle's.
+    With 1/beta = 64 over a third of the vertices wake in round 0, the clusters stay
+    tiny, the list of edges between clusters outgrows its space, and the full hook
+    pass takes over (flag 0); a sparse graph keeps the list (flag 1)."""
+    from paper_2301_01356_gb300 import fbcc
+    for g, cfg, held in ((gg.uniform(30000, 150000, 8), {"cc_ldd": 2}, 1),
+                         (gg.grid(300, 280, p=0.62, extra_frac=0.001, seed=4), {"cc_ldd": 8}, 1),
+                         (gg.uniform(200000, 4000000, 12), {"cc_ldd": 64}, 0)):
+        e = oracle.solve(g.offsets, g.adj)
+        s = fbcc.Solver(g.n, g.nnz, use_graph=-1, **cfg)
+        off, adj = to_dev(torch_cuda, g)
+        for _ in range(2):
+            assert_same(s.solve(off, adj), e, f"{g.name} {cfg}")
+        assert fbcc.fbcc_debug_read(s.ws, "sampled", 2)[1] == held, (g.name, cfg)
         s.close()
 
 

@@ -146,3 +146,4 @@ def test_phases(torch_cuda, family):
     phase_check(torch_cuda, g)
     phase_check(torch_cuda, g, {"ruler_stride": 8, "cc_local": 4096})
     phase_check(torch_cuda, g, {"cc_sample": 2, "lcc_sample": 2})
+    phase_check(torch_cuda, g, {"cc_ldd": 4})
