@@ -146,7 +146,8 @@ class ClockSampler:
 # Algorithm 1's steps as the profiled kernels run them: a phase starts at its first
 # kernel and lasts until the next phase starts.
 PHASES = ("first_cc", "rooting", "tagging", "last_cc", "outputs")
-PHASE_START = {"k_cc_count": "rooting", "k_link": "rooting", "k_first_of": "tagging", "k_ext_compact": "last_cc", "k_ap_keys": "outputs"}
+PHASE_START = {"k_cc_count": "rooting", "k_link": "rooting", "k_first_of": "tagging", "k_ext_compact": "last_cc",
+               "k_tv_init": "last_cc", "k_ap_keys": "outputs"}
 
 
 def phase_bytes(n: int, nnz: int, n_cc: int, off_bytes: int) -> dict:
@@ -192,6 +193,10 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_last_cc_cross": B * n + 4 * nnz + 20 * n, "k_last_cc_cross_rest": B * n + 4 * nnz + 20 * n,
         "k_lcc_sample": 0, "k_last_cc_cross_chunks": 0, "k_pos_compress": 0, "k_pos_pick_big": 0,
         "k_final_label": 8 * n,
+        # the Tarjan-Vishkin foil in place of Last-CC: its skeleton's pairs are
+        # written and read once, and the union-find over n + nnz ids set up once
+        "k_tv_init": 4 * (n + nnz), "k_tv_arcs": B * n + 4 * nnz + 8 * nnz, "k_tv_tree": 8 * n,
+        "k_tv_unite": 8 * (nnz + n),
         # Outputs
         "k_ap_keys": 12 * n, "k_key_list": 0, "k_key_adj": 0, "k_key_scan": 0, "k_key_bits": 0, "k_scan_popc": 0, "k_rank": 0, "k_fo": 0,
         "k_edge_out": B * n + 9 * nnz, "k_bcc_base": 0, "k_batch_stats": 0, "k_finish": 0,
@@ -409,6 +414,44 @@ def time_queries(torch, solver, off, adj, n: int, nnz: int, g, count: int) -> di
             "api": "fbcc_query_biconnected; fbcc_query_bcc_count + fbcc_query_bccs_of (device arrays)"}
 
 
+def time_tv_foil(torch, solver, off, adj, n: int, nnz: int, flush, reps: int = 5) -> dict:
+    """The Tarjan-Vishkin foil on the same workload and workspace (the skeleton built
+    explicitly in caller memory instead of Last-CC's implicit one): CUDA-event time
+    per solve (L2 flushed between solves), its scratch bytes against the workspace's,
+    and whether every output equals FAST-BCC's."""
+    from paper_2301_01356_gb300 import fbcc
+    solver.enqueue(off, adj)
+    torch.cuda.synchronize()
+    ref = (solver.edge_bcc[:nnz].clone(), solver.is_ap[:n].clone(), solver.is_bridge[:nnz].clone(),
+           solver.bcc_head[:n].clone(), solver.stats.as_dict())
+    scratch_bytes = fbcc.fbcc_tv_scratch_bytes(n, nnz)
+    scratch = torch.empty(scratch_bytes, dtype=torch.uint8, device="cuda")
+    m = nnz // 2
+    tv = lambda: fbcc.fbcc_solve_tv(off, adj, n, m, solver.edge_bcc, solver.bcc_head, solver.is_ap,
+                                     solver.is_bridge, scratch, solver.ws, None, solver.stats)
+    tv()
+    torch.cuda.synchronize()
+    st = solver.stats.as_dict()
+    nb = st["n_bcc"]
+    same = (torch.equal(ref[0], solver.edge_bcc[:nnz]) and torch.equal(ref[1], solver.is_ap[:n])
+            and torch.equal(ref[2], solver.is_bridge[:nnz]) and torch.equal(ref[3][:nb], solver.bcc_head[:nb])
+            and all(st[k] == ref[4][k] for k in ("n_bcc", "n_ap", "n_bridge", "n_cc")))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        tv()
+        b.record()
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
+    del scratch
+    ws_bytes = fbcc.fbcc_workspace_bytes(solver.n_max, solver.nnz_max)
+    return {"ms_per_solve": ms, "undirected_edges_per_s": m / (ms / 1e3), "scratch_bytes": scratch_bytes,
+            "workspace_bytes": ws_bytes, "scratch_over_workspace": scratch_bytes / ws_bytes,
+            "outputs_equal_fbcc": bool(same),
+            "api": "fbcc_solve_tv (direct launches) on the same workspace, scratch in a caller tensor"}
+
+
 def run_gpu(args, world, rank, local):
     import torch
     from paper_2301_01356_gb300 import fbcc
@@ -484,6 +527,7 @@ def run_gpu(args, world, rank, local):
                              args.workload)
 
     queries = time_queries(torch, solver, off, adj, n, nnz, g, args.query_count)
+    tv_foil = time_tv_foil(torch, solver, off, adj, n, nnz, flush) if n + nnz < 2**31 - 1 else None
 
     # end to end through the public host API: pinned host in, pinned host out
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
@@ -574,6 +618,7 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "queries": queries,
+        "tv_foil": tv_foil,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "parity_vs_oracle": parity,

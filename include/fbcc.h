@@ -156,6 +156,29 @@ fbcc_status fbcc_solve(const void *csr_offsets, int offsets_64, const int32_t *c
                        fbcc_stats *stats, fbcc_workspace *ws, void *stream);
 
 /*
+ * The Tarjan-Vishkin foil (section 3.2; the skeleton's three rules are in the
+ * appendix on Tarjan-Vishkin, its O(m) space in the appendix on its performance):
+ * the same outputs as fbcc_solve, with Last-CC's implicit skeleton replaced by
+ * Tarjan-Vishkin's explicit one. The skeleton has one vertex per edge of G, and a
+ * list of up to m + n vertex pairs is materialised in `scratch` and united. The
+ * forest, rooting and tags are FAST-BCC's, on `ws`; the labels it produces equal
+ * Last-CC's, so every output equals fbcc_solve's.
+ *   scratch        device, 256-byte aligned, at least fbcc_tv_scratch_bytes(n, 2m)
+ *                  bytes (12 per arc and 16 per vertex: the O(m) auxiliary space
+ *                  that FAST-BCC avoids), owned by the caller, untouched after the
+ *                  stream is synchronised
+ * The solve is enqueued with direct launches (no CUDA graph). Returns
+ * FBCC_E_WORKSPACE when scratch is too small, FBCC_E_INVALID for n + 2m >= 2^31
+ * (the skeleton's 32-bit vertex ids) or an unaligned scratch; otherwise as
+ * fbcc_solve. Calls on one workspace must not overlap on the device.
+ */
+size_t fbcc_tv_scratch_bytes(int64_t n, int64_t nnz);
+fbcc_status fbcc_solve_tv(const void *csr_offsets, int offsets_64, const int32_t *csr_adj,
+                          int64_t n, int64_t m,
+                          int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
+                          fbcc_stats *stats, void *scratch, size_t scratch_bytes, fbcc_workspace *ws, void *stream);
+
+/*
  * Same as fbcc_solve with every buffer in HOST memory (pinned memory makes the
  * copies asynchronous-capable). The inputs are copied into workspace-owned device
  * staging buffers, solved, and the outputs copied back; the call returns after the

@@ -400,7 +400,7 @@ __global__ void k_batch_globalize(int32_t G, const int64_t *__restrict__ vtx_bas
 template <typename OffT>
 cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *adj, int64_t n, int64_t m,
                           int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge, cudaStream_t s,
-                          const Batch &B = Batch())
+                          const Batch &B = Batch(), const TvScratch *tv = nullptr)
 {
     const Dev &d = ws->d;
     const int64_t nnz = 2 * m;
@@ -422,7 +422,8 @@ cudaError_t enqueue_solve(fbcc_workspace *ws, const OffT *off, const int32_t *ad
         CK(launch_rooting<OffT>(d, off, adj, n, nnz, ws->cfg.ruler_stride, ws->cfg.chase_chains,
                                 ws->cfg.rank_variant, ws->cfg.cc_order, hub_deg > 0, L));
         CK(launch_tagging<OffT>(d, off, adj, n, nnz, vec, ws->cfg.profile != 0, L));
-        CK(launch_last_cc<OffT>(d, off, adj, n, nnz, ws->cfg.lcc_sample, vec, L));
+        if (tv) CK(launch_tv_connect<OffT>(d, off, adj, n, nnz, *tv, vec, L));
+        else CK(launch_last_cc<OffT>(d, off, adj, n, nnz, ws->cfg.lcc_sample, vec, L));
         CK(launch_outputs<OffT>(d, off, adj, n, nnz, vec, hub_deg > 0, edge_bcc, bcc_head, is_ap, is_bridge, B,
                                 L));
     }
@@ -517,6 +518,37 @@ size_t batch_stage_bytes(int64_t N, int64_t Z, int32_t G)
 }  // namespace
 
 extern "C" {
+
+size_t fbcc_tv_scratch_bytes(int64_t n, int64_t nnz)
+{
+    return tv_scratch_bytes(n < 0 ? 0 : n, nnz < 0 ? 0 : nnz);
+}
+
+fbcc_status fbcc_solve_tv(const void *csr_offsets, int offsets_64, const int32_t *csr_adj, int64_t n, int64_t m,
+                          int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge,
+                          fbcc_stats *stats, void *scratch, size_t scratch_bytes, fbcc_workspace *ws, void *stream)
+{
+    fbcc_status st = check_args(csr_offsets, csr_adj, n, m, edge_bcc, bcc_head, is_ap, is_bridge, ws);
+    if (st != FBCC_OK) return st;
+    if (n + 2 * m >= INT32_MAX) return FBCC_E_INVALID;   // skeleton vertices are 32-bit ids
+    if (!scratch || ((uintptr_t)scratch & 255)) return FBCC_E_INVALID;
+    if (scratch_bytes < tv_scratch_bytes(n, 2 * m)) return FBCC_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    ws->last_n = n;
+    ws->qindex = false;
+    if (ws->cfg.profile && !ws->prof.ready) {
+        for (int i = 0; i <= kProfMax; ++i) API_CK(cudaEventCreate(&ws->prof.ev[i]), "cudaEventCreate");
+        ws->prof.ready = true;
+    }
+    const TvScratch tv{scratch, scratch_bytes};
+    API_CK(offsets_64 ? enqueue_solve<int64_t>(ws, (const int64_t *)csr_offsets, csr_adj, n, m, edge_bcc, bcc_head,
+                                               is_ap, is_bridge, s, Batch(), &tv)
+                      : enqueue_solve<int32_t>(ws, (const int32_t *)csr_offsets, csr_adj, n, m, edge_bcc, bcc_head,
+                                               is_ap, is_bridge, s, Batch(), &tv),
+           "enqueue (Tarjan-Vishkin)");
+    if (stats) API_CK(cudaMemcpyAsync(stats, ws->d.stats, sizeof(fbcc_stats), cudaMemcpyDeviceToHost, s), "stats copy");
+    return FBCC_OK;
+}
 
 fbcc_status fbcc_solve(const void *csr_offsets, int offsets_64, const int32_t *csr_adj, int64_t n, int64_t m,
                        int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap, uint8_t *is_bridge, fbcc_stats *stats,

@@ -911,11 +911,19 @@ cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, in
             off, adj, nnz, d.tile_v, ntiles, d.cr, d.lastp, d.dirb, d.uf, d.err, vec, nullptr);
         L.mark("k_last_cc_cross");
     }
-    CK(cudaMemsetAsync(d.smin, 0x7f, n * sizeof(int32_t), L.s));
-    CK(cudaMemsetAsync(d.nh, 0, n * sizeof(int32_t), L.s));
-    k_final_label<<<gv, kThreads, 0, L.s>>>(n, d.lp, d.uf, d.ord, d.porig, d.lab, d.smin, d.nh, d.stats, d.err);
-    L.mark("k_final_label");
+    CK(launch_final_labels(d, n, d.lp, d.uf, L));
 #undef CK
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_labels(const Dev &d, int64_t n, const int32_t *lp, const int32_t *uf, const Launch &L)
+{
+    cudaError_t e = cudaMemsetAsync(d.smin, 0x7f, n * sizeof(int32_t), L.s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.nh, 0, n * sizeof(int32_t), L.s);
+    if (e != cudaSuccess) return e;
+    k_final_label<<<grid_for(L, ceil_div(n, kThreads)), kThreads, 0, L.s>>>(n, lp, uf, d.ord, d.porig, d.lab, d.smin,
+                                                                          d.nh, d.stats, d.err);
+    L.mark("k_final_label");
     return cudaGetLastError();
 }
 

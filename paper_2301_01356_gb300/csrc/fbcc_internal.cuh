@@ -253,6 +253,23 @@ __device__ __forceinline__ bool rest_queue(int2 *lq, int64_t cap, long long *nq,
     return true;
 }
 
+// One slot per wanting lane, reserved with one atomic per warp (the whole warp
+// calls); slots at or above cap are counted but not written.
+template <typename T>
+__device__ __forceinline__ void warp_append(T *q, long long *cnt, int64_t cap, bool want, T val)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    long long base = 0;
+    if (lane == leader) base = (long long)atomicAdd((unsigned long long *)cnt, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) {
+        const long long i = base + __popc(m & ((1u << lane) - 1u));
+        if (i < cap) q[i] = val;
+    }
+}
+
 __device__ __forceinline__ int32_t warp_sum_i32(int32_t x)
 {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -580,6 +597,20 @@ cudaError_t launch_tagging(const Dev &d, const OffT *off, const int32_t *adj, in
 template <typename OffT>
 cudaError_t launch_last_cc(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            int lcc_sample, bool vec, const Launch &L);
+// Labels from a union-find over positions (uf; lp the plain-component pointers,
+// the identity where uf holds every union): lab, smin, nh and the BCC count.
+cudaError_t launch_final_labels(const Dev &d, int64_t n, const int32_t *lp, const int32_t *uf, const Launch &L);
+// The Tarjan-Vishkin skeleton (section 3.2; its rules in the appendix on
+// Tarjan-Vishkin) built explicitly in caller memory and connected in place of
+// Last-CC.
+struct TvScratch {
+    void *mem;
+    size_t bytes;
+};
+size_t tv_scratch_bytes(int64_t n, int64_t nnz);
+template <typename OffT>
+cudaError_t launch_tv_connect(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
+                              const TvScratch &tv, bool vec, const Launch &L);
 template <typename OffT>
 cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, int64_t n, int64_t nnz,
                            bool vec, bool hubs, int32_t *edge_bcc, int32_t *bcc_head, uint8_t *is_ap,

@@ -41,23 +41,6 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k)
     return z ^ (z >> 31);
 }
 
-// One slot per wanting lane, reserved with one atomic per warp (the whole warp
-// calls); slots at or above cap are counted but not written.
-template <typename T>
-__device__ __forceinline__ void warp_append(T *q, long long *cnt, int64_t cap, bool want, T val)
-{
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    long long base = 0;
-    if (lane == leader) base = (long long)atomicAdd((unsigned long long *)cnt, (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (want) {
-        const long long i = base + __popc(m & ((1u << lane) - 1u));
-        if (i < cap) q[i] = val;
-    }
-}
-
 // Wake rounds, the count of vertices waking in each round (a histogram in shared
 // memory per CTA), and the centres of round 0 (their queue is q0).
 __global__ void __launch_bounds__(kThreads) k_ldd_init(int64_t n, int inv_beta, int D, uint64_t seed,

@@ -25,6 +25,7 @@ EXPORTS = (
     "fbcc_solve", "fbcc_solve_host", "fbcc_solve_host_async", "fbcc_solve_noalloc", "fbcc_solve_batch", "fbcc_batch_workspace_bytes", "fbcc_validate",
     "fbcc_profile_count", "fbcc_profile_get", "fbcc_debug_read", "fbcc_status_string", "fbcc_last_cuda_error",
     "fbcc_query_biconnected", "fbcc_query_bcc_count", "fbcc_query_bccs_of", "fbcc_workspace_create_in",
+    "fbcc_solve_tv", "fbcc_tv_scratch_bytes",
 )
 
 
@@ -86,6 +87,10 @@ def load(path: str = LIB_PATH):
             f.restype = INT
         lib.fbcc_solve_noalloc.argtypes = [P, INT, P, I64, I64, P, P, P, P, P, P]
         lib.fbcc_solve_noalloc.restype = INT
+        lib.fbcc_solve_tv.argtypes = [P, INT, P, I64, I64, P, P, P, P, P, P, ctypes.c_size_t, P, P]
+        lib.fbcc_solve_tv.restype = INT
+        lib.fbcc_tv_scratch_bytes.argtypes = [I64, I64]
+        lib.fbcc_tv_scratch_bytes.restype = ctypes.c_size_t
         lib.fbcc_solve_batch.argtypes = [I32, P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.fbcc_solve_batch.restype = INT
         lib.fbcc_batch_workspace_bytes.argtypes = [I64, I64, I32]
@@ -158,6 +163,24 @@ def fbcc_workspace_configure(ws: int, ruler_stride=0, cc_sample=0, grid_ctas=0, 
     cfg = fbcc_config(ruler_stride, cc_sample, grid_ctas, use_graph, profile, chase_chains, cc_local, lcc_sample,
                       rank_variant, cc_order, hub_deg, cc_ldd)
     _check(load().fbcc_workspace_configure(ws, ctypes.byref(cfg)), "fbcc_workspace_configure")
+
+
+def fbcc_tv_scratch_bytes(n: int, nnz: int) -> int:
+    return int(load().fbcc_tv_scratch_bytes(n, nnz))
+
+
+def fbcc_solve_tv(offsets, adj, n: int, m: int, edge_bcc, bcc_head, is_ap, is_bridge, scratch, ws: int,
+                  stream=None, stats: fbcc_stats | None = None) -> fbcc_stats:
+    """The Tarjan-Vishkin foil: fbcc_solve's outputs through the explicit skeleton,
+    built in the device tensor ``scratch`` (fbcc_tv_scratch_bytes(n, 2m) bytes)."""
+    import torch
+    stats = stats if stats is not None else fbcc_stats()
+    off64 = int(offsets.dtype == torch.int64)
+    _check(load().fbcc_solve_tv(_ptr(offsets), off64, _ptr(adj), n, m, _ptr(edge_bcc), _ptr(bcc_head), _ptr(is_ap),
+                                _ptr(is_bridge), ctypes.byref(stats), _ptr(scratch),
+                                scratch.numel() * scratch.element_size(), ws, _stream_handle(stream)),
+           "fbcc_solve_tv")
+    return stats
 
 
 def fbcc_solve(offsets, adj, n: int, m: int, edge_bcc, bcc_head, is_ap, is_bridge, ws: int,
@@ -300,6 +323,26 @@ class Solver:
         n = offsets.numel() - 1
         nnz = adj.numel()
         st = self.enqueue(offsets, adj, stream)
+        (stream or torch.cuda.current_stream()).synchronize()
+        s = st.as_dict()
+        return {
+            "edge_bcc": self.edge_bcc[:nnz].cpu().numpy(),
+            "bcc_head": self.bcc_head[:s["n_bcc"]].cpu().numpy(),
+            "is_ap": self.is_ap[:n].cpu().numpy(),
+            "is_bridge": self.is_bridge[:nnz].cpu().numpy(),
+            **s,
+        }
+
+    def solve_tv(self, offsets, adj, scratch=None, stream=None) -> dict:
+        """The Tarjan-Vishkin foil on this workspace (scratch: a uint8 device tensor of
+        at least fbcc_tv_scratch_bytes(n, nnz) bytes, allocated here when None)."""
+        import torch
+        n = offsets.numel() - 1
+        nnz = adj.numel()
+        if scratch is None:
+            scratch = torch.empty(fbcc_tv_scratch_bytes(n, nnz), dtype=torch.uint8, device=self.device)
+        st = fbcc_solve_tv(offsets, adj, n, nnz // 2, self.edge_bcc, self.bcc_head, self.is_ap, self.is_bridge,
+                           scratch, self.ws, stream, self.stats)
         (stream or torch.cuda.current_stream()).synchronize()
         s = st.as_dict()
         return {
