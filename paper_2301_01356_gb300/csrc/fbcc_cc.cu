@@ -14,35 +14,54 @@
 namespace fbcc {
 
 // tile_v[t] = source of arc t*kWTile; tile_v[ntiles] = source of the last arc.
-// Also resets the union-find and the tree-edge record.
+// Also resets the union-find and the tree-edge record, finds the hubs (hub_deg >
+// 0: a vertex of at least hub_deg arcs gets a hub slot while slots last, a warp's
+// hubs taking consecutive slots with one atomic; rooting uses them to split their
+// forest-arc lists), and the largest degree, by which rooting decides how to
+// aggregate its list pushes (each warp's maximum over its vertices, with one
+// atomic when it beats the value read from L2).
 template <typename OffT>
-// Also finds the hubs (hub_deg > 0): a vertex of at least hub_deg arcs gets a hub
-// slot (while slots last), which rooting uses to split its forest-arc list.
 __global__ void __launch_bounds__(kThreads) k_cc_init(const OffT *__restrict__ off, int64_t n, int64_t nnz,
                                                       int32_t *tile_v, int64_t ntiles, int32_t *uf,
                                                       int32_t *te_u, int hub_deg, int32_t *hubidx,
-                                                      int32_t *hubvert, int64_t hub_cap, long long *nhub)
+                                                      int32_t *hubvert, int64_t hub_cap, long long *nhub,
+                                                      int32_t *maxdeg)
 {
-    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
-        uf[v] = (int32_t)v;
-        te_u[v] = -1;
-        int64_t b = off[v], e = off[v + 1];
-        if (e > b) {
-            for (int64_t t = (b + kWTile - 1) / kWTile; t * kWTile < e; ++t) tile_v[t] = (int32_t)v;
-            if (b <= nnz - 1 && nnz - 1 < e) tile_v[ntiles] = (int32_t)v;
+    int64_t top = 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_pad = (n + 31) & ~31ll;
+    for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n_pad; v += (int64_t)gridDim.x * kThreads) {
+        int64_t b = 0, e = 0;
+        if (v < n) {
+            uf[v] = (int32_t)v;
+            te_u[v] = -1;
+            b = off[v];
+            e = off[v + 1];
+            top = e - b > top ? e - b : top;
+            if (e > b) {
+                for (int64_t t = (b + kWTile - 1) / kWTile; t * kWTile < e; ++t) tile_v[t] = (int32_t)v;
+                if (b <= nnz - 1 && nnz - 1 < e) tile_v[ntiles] = (int32_t)v;
+            }
         }
         if (hub_deg > 0) {
+            const bool hub = v < n && e - b >= hub_deg;
+            const unsigned m = __ballot_sync(0xffffffffu, hub);
+            long long k0 = 0;
+            if (m && lane == 0) k0 = (long long)atomicAdd((unsigned long long *)nhub, (unsigned long long)__popc(m));
+            k0 = __shfl_sync(0xffffffffu, k0, 0);
             int32_t id = -1;
-            if (e - b >= hub_deg) {
-                const long long k = (long long)atomicAdd((unsigned long long *)nhub, 1ull);
+            if (hub) {
+                const long long k = k0 + __popc(m & ((1u << lane) - 1u));
                 if (k < hub_cap) {
                     id = (int32_t)k;
                     hubvert[id] = (int32_t)v;
                 }
             }
-            hubidx[v] = id;
+            if (v < n) hubidx[v] = id;
         }
     }
+    const unsigned t = __reduce_max_sync(0xffffffffu, (unsigned)(top < INT32_MAX ? top : INT32_MAX));
+    if (lane == 0 && (int32_t)t > __ldcg(maxdeg)) atomicMax(maxdeg, (int32_t)t);
 }
 
 // Hook every edge u-v (from its arc with u < v). A successful CAS hooks root r
@@ -435,8 +454,11 @@ cudaError_t launch_first_cc(const Dev &d, const OffT *off, const int32_t *adj, i
     if (e0 != cudaSuccess) return e0;
     // the tree edges' CSR positions are kept only where hubs are in use (their keys read them)
     int32_t *te_a = hub_deg > 0 ? d.te_a : nullptr;
+    int32_t *maxdeg = reinterpret_cast<int32_t *>(d.counters + 5);
+    const cudaError_t e1 = cudaMemsetAsync(maxdeg, 0, sizeof(int32_t), L.s);
+    if (e1 != cudaSuccess) return e1;
     k_cc_init<OffT><<<gv, kThreads, 0, L.s>>>(off, n, nnz, d.tile_v, ntiles, d.uf, d.te_u, hub_deg, d.hubidx,
-                                              d.hubvert, d.hub_cap, nhub);
+                                              d.hubvert, d.hub_cap, nhub, maxdeg);
     L.mark("k_cc_init");
     if (nnz > 0) {
         if (cc_local > 0) {

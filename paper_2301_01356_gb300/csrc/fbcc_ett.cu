@@ -113,14 +113,17 @@ __device__ __forceinline__ int hub_sub(int64_t h)
 // exchanges of its many forest edges spread over kHubSub words; sub-list s of hub
 // slot i has its head at hubhead[s * hub_cap + i], so that a hub's heads lie in
 // different cache lines (atomics on one line are processed one at a time).
-// Pushes arc a onto the list whose head is *head, aggregated over runs of
-// neighbouring lanes that push onto the same list (a hub's tree arcs, which come
-// in runs of consecutive edge ids): a run chains its arcs in lane order and its
-// first lane exchanges the head once. A run costs a shuffle and a ballot to find,
-// where matching equal keys anywhere in the warp costs far more and pays only on
-// hub-heavy forests. Every lane calls it; lanes with head == nullptr push nothing.
-// Returns the successor of a in its list.
-__device__ __forceinline__ int32_t push_arc_warp(int32_t *head, int32_t a)
+// Pushes arc a onto the list whose head is *head, aggregated over the warp: lanes
+// that push onto the same list chain their arcs in lane order, and the first of
+// them exchanges the head once. Every lane calls it; lanes with head == nullptr
+// push nothing. Returns the successor of a in its list.
+//  - push_arc_runs: only runs of neighbouring lanes with the same list are joined
+//    (a shuffle and a ballot find them: a hub's tree arcs often come in runs of
+//    edge ids), which costs next to nothing where no list repeats;
+//  - push_arc_match: every lane of the warp with the same list (__match_any_sync),
+//    for graphs with heavy hubs, whose list heads otherwise take a serialised
+//    exchange per arc.
+__device__ __forceinline__ int32_t push_arc_runs(int32_t *head, int32_t a)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long key =
@@ -137,13 +140,32 @@ __device__ __forceinline__ int32_t push_arc_warp(int32_t *head, int32_t a)
     return last ? old : next_a;
 }
 
+__device__ __forceinline__ int32_t push_arc_match(int32_t *head, int32_t a)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long key = head ? (unsigned long long)head : ~0ull - (unsigned long long)lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int first = __ffs(peers) - 1;
+    const unsigned above = peers & ~((2u << lane) - 1u);   // peers above this lane
+    int32_t old = 0;
+    if (head && lane == first) old = atomicExch(head, a);
+    old = __shfl_sync(0xffffffffu, old, first);
+    const int32_t next_a = __shfl_sync(0xffffffffu, a, above ? __ffs(above) - 1 : lane);
+    return above ? next_a : old;
+}
+
+// Degree from which the forest-arc pushes are matched over the whole warp.
+constexpr int kLinkMatchDeg = 4096;
+
 __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__restrict__ te_u,
                                                    const int32_t *__restrict__ te_v,
                                                    const int32_t *__restrict__ hubidx, int32_t *lhead,
-                                                   int32_t *hubhead, int64_t hub_cap, int32_t *nxt)
+                                                   int32_t *hubhead, int64_t hub_cap, int32_t *nxt,
+                                                   const int32_t *__restrict__ maxdeg)
 {
+    const bool match = *maxdeg >= kLinkMatchDeg;   // the same in every thread
     // four edges per thread and step (their loads in flight together); the pushes
-    // are aggregated per warp, see push_arc_warp
+    // are aggregated per warp (push_arc_runs, or push_arc_match on graphs with hubs)
     constexpr int kPer = 4;
     const int64_t T = (int64_t)gridDim.x * kThreads;
     const int64_t n_pad = (n + 31) & ~31ll;
@@ -173,8 +195,13 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
                 pv = hv[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hv[k] : lhead + v[k];
             }
             int2 o;
-            o.x = push_arc_warp(pu, (int32_t)(2 * h));
-            o.y = push_arc_warp(pv, (int32_t)(2 * h + 1));
+            if (match) {
+                o.x = push_arc_match(pu, (int32_t)(2 * h));
+                o.y = push_arc_match(pv, (int32_t)(2 * h + 1));
+            } else {
+                o.x = push_arc_runs(pu, (int32_t)(2 * h));
+                o.y = push_arc_runs(pv, (int32_t)(2 * h + 1));
+            }
             if (u[k] >= 0) *reinterpret_cast<int2 *>(nxt + 2 * h) = o;
         }
     }
@@ -838,7 +865,8 @@ cudaError_t launch_rooting(const Dev &d, const OffT *off, const int32_t *adj, in
     const int32_t *hubidx = hubs ? d.hubidx : nullptr;
     CK(cudaMemsetAsync(d.lhead, 0xff, n * sizeof(int32_t), L.s));
     if (hubs) CK(cudaMemsetAsync(d.hubhead, 0xff, d.hub_cap * kHubSub * sizeof(int32_t), L.s));
-    k_link<<<gv, kThreads, 0, L.s>>>(n, te_u, te_v, hubidx, d.lhead, d.hubhead, d.hub_cap, d.nxt);
+    k_link<<<gv, kThreads, 0, L.s>>>(n, te_u, te_v, hubidx, d.lhead, d.hubhead, d.hub_cap, d.nxt,
+                                     reinterpret_cast<const int32_t *>(d.counters + 5));
     L.mark("k_link");
     if (hubs) {
         k_hub_order<<<grid_for(L, ceil_div(d.hub_cap * 32, kThreads)), kThreads, 0, L.s>>>(
