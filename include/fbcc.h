@@ -80,8 +80,9 @@ typedef struct {
                               shared memory first (power of 2, 1024..16384; 0 = off); a range
                               whose lists hold 2^31 arcs or more makes the solve report
                               FBCC_E_INVALID in device_status */
-    int32_t lcc_sample;    /* Last-CC: first arcs per vertex tested and united before the full pass
-                              (0 = off, 1..4); the full pass then chooses as for cc_sample */
+    int32_t lcc_sample;    /* Last-CC: first arcs per vertex (the tree arc to its parent not
+                              counted) tested and united before the full pass (0 = off, 1..4);
+                              the full pass then chooses as for cc_sample */
     int32_t rank_variant;  /* list ranking above the rulers: 0 = sample the ruler lists again and rank
                               the top level in one CTA (default); 1 = pointer jumping (Wyllie) over
                               the ruler lists, a fixed number of grid-wide rounds */

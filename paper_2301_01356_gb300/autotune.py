@@ -44,7 +44,7 @@ KNOBS = [
             dict(cc_local=0, cc_sample=2, cc_ldd=0), dict(cc_local=0, cc_sample=0, cc_ldd=2),
             dict(cc_local=0, cc_sample=0, cc_ldd=8)]),
     ("ruler_stride", [dict(ruler_stride=s) for s in (8, 16, 32, 64)]),
-    ("lcc_sample", [dict(lcc_sample=q) for q in (0, 2, 4)]),
+    ("lcc_sample", [dict(lcc_sample=q) for q in (0, 1, 2, 4)]),
     ("chase_chains", [dict(chase_chains=c) for c in (1, 2)]),
     ("rank_variant", [dict(rank_variant=r) for r in (0, 1)]),
     ("cc_order", [dict(cc_order=o) for o in (0, 1)]),

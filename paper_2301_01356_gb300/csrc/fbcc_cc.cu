@@ -695,8 +695,10 @@ __device__ __forceinline__ bool cross_from(int32_t fu, int32_t lastu, int32_t fw
     return later ? fw > lastu : fu > __ldg(lastp + fw);
 }
 
-// One vertex per thread, its K arcs' gathers issued together before the unions
-// (a tree root has no cross edges and is passed over).
+// One vertex per thread: its first K arcs other than the tree arc to its parent
+// (which is never a cross edge, and under sampled hooking is usually the first
+// arc), their gathers issued together before the unions (a tree root has no
+// cross edges and is passed over).
 template <typename OffT, int K>
 __global__ void __launch_bounds__(kThreads) k_lcc_sample(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
                                                          int64_t n, const int2 *__restrict__ fp,
@@ -704,26 +706,33 @@ __global__ void __launch_bounds__(kThreads) k_lcc_sample(const OffT *__restrict_
                                                          const uint8_t *__restrict__ dirb, int32_t *uf, int *err)
 {
     for (int64_t v = blockIdx.x * (int64_t)kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
-        if (fp[v].y < 0) continue;
+        const int32_t par = fp[v].y;
+        if (par < 0) continue;
         const int64_t b = off[v];
         const int64_t deg = off[v + 1] - b;
-        const int cnt = deg < K ? (int)deg : K;
+        const int cntl = deg < K + 1 ? (int)deg : K + 1;
         const int2 cs = cr[v];
-        int32_t w[K];
+        int32_t wl[K + 1];
 #pragma unroll
-        for (int j = 0; j < K; ++j) w[j] = j < cnt ? adj[b + j] : 0;
+        for (int j = 0; j <= K; ++j) wl[j] = j < cntl ? adj[b + j] : -1;
+        int sk = K;   // the parent arc's index among the first K arcs, else K
+#pragma unroll
+        for (int j = K - 1; j >= 0; --j)
+            if (wl[j] == par) sk = j;
         const int32_t lastu = __ldg(lastp + cs.x);
         int2 cd[K];
-        bool later[K];
+        bool later[K], ok[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            cd[j] = j < cnt ? __ldg(cr + w[j]) : cs;
-            later[j] = j < cnt && dir_bit(dirb, b + j);
+        for (int i = 0; i < K; ++i) {
+            const int idx = i < sk ? i : i + 1;
+            ok[i] = idx < cntl;
+            cd[i] = ok[i] ? __ldg(cr + wl[idx]) : cs;
+            later[i] = ok[i] && dir_bit(dirb, b + idx);
         }
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (cd[j].y == cs.y || !cross_from(cs.x, lastu, cd[j].x, later[j], lastp)) continue;
-            uf_unite(uf, cs.y, cd[j].y, err);
+        for (int i = 0; i < K; ++i) {
+            if (!ok[i] || cd[i].y == cs.y || !cross_from(cs.x, lastu, cd[i].x, later[i], lastp)) continue;
+            uf_unite(uf, cs.y, cd[i].y, err);
         }
     }
 }
