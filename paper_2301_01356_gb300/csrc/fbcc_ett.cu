@@ -113,45 +113,44 @@ __device__ __forceinline__ int hub_sub(int64_t h)
 // exchanges of its many forest edges spread over kHubSub words; sub-list s of hub
 // slot i has its head at hubhead[s * hub_cap + i], so that a hub's heads lie in
 // different cache lines (atomics on one line are processed one at a time).
-// Pushes arc a onto the list whose head is *head, aggregated over the warp: lanes
-// that push onto the same list chain their arcs in lane order, and the first of
-// them exchanges the head once. Every lane calls it; lanes with head == nullptr
-// push nothing. Returns the successor of a in its list.
-//  - push_arc_runs: only runs of neighbouring lanes with the same list are joined
-//    (a shuffle and a ballot find them: a hub's tree arcs often come in runs of
-//    edge ids), which costs next to nothing where no list repeats;
-//  - push_arc_match: every lane of the warp with the same list (__match_any_sync),
-//    for graphs with heavy hubs, whose list heads otherwise take a serialised
+// Pushes of arcs onto lists, aggregated over the warp: the lanes that push onto
+// the same list chain their arcs in lane order, and the first of them exchanges
+// the list head once. Every lane takes part; a lane with head == nullptr pushes
+// nothing. A push is split in two so that a thread's exchanges are all in flight
+// together: push_group finds the lane's group (the first lane, which exchanges,
+// and the next lane of the group, or -1 for the last, whose successor is the old
+// head), the caller issues the exchanges, and push_resolve turns them into each
+// arc's successor.
+//  - runs: only runs of neighbouring lanes with the same list are joined (a
+//    shuffle and a ballot find them: a hub's tree arcs often come in runs of edge
+//    ids), which costs next to nothing where no list repeats;
+//  - match: every lane of the warp with the same list (__match_any_sync), for
+//    graphs with heavy hubs, whose list heads otherwise take a serialised
 //    exchange per arc.
-__device__ __forceinline__ int32_t push_arc_runs(int32_t *head, int32_t a)
+__device__ __forceinline__ void push_group(const int32_t *head, bool match, int &first, int &next)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long key =
-        head ? (unsigned long long)head : ~0ull - (unsigned long long)lane;   // an idle lane is its own run
-    const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
-    const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
-    const unsigned upto = starts & ((2u << lane) - 1u);   // run starts at or below this lane (2u << 31 wraps to 0)
-    const int first = 31 - __clz(upto);
-    const bool last = lane == 31 || ((starts >> (lane + 1)) & 1u);
-    int32_t old = 0;
-    if (head && lane == first) old = atomicExch(head, a);   // the run's first arc heads its chain
-    old = __shfl_sync(0xffffffffu, old, first);
-    const int32_t next_a = __shfl_down_sync(0xffffffffu, a, 1);
-    return last ? old : next_a;
+        head ? (unsigned long long)head : ~0ull - (unsigned long long)lane;   // an idle lane is alone
+    if (match) {
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        first = __ffs(peers) - 1;
+        const unsigned above = peers & ~((2u << lane) - 1u);   // peers above this lane (2u << 31 wraps to 0)
+        next = above ? __ffs(above) - 1 : -1;
+    } else {
+        const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+        first = 31 - __clz(starts & ((2u << lane) - 1u));       // the run's start at or below this lane
+        next = (lane == 31 || ((starts >> (lane + 1)) & 1u)) ? -1 : lane + 1;
+    }
 }
 
-__device__ __forceinline__ int32_t push_arc_match(int32_t *head, int32_t a)
+__device__ __forceinline__ int32_t push_resolve(int32_t old, int32_t a, int first, int next)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned long long key = head ? (unsigned long long)head : ~0ull - (unsigned long long)lane;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int first = __ffs(peers) - 1;
-    const unsigned above = peers & ~((2u << lane) - 1u);   // peers above this lane
-    int32_t old = 0;
-    if (head && lane == first) old = atomicExch(head, a);
-    old = __shfl_sync(0xffffffffu, old, first);
-    const int32_t next_a = __shfl_sync(0xffffffffu, a, above ? __ffs(above) - 1 : lane);
-    return above ? next_a : old;
+    const int32_t head_old = __shfl_sync(0xffffffffu, old, first);
+    const int32_t next_a = __shfl_sync(0xffffffffu, a, next >= 0 ? next : lane);
+    return next >= 0 ? next_a : head_old;
 }
 
 // Degree from which the forest-arc pushes are matched over the whole warp.
@@ -164,8 +163,9 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
                                                    const int32_t *__restrict__ maxdeg)
 {
     const bool match = *maxdeg >= kLinkMatchDeg;   // the same in every thread
-    // four edges per thread and step (their loads in flight together); the pushes
-    // are aggregated per warp (push_arc_runs, or push_arc_match on graphs with hubs)
+    const int lane = threadIdx.x & 31;
+    // four edges per thread and step: their loads, and then their eight exchanges,
+    // in flight together
     constexpr int kPer = 4;
     const int64_t T = (int64_t)gridDim.x * kThreads;
     const int64_t n_pad = (n + 31) & ~31ll;
@@ -185,23 +185,27 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
             hu[k] = __ldg(hubidx + u[k]);
             hv[k] = __ldg(hubidx + v[k]);
         }
+        int first[2 * kPer], next[2 * kPer];
+        int32_t old[2 * kPer];
+#pragma unroll
+        for (int j = 0; j < 2 * kPer; ++j) {
+            const int k = j >> 1;
+            const int64_t h = h0 + k * T;
+            const int s = hub_sub(h);   // the sub-list of both arcs of edge h
+            int32_t *p = nullptr;
+            if (u[k] >= 0) {
+                if (j & 1) p = hv[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hv[k] : lhead + v[k];
+                else p = hu[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hu[k] : lhead + u[k];
+            }
+            push_group(p, match, first[j], next[j]);
+            old[j] = (p && lane == first[j]) ? atomicExch(p, (int32_t)(2 * h + (j & 1))) : 0;
+        }
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int64_t h = h0 + k * T;
-            const int s = hub_sub(h);   // the sub-list of both arcs of edge h
-            int32_t *pu = nullptr, *pv = nullptr;
-            if (u[k] >= 0) {
-                pu = hu[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hu[k] : lhead + u[k];
-                pv = hv[k] >= 0 ? hubhead + (int64_t)s * hub_cap + hv[k] : lhead + v[k];
-            }
             int2 o;
-            if (match) {
-                o.x = push_arc_match(pu, (int32_t)(2 * h));
-                o.y = push_arc_match(pv, (int32_t)(2 * h + 1));
-            } else {
-                o.x = push_arc_runs(pu, (int32_t)(2 * h));
-                o.y = push_arc_runs(pv, (int32_t)(2 * h + 1));
-            }
+            o.x = push_resolve(old[2 * k], (int32_t)(2 * h), first[2 * k], next[2 * k]);
+            o.y = push_resolve(old[2 * k + 1], (int32_t)(2 * h + 1), first[2 * k + 1], next[2 * k + 1]);
             if (u[k] >= 0) *reinterpret_cast<int2 *>(nxt + 2 * h) = o;
         }
     }
