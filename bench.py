@@ -865,6 +865,13 @@ def run_serve(args, world, rank, local):
         alone.close()
         vsrv.close()
         check = {"requests": len(vsrv.outputs), "graphs": len(solo), "equal_to_alone": bool(ok)}
+    # queries from resident state (section 3.4): query requests on pool graphs, each
+    # graph solved on its first query and answered from its resident state after
+    qs = serving.QueryServer(pool, hbm_budget=150 << 30)
+    qids = np.random.default_rng(5).integers(0, len(graphs), size=args.query_requests)
+    qrep = qs.run(qids, pairs=4096, seed=5)
+    qs.close()
+    qrep["api"] = "serving.QueryServer: fbcc_query_biconnected on each graph's resident solved workspace"
     line = {
         "metric": METRIC, "value": rep["edges_per_s"], "unit": UNIT, "n_gpus": world, "steps": rep["requests"],
         "warmup": 1, "ms_per_step": rep["p50_ms"], "higher_is_better": True, "scaling": "weak",
@@ -881,7 +888,7 @@ def run_serve(args, world, rank, local):
                              "edges_per_s": loop["edges_per_s"],
                              "api": "fbcc_solve per request on its resident CSR, outputs to pinned host memory"},
         "serving_vs_loop_graphs_per_s": sat["completed_per_s"] / loop["graphs_per_s"],
-        "mix_vs_alone": check, "clocks": clocks,
+        "mix_vs_alone": check, "queries": qrep, "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -903,6 +910,8 @@ def main(argv=None):
     ap.add_argument("--saturation-requests", type=int, default=4000,
                     help="serve: requests of the all-at-once saturation run")
     ap.add_argument("--loop-requests", type=int, default=1000, help="serve: requests of the per-request loop")
+    ap.add_argument("--query-requests", type=int, default=2000,
+                    help="serve: query requests (4096 vertex pairs each) answered from resident state")
     ap.add_argument("--impl", default="fbcc", choices=("fbcc", "reference"))
     ap.add_argument("--config", default="tuned", choices=("tuned", "default"),
                     help="start from the autotuner's table (paper_2301_01356_gb300/tuning.json) or the defaults")

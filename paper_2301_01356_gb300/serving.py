@@ -21,6 +21,11 @@ clock. The server keeps several batches in flight, each on its own stream:
 A request is complete when its batch's copies have landed; latency = completion
 minus arrival. The same requests can also be served one at a time with the plain
 form (per_request_loop) for comparison.
+
+Queries (QueryServer) are served from resident state: a graph's solved workspace
+(labels, heads and ranks, section 3.4's representation) stays on the device after
+its first query, so later "are u and v biconnected" and "BCCs of v" queries on it
+need no new solve.
 """
 from __future__ import annotations
 
@@ -280,6 +285,101 @@ class Server:
             fbcc.fbcc_workspace_destroy(b.ws)
         self.inflight = []
         self.store.clear()
+
+
+class QueryServer:
+    """Biconnectivity queries (section 3.4: "are u and v biconnected", "the BCCs of
+    v") answered from solved state kept on the device.
+
+    A graph is solved on its first query into a workspace of its own; its labels,
+    heads and ranks then answer every later query on it with the fbcc_query_* calls,
+    without another solve. When the next graph's state would not fit the HBM budget,
+    the states of the least recently queried graphs are released. Queries are
+    enqueued on the current stream after the solve they read, in call order."""
+
+    def __init__(self, pool: Pool, hbm_budget: int = 150 << 30, config: dict | None = None, device="cuda"):
+        import torch
+        self.torch, self.pool, self.budget, self.device = torch, pool, int(hbm_budget), device
+        self.config = dict(config or {})
+        self.state = collections.OrderedDict()   # graph id -> (Solver, offsets, adjacency, bytes)
+        self.held = 0
+        self.solves = self.hits = self.evictions = 0
+
+    def state_bytes(self, g: int) -> int:
+        """Device bytes of graph g's resident state: workspace, outputs and CSR."""
+        n, z = int(self.pool.n[g]), int(self.pool.nnz[g])
+        return fbcc.fbcc_workspace_bytes(n, z) + 9 * n + 5 * z + 8 * (n + 1) + 4 * z + 4096
+
+    def solver(self, g: int):
+        """Graph g's solved state, solving it (and releasing older states) when absent."""
+        g = int(g)
+        if g in self.state:
+            self.state.move_to_end(g)
+            self.hits += 1
+            return self.state[g][0]
+        need = self.state_bytes(g)
+        if need > self.budget:
+            raise MemoryError(f"graph {g} needs {need} bytes of state, over the budget of {self.budget}")
+        while self.state and self.held + need > self.budget:
+            _, (old, _, _, b) = self.state.popitem(last=False)
+            old.close()
+            self.held -= b
+            self.evictions += 1
+        torch = self.torch
+        gr = self.pool.graphs[g]
+        offs = gr.offsets.astype(np.int64 if gr.nnz >= (1 << 31) else np.int32)
+        off = torch.from_numpy(offs).to(self.device, non_blocking=True)
+        adj = self.pool.adj[g].to(self.device, non_blocking=True)
+        s = fbcc.Solver(gr.n, gr.nnz, device=self.device, **self.config)
+        s.enqueue(off, adj)
+        self.state[g] = (s, off, adj, need)
+        self.held += need
+        self.solves += 1
+        return s
+
+    def biconnected(self, g: int, u, v):
+        """Device int32 tensor: the BCC that u[i] and v[i] of graph g share, or -1."""
+        return self.solver(g).biconnected(u, v)
+
+    def bccs_of(self, g: int, v):
+        """(offsets, ids) on the device: the BCCs of v[i] of graph g are ids[offsets[i]:offsets[i + 1]]."""
+        return self.solver(g).bccs_of(v)
+
+    def run(self, graph_ids: np.ndarray, pairs: int, seed: int = 0) -> dict:
+        """One query request per entry of graph_ids, each `pairs` random vertex pairs of
+        its graph, answered back to back with the answers copied to pinned host
+        memory; the throughput, the share answered from resident state, and the
+        per-request latency."""
+        torch = self.torch
+        rng = np.random.default_rng(seed)
+        h_out = torch.empty(pairs, dtype=torch.int32).pin_memory()
+        lat = []
+        s0, h0 = self.solves, self.hits
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g in graph_ids:
+            n = int(self.pool.n[g])
+            t1 = time.perf_counter()
+            uv = torch.from_numpy(rng.integers(0, max(n, 1), size=(2, pairs), dtype=np.int32)).to(self.device)
+            out = self.biconnected(int(g), uv[0], uv[1])
+            h_out.copy_(out, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            lat.append(time.perf_counter() - t1)
+        wall = time.perf_counter() - t0
+        lat = np.sort(np.array(lat)) * 1e3
+        R = len(graph_ids)
+        return {"requests": R, "pairs_per_request": pairs, "wall_s": wall, "requests_per_s": R / wall,
+                "pairs_per_s": R * pairs / wall, "solves": self.solves - s0,
+                "answered_from_resident_state": self.hits - h0,
+                "p50_ms": float(lat[len(lat) // 2]), "p99_ms": float(lat[min(len(lat) - 1, int(0.99 * len(lat)))]),
+                "resident_states": len(self.state), "resident_bytes": self.held, "evictions": self.evictions}
+
+    def close(self):
+        self.torch.cuda.synchronize()
+        for s, _, _, _ in self.state.values():
+            s.close()
+        self.state.clear()
+        self.held = 0
 
 
 def per_request_loop(pool: Pool, graph_ids: np.ndarray, device="cuda") -> dict:

@@ -76,3 +76,43 @@ def test_serving_admission_by_footprint(torch_cuda, oracle):
     assert loop["requests"] == 24 and loop["graphs_per_s"] > 0
     with pytest.raises(ValueError):
         serving.Server(pool, hbm_budget=big // 4)
+
+
+def test_queries_from_resident_state(torch_cuda, oracle):
+    """Queries served from resident solved state (QueryServer): every answer equals the
+    one derived from the oracle's labels; repeated graphs are answered without a new
+    solve; a budget that holds two graphs' states evicts the least recently queried,
+    and a graph solved again after eviction answers the same."""
+    from paper_2301_01356_gb300 import serving
+    from test_gpu_query import expected_pairs, vertex_bccs
+    graphs = [gg.grid(80, 70, p=0.62, seed=4), gg.uniform(6000, 15000, 3), gg.rmat(12, 8, seed=2),
+              gg.cycle_chain(5000, 10, 3, 300, 5)]
+    pool = serving.Pool(torch_cuda, graphs)
+    sets = []
+    for g in graphs:
+        e = oracle.solve(g.offsets, g.adj)
+        sets.append(vertex_bccs(g.offsets, np.asarray(e["edge_bcc"])))
+    budget = max(serving.QueryServer(pool).state_bytes(g) for g in range(len(graphs))) * 2 + 1
+    qs = serving.QueryServer(pool, hbm_budget=budget)
+    rng = np.random.default_rng(11)
+    order = [0, 0, 1, 0, 2, 3, 1, 1, 0, 2, 3, 3]
+    for g in order:
+        n = graphs[g].n
+        u = rng.integers(0, n, 500).astype(np.int32)
+        v = rng.integers(0, n, 500).astype(np.int32)
+        # half the pairs are the two ends of an edge, which always share a BCC
+        a = rng.integers(0, graphs[g].nnz, 250)
+        u[:250] = (np.searchsorted(graphs[g].offsets, a, side="right") - 1).astype(np.int32)
+        v[:250] = graphs[g].adj[a]
+        dev = lambda x: torch_cuda.from_numpy(x).cuda()
+        got = qs.biconnected(g, dev(u), dev(v)).cpu().numpy()
+        assert np.array_equal(got, expected_pairs(sets[g], u, v)), f"graph {g}"
+        off, ids = qs.bccs_of(g, dev(np.arange(n, dtype=np.int32)))
+        off, ids = off.cpu().numpy(), ids.cpu().numpy()
+        for x in range(0, n, 97):
+            assert np.array_equal(np.sort(ids[off[x]:off[x + 1]]), sets[g][x]), f"graph {g}: BCCs of {x}"
+        assert qs.held <= budget
+    assert qs.hits > 0 and qs.evictions > 0 and qs.solves > len(graphs)
+    rep = qs.run(np.array([0, 1, 0, 1, 0], np.int64), pairs=1000, seed=3)
+    assert rep["requests"] == 5 and rep["answered_from_resident_state"] >= 3
+    qs.close()
