@@ -186,7 +186,7 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_cc_count": 0, "k_cc_place": 0, "k_permute_te": 0, "k_scan_i32": 0, "k_link": 8 * A, "k_hub_order": 0, "k_succ_rulers": 16 * A, "k_chase": 8 * A, "k_lvl_rulers": 0, "k_lvl_chase": 0,
         "k_top": 0, "k_lvl_expand": 0, "k_jump": 0, "k_comp_size": 0, "k_place_records": 8 * A, "k_preorder": 8 * A + 16 * n,
         # Tagging
-        "k_first_of": 0, "k_w12": B * n + 4 * nnz + 8 * n, "k_rmq_prefix": 8 * n, "k_rmq_level": 0,
+        "k_first_of": 0, "k_w12": B * n + 4 * nnz + 8 * n, "k_w12_keep": B * n + 4 * nnz + 8 * n, "k_rmq_prefix": 8 * n, "k_rmq_level": 0,
         "k_rmq_query": 24 * n,
         # Last-CC
         "k_ext_compact": 0, "k_ext_halve": 0, "k_ext_finish": 0, "k_plain_label": 0,

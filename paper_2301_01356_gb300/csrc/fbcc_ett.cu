@@ -153,8 +153,6 @@ __device__ __forceinline__ int32_t push_resolve(int32_t old, int32_t a, int firs
     return next >= 0 ? next_a : head_old;
 }
 
-// Degree from which the forest-arc pushes are matched over the whole warp.
-constexpr int kLinkMatchDeg = 4096;
 
 __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__restrict__ te_u,
                                                    const int32_t *__restrict__ te_v,
@@ -162,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_link(int64_t n, const int32_t *__r
                                                    int32_t *hubhead, int64_t hub_cap, int32_t *nxt,
                                                    const int32_t *__restrict__ maxdeg)
 {
-    const bool match = *maxdeg >= kLinkMatchDeg;   // the same in every thread
+    const bool match = *maxdeg >= kHeavyDeg;   // the same in every thread
     const int lane = threadIdx.x & 31;
     // four edges per thread and step: their loads, and then their eight exchanges,
     // in flight together

@@ -270,6 +270,28 @@ __device__ __forceinline__ void warp_append(T *q, long long *cnt, int64_t cap, b
     }
 }
 
+// Graphs whose largest degree (taken by First-CC's init pass into counters[5]) is
+// at least this have heavy hubs: their arc passes see the same targets again and
+// again, and some kernels take another form for them.
+constexpr int kHeavyDeg = 4096;
+
+// L2 eviction priority of a gather (a PTX cache policy, sm_80 and later): lines
+// loaded with the evict_last policy stay in L2 ahead of lines loaded normally.
+__device__ __forceinline__ uint64_t l2_keep_policy()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// A read-only 4-byte load through the non-coherent path with an L2 cache policy.
+__device__ __forceinline__ int32_t ld_nc_policy(const int32_t *a, uint64_t policy)
+{
+    int32_t v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(policy));
+    return v;
+}
+
 __device__ __forceinline__ int32_t warp_sum_i32(int32_t x)
 {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
