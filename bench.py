@@ -199,7 +199,7 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, n_cc: int, off_bytes: int, 
         "k_tv_unite": 8 * (nnz + n),
         # Outputs
         "k_ap_keys": 12 * n, "k_key_list": 0, "k_key_adj": 0, "k_key_scan": 0, "k_key_bits": 0, "k_scan_popc": 0, "k_rank": 0, "k_fo": 0,
-        "k_edge_out": B * n + 9 * nnz, "k_bcc_base": 0, "k_batch_stats": 0, "k_finish": 0,
+        "k_edge_out": B * n + 9 * nnz, "k_edge_out_keep": B * n + 9 * nnz, "k_bcc_base": 0, "k_batch_stats": 0, "k_finish": 0,
     }
     return table.get(kernel)
 

@@ -465,14 +465,23 @@ __global__ void __launch_bounds__(kThreads) k_batch_stats(int64_t n, Batch B, co
     }
 }
 
-// edge_bcc / is_bridge for every arc.
-template <typename OffT>
-__global__ void __launch_bounds__(kThreads, 8) k_edge_out(const OffT *__restrict__ off, const int32_t *__restrict__ adj,
-                                                       int64_t nnz, const int32_t *__restrict__ tile_v, int64_t ntiles,
-                                                       const int32_t *__restrict__ word,
-                                                       const uint8_t *__restrict__ dirb, int32_t *edge_bcc,
-                                                       uint8_t *is_bridge, bool vec, bool vec_out)
+// edge_bcc / is_bridge for every arc. Two forms, both launched; the one that does
+// not fit the graph returns at once. On graphs with heavy hubs (kKeep) the word
+// gathers keep their lines in L2 ahead of the streaming adjacency and outputs,
+// with the register room that the policy takes.
+template <typename OffT, bool kKeep>
+__global__ void __launch_bounds__(kThreads, kKeep ? 6 : 8) k_edge_out(const OffT *__restrict__ off,
+                                                                     const int32_t *__restrict__ adj, int64_t nnz,
+                                                                     const int32_t *__restrict__ tile_v,
+                                                                     int64_t ntiles,
+                                                                     const int32_t *__restrict__ word,
+                                                                     const uint8_t *__restrict__ dirb,
+                                                                     int32_t *edge_bcc, uint8_t *is_bridge, bool vec,
+                                                                     bool vec_out,
+                                                                     const int32_t *__restrict__ maxdeg)
 {
+    if ((*maxdeg >= kHeavyDeg) != kKeep) return;
+    const uint64_t policy = kKeep ? l2_keep_policy() : 0ull;
     __shared__ OffT win_all[kWarpsPerCta * kWarpWin];
     OffT *win = win_all + (threadIdx.x >> 5) * kWarpWin;
     ArcTile<OffT> at;
@@ -490,8 +499,13 @@ __global__ void __launch_bounds__(kThreads, 8) k_edge_out(const OffT *__restrict
         // are few and neighbouring, so their repeated loads hit L1)
         int32_t wx[kItems];
 #pragma unroll
-        for (int j = 0; j < kItems; ++j)
-            wx[j] = j < at.cnt ? __ldg(word + ((bits >> j) & 1u ? d[j] : at.src[j])) : 0;
+        for (int j = 0; j < kItems; ++j) {
+            wx[j] = 0;
+            if (j < at.cnt) {
+                const int32_t *a = word + ((bits >> j) & 1u ? d[j] : at.src[j]);
+                wx[j] = kKeep ? ld_nc_policy(a, policy) : __ldg(a);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             lab8[j] = 0;
@@ -566,9 +580,14 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
         k_fo<<<gv, kThreads, 0, L.s>>>(n, d.fp, d.lab, d.rank, d.vbits, d.word, d.stats);
         L.mark("k_fo");
         const bool vec_out = ((uintptr_t)edge_bcc & 15) == 0 && ((uintptr_t)is_bridge & 7) == 0;
-        k_edge_out<OffT><<<grid_for(L, ceil_div(ntiles, kWarpsPerCta)), kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles,
-                                                                   d.word, d.dirb, edge_bcc, is_bridge, vec, vec_out);
+        const int32_t *maxdeg = reinterpret_cast<const int32_t *>(d.counters + 5);
+        const int ge = grid_for(L, ceil_div(ntiles, kWarpsPerCta));
+        k_edge_out<OffT, false><<<ge, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.word, d.dirb, edge_bcc,
+                                                          is_bridge, vec, vec_out, maxdeg);
         L.mark("k_edge_out");
+        k_edge_out<OffT, true><<<ge, kThreads, 0, L.s>>>(off, adj, nnz, d.tile_v, ntiles, d.word, d.dirb, edge_bcc,
+                                                         is_bridge, vec, vec_out, maxdeg);
+        L.mark("k_edge_out_keep");
     } else if (B.G > 0) {
         CK(cudaMemsetAsync(B.bcc_base, 0, (B.G + 1) * sizeof(int64_t), L.s));
     }
