@@ -298,8 +298,13 @@ __global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const OffT *__
                                                        const int32_t *__restrict__ lab,
                                                        const int32_t *__restrict__ kmin,
                                                        const int32_t *__restrict__ parc, unsigned long long *key,
-                                                       uint32_t *key_bits, int64_t nnz, int *err)
+                                                       uint32_t *key_bits, int64_t nnz, int *err,
+                                                       const int32_t *__restrict__ maxdeg)
 {
+    // On graphs with heavy hubs many labels search one hub's list: the searches load
+    // with the evict-last policy, so that the levels they share stay in L2.
+    const bool keep = *maxdeg >= kHeavyDeg;
+    const uint64_t policy = l2_keep_policy();
     // kVPer vertices per thread and step, each round of their loads issued together
     const int64_t T = (int64_t)gridDim.x * kThreads;
     for (int64_t v0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; v0 < n; v0 += T * kVPer) {
@@ -335,7 +340,8 @@ __global__ void __launch_bounds__(kThreads) k_key_bits(int64_t n, const OffT *__
             int64_t lo = off[h], hi = off[h + 1];
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
-                if (adj[mid] < w) lo = mid + 1; else hi = mid;
+                const int32_t am = keep ? ld_nc_policy(adj + mid, policy) : __ldg(adj + mid);
+                if (am < w) lo = mid + 1; else hi = mid;
             }
             if (lo >= (int64_t)off[h + 1] || adj[lo] != w) {
                 atomicOr(err, kErrIndex);
@@ -567,7 +573,8 @@ cudaError_t launch_outputs(const Dev &d, const OffT *off, const int32_t *adj, in
         L.mark("k_key_scan");
         CK(cudaMemsetAsync(d.key_bits, 0, nwords * sizeof(uint32_t), L.s));
         k_key_bits<OffT><<<gv, kThreads, 0, L.s>>>(n, off, adj, d.fp, d.lab, d.kmin, hubs ? d.parc : nullptr, d.key,
-                                                    d.key_bits, nnz, d.err);
+                                                    d.key_bits, nnz, d.err,
+                                                    reinterpret_cast<const int32_t *>(d.counters + 5));
         L.mark("k_key_bits");
         CK(cudaGetLastError());
         CK(launch_scan_popc(d, d.key_bits, d.key_pre, nwords, L));
