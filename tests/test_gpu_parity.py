@@ -382,3 +382,21 @@ def test_bucketed_batch_runner(torch_cuda, oracle, max_chunk_arcs):
             assert got["n_bcc"] == bt.truth_bcc[g] and got["n_ap"] == bt.truth_ap[g]
     alone.close()
     runner.close()
+
+
+def test_heavy_hub_forms_both_offset_widths(torch_cuda, oracle):
+    """A graph whose largest degree reaches the heavy-hub threshold (4,096 arcs), so
+    that the two full arc passes and the key searches take their L2-hinted forms:
+    every output equals the oracle's with int32 and int64 offsets, in the defaults
+    and in the tuned R-MAT configuration, and through the Tarjan-Vishkin foil."""
+    from paper_2301_01356_gb300 import fbcc
+    g = gg.rmat(16, 16, seed=3)
+    assert int(np.diff(g.offsets).max()) >= 4096
+    e = oracle.solve(g.offsets, g.adj)
+    for cfg in ({}, _tuned("rmat24")):
+        s = fbcc.Solver(g.n, g.nnz, **cfg)
+        for off64 in (True, False):
+            off, adj = to_dev(torch_cuda, g, off64)
+            assert_same(s.solve(off, adj), e, f"{cfg} off64={off64}")
+            assert_same(s.solve_tv(off, adj), e, f"tv {cfg} off64={off64}")
+        s.close()
