@@ -85,6 +85,7 @@ class Server:
         self.peak_bytes = 0
         self.keep_outputs = keep_outputs
         self.outputs = {}
+        self.failed = 0                                  # requests whose solve reported a device status
         g_max = int(np.argmax(pool.nnz))
         if batch_footprint(int(pool.n[g_max]), int(pool.nnz[g_max]), 1) + self._csr_bytes(g_max) > self.budget:
             raise ValueError("the largest pool graph does not fit the HBM budget")
@@ -194,10 +195,12 @@ class Server:
         self.inflight.append(b)
 
     def _collect(self, b, now: float, complete: np.ndarray):
-        for r, _ in b.requests:
+        st = b.h_stats.numpy()
+        for j, (r, _) in enumerate(b.requests):
             complete[r] = now
+            if int(st[j * STATS_WORDS + 4]) & 0xffffffff:
+                self.failed += 1
         if self.keep_outputs:
-            st = b.h_stats.numpy()
             for j, (r, g) in enumerate(b.requests):
                 s = st[j * STATS_WORDS:(j + 1) * STATS_WORDS]
                 nb = int(s[0])
@@ -238,6 +241,7 @@ class Server:
         """Serve requests arriving at `arrivals` (seconds from the start, ascending)
         for pool graphs `graph_ids`; returns latency and throughput figures."""
         R = len(arrivals)
+        f0 = self.failed
         complete = np.full(R, np.nan)
         waiting = collections.deque()
         nxt = 0
@@ -277,6 +281,7 @@ class Server:
             "max_queue": int(max(depth) if depth else 0), "streams": len(self.streams),
             "peak_device_bytes": self.peak_bytes, "resident_graphs": len(self.store),
             "resident_bytes": self.store_bytes, "budget_bytes": self.budget,
+            "failed": self.failed - f0,
         }
 
     def close(self):
@@ -331,7 +336,11 @@ class QueryServer:
         off = torch.from_numpy(offs).to(self.device, non_blocking=True)
         adj = self.pool.adj[g].to(self.device, non_blocking=True)
         s = fbcc.Solver(gr.n, gr.nnz, device=self.device, **self.config)
-        s.enqueue(off, adj)
+        st = s.enqueue(off, adj)
+        torch.cuda.current_stream().synchronize()    # a failed solve must not answer queries
+        if st.device_status:
+            s.close()
+            raise fbcc.FbccError(st.device_status, f"solve of graph {g}")
         self.state[g] = (s, off, adj, need)
         self.held += need
         self.solves += 1
